@@ -1,0 +1,172 @@
+/*
+ * nbody_oracle.c -- plain FP64 CPU oracle for direct-summation gravity.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library and
+ * its Python binding) may include, link or call this file; only the tests, the
+ * smoke check and the CPU-baseline leg of the benchmark do.  It shares no code,
+ * header, table or helper with the CUDA path.
+ *
+ * What it computes (Almerol et al., SC'25 workshops, Sec. 3, the force sum):
+ *
+ *     F_i = sum_{j != i} G m_i m_j (r_j - r_i) / r_ij^3
+ *
+ * divided by m_i (the paper computes the acceleration), with the Plummer
+ * softening length eps inserted as r_ij^2 -> r_ij^2 + eps^2, plus the softened
+ * potential at particle i due to all others:
+ *
+ *     a_i   =  G sum_{j != i} m_j (r_j - r_i) / (|r_j - r_i|^2 + eps^2)^(3/2)
+ *     phi_i = -G sum_{j != i} m_j           / (|r_j - r_i|^2 + eps^2)^(1/2)
+ *
+ * Every quantity is IEEE double.  Each i runs one sequential j loop in
+ * increasing j with Neumaier-compensated sums, so the result is the exact sum up
+ * to one or two final roundings, and it does not depend on the OpenMP thread
+ * count (threads only split the i loop).
+ *
+ * The time integrator is kick-drift-kick leapfrog (the paper says the
+ * integration runs in FP64 on the host, Sec. 3, mixed-precision paragraph; it
+ * does not name the scheme, KDK is the reading used here):
+ *
+ *     v_{1/2} = v + (dt/2) a(x);   x' = x + dt v_{1/2};   v' = v_{1/2} + (dt/2) a(x')
+ *
+ * Diagnostics: K = 1/2 sum m |v|^2, W = 1/2 sum m phi, E = K + W,
+ * P = sum m v, L = sum m (x cross v).
+ *
+ * Layout: positions, velocities and accelerations are structure-of-arrays
+ * [3][n] (x row, then y row, then z row), masses and potentials are [n].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Neumaier's improved Kahan summation: s + c carries the running sum. */
+typedef struct {
+    double s, c;
+} csum;
+
+static void csum_add(csum *a, double x) {
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x))
+        a->c += (a->s - t) + x;
+    else
+        a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+static double csum_get(const csum *a) { return a->s + a->c; }
+
+/* Acceleration and potential on particle i from all j != i (the definition). */
+static void oracle_one(int64_t n, const double *pos, const double *mass, double eps,
+                       double G, int64_t i, double out[4]) {
+    const double *x = pos, *y = pos + n, *z = pos + 2 * n;
+    csum ax = {0, 0}, ay = {0, 0}, az = {0, 0}, ph = {0, 0};
+    const double eps2 = eps * eps;
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue; /* the sum excludes j = i */
+        double dx = x[j] - x[i];
+        double dy = y[j] - y[i];
+        double dz = z[j] - z[i];
+        double r2 = dx * dx + dy * dy + dz * dz + eps2;
+        if (r2 == 0.0) continue; /* eps = 0 and coincident particles: no defined force */
+        double r = sqrt(r2);
+        double r3 = r2 * r; /* (r^2 + eps^2)^(3/2) */
+        csum_add(&ax, mass[j] * dx / r3);
+        csum_add(&ay, mass[j] * dy / r3);
+        csum_add(&az, mass[j] * dz / r3);
+        csum_add(&ph, mass[j] / r);
+    }
+    out[0] = G * csum_get(&ax);
+    out[1] = G * csum_get(&ay);
+    out[2] = G * csum_get(&az);
+    out[3] = -G * csum_get(&ph);
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* acc: [3][n] (may be NULL), pot: [n] (may be NULL). */
+void oracle_forces(int64_t n, const double *pos, const double *mass, double eps, double G,
+                   double *acc, double *pot) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double o[4];
+        oracle_one(n, pos, mass, eps, G, i, o);
+        if (acc) {
+            acc[i] = o[0];
+            acc[n + i] = o[1];
+            acc[2 * n + i] = o[2];
+        }
+        if (pot) pot[i] = o[3];
+    }
+}
+
+/* The same quantity for a subset of rows: acc is [3][nrows], pot is [nrows]. */
+void oracle_forces_rows(int64_t n, const double *pos, const double *mass, double eps, double G,
+                        const int64_t *rows, int64_t nrows, double *acc, double *pot) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = 0; k < nrows; ++k) {
+        double o[4];
+        oracle_one(n, pos, mass, eps, G, rows[k], o);
+        if (acc) {
+            acc[k] = o[0];
+            acc[nrows + k] = o[1];
+            acc[2 * nrows + k] = o[2];
+        }
+        if (pot) pot[k] = o[3];
+    }
+}
+
+/* out[9] = K, W, E, Px, Py, Pz, Lx, Ly, Lz. */
+void oracle_energy(int64_t n, const double *pos, const double *vel, const double *mass,
+                   const double *pot, double *out) {
+    csum k = {0, 0}, w = {0, 0}, p[3] = {{0, 0}, {0, 0}, {0, 0}}, l[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int64_t i = 0; i < n; ++i) {
+        double x = pos[i], y = pos[n + i], zz = pos[2 * n + i];
+        double vx = vel[i], vy = vel[n + i], vz = vel[2 * n + i];
+        double m = mass[i];
+        csum_add(&k, 0.5 * m * (vx * vx + vy * vy + vz * vz));
+        csum_add(&w, 0.5 * m * pot[i]);
+        csum_add(&p[0], m * vx);
+        csum_add(&p[1], m * vy);
+        csum_add(&p[2], m * vz);
+        csum_add(&l[0], m * (y * vz - zz * vy));
+        csum_add(&l[1], m * (zz * vx - x * vz));
+        csum_add(&l[2], m * (x * vy - y * vx));
+    }
+    out[0] = csum_get(&k);
+    out[1] = csum_get(&w);
+    out[2] = out[0] + out[1];
+    for (int d = 0; d < 3; ++d) {
+        out[3 + d] = csum_get(&p[d]);
+        out[6 + d] = csum_get(&l[d]);
+    }
+}
+
+/*
+ * nsteps of KDK leapfrog, in place on pos and vel.
+ * acc/pot: on entry the acceleration/potential at the initial positions if
+ * have_acc != 0 (else they are computed first); on exit those at the final
+ * positions.  diag (may be NULL): [nsteps + 1][9], row 0 the initial state and
+ * row s the state after step s (oracle_energy layout).
+ */
+void oracle_kdk(int64_t n, double *pos, double *vel, const double *mass, double eps, double G,
+                double dt, int64_t nsteps, double *acc, double *pot, int have_acc, double *diag) {
+    if (!have_acc) oracle_forces(n, pos, mass, eps, G, acc, pot);
+    if (diag) oracle_energy(n, pos, vel, mass, pot, diag);
+    const double h = 0.5 * dt;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        for (int64_t q = 0; q < 3 * n; ++q) vel[q] += h * acc[q]; /* kick */
+        for (int64_t q = 0; q < 3 * n; ++q) pos[q] += dt * vel[q]; /* drift */
+        oracle_forces(n, pos, mass, eps, G, acc, pot);
+        for (int64_t q = 0; q < 3 * n; ++q) vel[q] += h * acc[q]; /* kick */
+        if (diag) oracle_energy(n, pos, vel, mass, pot, diag + 9 * (s + 1));
+    }
+}
