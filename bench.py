@@ -1,0 +1,433 @@
+#!/usr/bin/env python3
+"""Benchmark: pairwise interactions/s of the direct-summation force path.
+
+Workload: two Plummer spheres of 524 288 particles each (N = 1 048 576) on a
+head-on approach (centres at x = -5 and +5, relative speed 0.5), Henon units,
+eps = 1e-3, FP32-compensated pairwise arithmetic with FP64 positions and
+velocities.  One bench step is one full kick-drift-kick leapfrog step through
+``nbody_step`` (replayed CUDA graph): kick + drift, Morton reordering, tile
+packing, the force kernel with the fused closing kick, and the per-step energy
+and momentum diagnostics.  Every step evaluates N^2 pairwise interactions.
+
+Output: one JSON line on rank 0.  ``value`` is N^2 * steps * ranks / device
+time of the timed steps (each step bracketed by CUDA events on the launching
+stream, L2 flushed between steps by writing a 512 MiB buffer outside the timed
+events).  ``roofline`` reports the force kernel against the FP32-pipe bound
+(13 FP32 operations per pair on 128 FP32 lanes per SM, at the maximum SM
+clock).  ``cpu_baseline`` times the FP64 oracle on a bounded sample of rows on
+the host cores.  ``e2e`` repeats the steps through the same C ABI call with
+pinned host buffers (host<->device copies inside the timed region).
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead
+(bounded row samples per step), since the paper ships no runnable code.
+
+With torchrun (N > 1) every rank integrates its own independent copy of the
+workload (replicas; the force path has no data exchange between systems), the
+steps are bracketed by a barrier, and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("pairwise interactions/s and % of FP32/rsqrt roofline at N=1M, "
+          "vs FP64 GPU at stated error")
+UNIT = "interactions/s"
+N_EACH = 524288
+EPS = 1.0e-3
+DT = 1.0e-4
+SEED = 5
+FP32_OPS_PER_PAIR = 13      # 3 add (dx), 3 fma (r^2), 3 mul, 1 add (phi), 3 fma (a)
+FP32_LANES_PER_SM = 128
+MUFU_PER_SM = 16
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
+FORCE_SRC = os.path.join(ROOT, "paper_2509_19294_gb300", "csrc", "forces_f32c.cuh")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    from paper_2509_19294_gb300 import ic
+    return ic.two_plummer(N_EACH, seed=SEED)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle_rows(pos, mass, budget_s, seed):
+    """FP64 oracle on random rows against all j, sized to ~budget_s of CPU."""
+    import oracle
+    from paper_2509_19294_gb300 import ic
+    n = mass.shape[0]
+    rows = ic.sample_rows(n, 64, seed)
+    t0 = time.perf_counter()
+    oracle.forces_rows(pos, mass, EPS, rows)
+    t1 = time.perf_counter()
+    per_row = (t1 - t0) / len(rows)
+    k = int(max(64, min(n, budget_s / max(per_row, 1e-9))))
+    rows = ic.sample_rows(n, k, seed + 1)
+    t0 = time.perf_counter()
+    oracle.forces_rows(pos, mass, EPS, rows)
+    t1 = time.perf_counter()
+    return len(rows) * n / (t1 - t0), len(rows), t1 - t0, oracle.num_threads()
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for name, val in zip(self.NAMES, parts[4:8]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for_current_kernel():
+    """DRAM bytes per force launch from the committed ncu summary, if it was
+    taken on the kernel source as it is now (else null)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+        with open(FORCE_SRC, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if rec.get("source_sha256") == sha:
+            return rec.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+# ----------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import paper_2509_19294_gb300 as nb
+    from paper_2509_19294_gb300 import build as nbuild
+
+    rank, world, local = dist_env()
+    if rank == 0 and not nbuild.up_to_date():
+        nbuild.build()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+        pg.barrier()            # the other ranks wait for rank 0's build
+    nb.load()
+
+    pos, vel, mass = workload()
+    n = mass.shape[0]
+    pairs_per_step = float(n) * n
+    stream = torch.cuda.current_stream()
+
+    flags = nb.NBODY_FLAG_PROFILE | nb.NBODY_FLAG_AUTOTUNE
+    ctx = nb.nbody_init(n, EPS, mode=nb.NBODY_F32C, reorder_every=1, flags=flags)
+    tiles = nb.nbody_get_tiles(ctx)
+    p = torch.from_numpy(pos).cuda()
+    v = torch.from_numpy(vel).cuda()
+    m = torch.from_numpy(mass).cuda()
+    acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+    pot = torch.empty(n, dtype=torch.float64, device="cuda")
+    diag = torch.empty((1, 1, 9), dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    nb.nbody_forces(ctx, p, m, acc, pot)
+    for _ in range(args.warmup):
+        nb.nbody_step(ctx, p, v, m, acc, pot, DT, 1, diag)
+    torch.cuda.synchronize()
+    e_first = nb.nbody_energy(ctx, p, v, m, pot)[0]
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    nb.nbody_profile_read(ctx, reset=True)
+    launches0 = nb.nbody_kernel_launches(ctx)
+    visible = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    sampler = ClockSampler(visible[local] if local < len(visible) else local)
+    sampler.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                                   # L2 flush, outside the events
+        ev[k][0].record(stream)
+        nb.nbody_step(ctx, p, v, m, acc, pot, DT, 1, diag)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    wall1 = time.perf_counter()
+    clocks = sampler.stop()
+    launches = nb.nbody_kernel_launches(ctx) - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_total = float(sum(step_ms))
+    kern_ms, kern_n = nb.nbody_profile_read(ctx, reset=True)
+    e_last = nb.nbody_energy(ctx, p, v, m, pot)[0]
+    if pg:
+        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_total = float(t.item())
+
+    # accuracy of the timed configuration: sampled rows against the FP64 oracle
+    # (the state after the timed steps; rows computed one by one on the host)
+    accuracy = None
+    cpu = None
+    if rank == 0:
+        import oracle
+        from paper_2509_19294_gb300 import ic
+        ph = p.cpu().numpy()
+        mh = m.cpu().numpy()
+        nb.nbody_forces(ctx, p, m, acc, pot)
+        ah = acc.cpu().numpy()
+        poth = pot.cpu().numpy()
+        rows = ic.sample_rows(n, 512, 99)
+        ra, rp = oracle.forces_rows(ph, mh, EPS, rows)
+        ga = ah[:, rows]
+        rel = np.linalg.norm(ga - ra, axis=0) / np.linalg.norm(ra, axis=0)
+        typical = math.sqrt(float(np.mean(np.sum(ra ** 2, axis=0))))
+        accuracy = {
+            "rows": int(len(rows)),
+            "median_rel_acc_err": float(np.median(rel)),
+            "max_rel_acc_err": float(rel.max()),
+            "paper_metric_max_abs_over_rms": float(np.abs(ga - ra).max() / typical),
+            "max_rel_pot_err": float((np.abs(poth[rows] - rp) / np.abs(rp)).max()),
+            "dE_over_E_timed_steps": float(abs(e_last[2] - e_first[2]) / abs(e_first[2])),
+        }
+        if not args.no_cpu_baseline:
+            val, nrows, secs, thr = time_oracle_rows(ph, mh, args.cpu_seconds, 7)
+            cpu = {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
+                   "sample": f"{nrows} random rows x all {n} particles of the same state "
+                             f"(FP64, {secs:.1f} s on {thr} threads)"}
+
+    # plain FP64 GPU kernel on the same GPU: one evaluation of a bounded sample
+    fp64 = None
+    if rank == 0 and not args.no_fp64:
+        n64 = args.fp64_n
+        from paper_2509_19294_gb300 import ic
+        p64, _, m64 = ic.two_plummer(n64 // 2, seed=SEED)
+        with nb.nbody_init(n64, EPS, mode=nb.NBODY_F64, flags=nb.NBODY_FLAG_PROFILE) as c64:
+            pp, mm = torch.from_numpy(p64).cuda(), torch.from_numpy(m64).cuda()
+            aa = torch.empty((3, n64), dtype=torch.float64, device="cuda")
+            nb.nbody_forces(c64, pp, mm, aa)
+            nb.nbody_profile_read(c64, reset=True)
+            nb.nbody_forces(c64, pp, mm, aa)
+            ms64, _ = nb.nbody_profile_read(c64, reset=True)
+        fp64 = {"value": float(n64) * n64 / (ms64 / 1e3), "unit": UNIT,
+                "sample": f"one FP64 evaluation, same workload recipe at N={n64}",
+                "ratio_f32c_over_f64": None}
+
+    # end to end through the same C ABI call with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        ph = torch.from_numpy(pos.copy()).pin_memory()
+        vh = torch.from_numpy(vel.copy()).pin_memory()
+        mh = torch.from_numpy(mass.copy()).pin_memory()
+        ah = torch.empty((3, n), dtype=torch.float64).pin_memory()
+        poth = torch.empty(n, dtype=torch.float64).pin_memory()
+        dh = torch.empty((1, 1, 9), dtype=torch.float64).pin_memory()
+        with nb.nbody_init(n, EPS, mode=nb.NBODY_F32C, reorder_every=1,
+                           tiles=tiles) as ce:
+            nb.nbody_forces(ce, ph, mh, ah, poth)
+            nb.nbody_step(ce, ph, vh, mh, ah, poth, DT, 1, dh)
+            if pg:
+                pg.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                nb.nbody_step(ce, ph, vh, mh, ah, poth, DT, 1, dh)   # H2D, step, D2H, sync
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+        secs = t1 - t0
+        if pg:
+            t = torch.tensor([secs], dtype=torch.float64, device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            secs = float(t.item())
+        bi = 8 * (3 * n + 3 * n + n + 3 * n + n)
+        bo = 8 * (3 * n + 3 * n + 3 * n + n + 9)
+        e2e = {"value": pairs_per_step * args.steps * world / secs, "unit": UNIT,
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+
+    nb.nbody_destroy(ctx)
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            sm_max = float(json.load(f).get("sm_max_mhz", 2070.0))
+    except (OSError, ValueError):
+        sm_max = 2070.0
+    value = pairs_per_step * args.steps * world / (ms_total / 1e3)
+    kern_avg_s = kern_ms / max(kern_n, 1) / 1e3
+    achieved = pairs_per_step / kern_avg_s / 1e9
+    peak_fp32 = FP32_LANES_PER_SM * sms * sm_max * 1e6 / FP32_OPS_PER_PAIR / 1e9
+    peak_mufu = MUFU_PER_SM * sms * sm_max * 1e6 / 1e9
+    peak = min(peak_fp32, peak_mufu)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginteractions/s",
+            "frac": achieved / peak, "traffic": traffic_for_current_kernel(),
+            "kernel": "forces_f32c_kernel", "avg_launch_ms": kern_avg_s * 1e3,
+            "launches": kern_n,
+            "peak_basis": f"FP32 pipe: {FP32_LANES_PER_SM} lanes/SM x {sms} SMs x {sm_max:.0f} MHz "
+                          f"/ {FP32_OPS_PER_PAIR} FP32 ops per pair (MUFU bound "
+                          f"{peak_mufu:.0f} G/s is looser); derived, not measured"}
+    if clocks and clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / sm_max)
+    if fp64 is not None:
+        fp64["ratio_f32c_over_f64"] = value / fp64["value"]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "two Plummer spheres head-on, N=1048576 (2x524288), eps=1e-3, "
+                               "KDK dt=1e-4, Morton reorder + pack + force + kick + diagnostics "
+                               "per step",
+                   "n": n, "eps": EPS, "dt": DT, "seed": SEED,
+                   "precision": "FP32 pairwise (MUFU rsqrt), Kahan-compensated FP32 tile sums, "
+                                "FP64 positions/velocities/reduction",
+                   "tiles": {"block": tiles[0], "p": tiles[1], "tj": tiles[2], "split": tiles[3]},
+                   "l2": "flushed between steps (512 MiB write outside the timed events)",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "fp64_gpu": fp64,
+        "accuracy": accuracy,
+        "clocks": clocks,
+        "wall_s_timed": wall1 - wall0,
+    }
+    print(json.dumps(out), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2509_19294_gb300 import ic
+    oracle.build()
+    pos, vel, mass = workload()
+    n = mass.shape[0]
+    # each step: the oracle's force rows on a bounded sample (sized so that
+    # warmup + steps stay within a few minutes on the host cores)
+    per_step_s = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    val0, nrows, _, thr = time_oracle_rows(pos, mass, per_step_s, 11)
+    for w in range(args.warmup):
+        oracle.forces_rows(pos, mass, EPS, ic.sample_rows(n, nrows, 100 + w))
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.forces_rows(pos, mass, EPS, ic.sample_rows(n, nrows, 200 + k))
+    secs = time.perf_counter() - t0
+    value = nrows * n * args.steps / secs
+    sample = f"{nrows} random rows x all {n} particles per step (FP64 oracle, {thr} threads)"
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "two Plummer spheres head-on, N=1048576 (2x524288), eps=1e-3",
+                   "n": n, "eps": EPS, "seed": SEED, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--fp64-n", type=int, default=65536)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * nbody.h -- C ABI of the GB300 direct-summation gravity library (libnbody.so).
+ *
+ * The library computes, for every particle i of one system or of each
+ * independent cluster of an ensemble, the softened gravitational acceleration
+ * and potential
+ *
+ *     a_i   =  G sum_{j != i} m_j (r_j - r_i) / (|r_j - r_i|^2 + eps^2)^(3/2)
+ *     phi_i = -G sum_{j != i} m_j           / (|r_j - r_i|^2 + eps^2)^(1/2)
+ *
+ * (the force sum of Almerol et al., SC'25 workshops, Sec. 3, divided by m_i,
+ * with Plummer softening eps), and advances the system with kick-drift-kick
+ * leapfrog in FP64 (the paper keeps all integration in double precision,
+ * Sec. 3, mixed-precision paragraph).
+ *
+ * Two arithmetic modes (chosen per context):
+ *   NBODY_F64  -- every pairwise operation in IEEE double.
+ *   NBODY_F32C -- positions stay FP64; each tile of particles is re-expressed
+ *                 as FP32 offsets from its own FP64 centre, pairwise terms run
+ *                 in FP32 (hardware rsqrt), each particle's per-tile partial
+ *                 sum is folded into a Kahan-compensated FP32 accumulator, and
+ *                 the cross-CTA reduction, the final scaling by G and the
+ *                 leapfrog run in FP64.  This is the paper's mixed-precision
+ *                 split (FP32 forces, FP64 everything else, Sec. 3).
+ *
+ * Conventions for every entry point:
+ *   * Array layout: positions, velocities and accelerations are
+ *     structure-of-arrays double[3][n] (all x, then all y, then all z);
+ *     masses and potentials are double[n].  n is the context's n_total and
+ *     particle k of cluster c is row cluster_offsets[c] + k.
+ *   * Pointers may be device memory (cudaMalloc, torch CUDA tensors) or host
+ *     memory (pageable or pinned).  Host arrays are staged through device
+ *     buffers owned by the context; when any OUTPUT array is host memory the
+ *     call synchronises the stream before it returns, so the values are ready.
+ *     All pointers must be 8-byte aligned.
+ *   * Ownership: the caller owns every array it passes; the library never
+ *     frees or keeps them past the call, except that nbody_step caches a CUDA
+ *     graph keyed by the pointer values (a later call with other pointers
+ *     captures a new graph).  The context owns its scratch (packed tiles,
+ *     partial sums, permutation, work queue, graphs, staging buffers).
+ *   * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *     Work is enqueued on it; only nbody_energy and calls with host outputs
+ *     synchronise.
+ *   * Errors: every int-returning call returns NBODY_OK (0) or a negative
+ *     NBODY_E* code.  An error inside a call leaves the context in a sticky
+ *     error state: later calls return NBODY_ESTATE until nbody_destroy.
+ *     nbody_last_error_message gives a one-line description.
+ *   * A context may be used from one host thread at a time.
+ *   * Empty systems (n_total == 0) and empty clusters are valid; calls on them
+ *     do nothing and succeed.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define NBODY_OK 0
+#define NBODY_EINVAL (-1)       /* invalid argument or configuration */
+#define NBODY_ENOMEM (-2)       /* a device or host allocation failed */
+#define NBODY_ECUDA (-3)        /* a CUDA runtime call failed */
+#define NBODY_ENONFINITE (-4)   /* NBODY_FLAG_CHECK_FINITE found a NaN/Inf output */
+#define NBODY_ETIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define NBODY_ESTATE (-6)       /* the context holds an earlier error */
+#define NBODY_EUNSUPPORTED (-7) /* no kernel instantiation for the requested tiles */
+
+/* arithmetic modes */
+#define NBODY_F64 0
+#define NBODY_F32C 1
+
+/* configuration flags */
+#define NBODY_FLAG_AUTOTUNE 1     /* choose the tile shape at init by timing candidates */
+#define NBODY_FLAG_PROFILE 2      /* time every force-kernel launch with CUDA events */
+#define NBODY_FLAG_CHECK_FINITE 4 /* verify outputs are finite after each call (syncs) */
+#define NBODY_FLAG_NO_GRAPH 8     /* nbody_step launches eagerly instead of graph replay */
+
+/*
+ * Tile shape of the F32C force kernel.  block = threads per CTA, p = i-particles
+ * held in registers by each thread (one CTA owns block*p consecutive packed
+ * particles, which also form one FP64-centred tile), tj = j-particles staged in
+ * shared memory per step, split = number of CTAs that share one i-tile's j-range
+ * (their FP64 partial sums are reduced in a fixed order).  All zero = choose
+ * automatically.  nbody_tiles_supported() lists the compiled (block, p, tj).
+ */
+typedef struct nbody_tiles {
+    int32_t block;
+    int32_t p;
+    int32_t tj;
+    int32_t split;
+} nbody_tiles;
+
+typedef struct nbody_config {
+    int64_t n_total;                 /* particles over all clusters, 0 <= n_total <= 2^30 */
+    int32_t n_clusters;              /* >= 1; clusters never interact */
+    int32_t mode;                    /* NBODY_F64 or NBODY_F32C */
+    const int64_t *cluster_offsets;  /* host, n_clusters + 1 nondecreasing entries from 0 to
+                                        n_total; may be NULL when n_clusters == 1 */
+    const double *eps;               /* host, n_clusters softening lengths, each finite, >= 0 */
+    double G;                        /* gravitational constant, finite */
+    int32_t reorder_every;           /* F32C: re-sort particles along a Morton curve every k
+                                        force evaluations (0 = keep the caller's order) */
+    int32_t flags;                   /* NBODY_FLAG_* */
+    nbody_tiles tiles;               /* F32C tile shape; zeros = default or autotuned */
+} nbody_config;
+
+typedef struct nbody_ctx nbody_ctx;
+
+/*
+ * Create a context: validates cfg, allocates the scratch for n_total particles
+ * on the current CUDA device, builds the work queue and, with
+ * NBODY_FLAG_AUTOTUNE, times the candidate tile shapes (results are cached in
+ * the file named by the NBODY_TUNE_CACHE environment variable, if set).
+ * `stream` carries the set-up work; the call synchronises it before returning.
+ * On failure *out is NULL.
+ */
+int nbody_init(nbody_ctx **out, const nbody_config *cfg, void *stream);
+
+/* Release everything the context owns (NULL is a no-op).  Synchronises the device. */
+void nbody_destroy(nbody_ctx *ctx);
+
+/*
+ * Acceleration and potential of every particle (Sec. 3 force sum, softened).
+ *   pos  in : double[3][n]   mass in : double[n]
+ *   acc  out: double[3][n]   pot  out: double[n], or NULL to skip it
+ * pos/mass are only read; acc/pot must not alias them.
+ */
+int nbody_forces(nbody_ctx *ctx, const double *pos, const double *mass, double *acc, double *pot,
+                 void *stream);
+
+/*
+ * nsteps >= 0 kick-drift-kick leapfrog steps of size dt (finite, any sign):
+ *   v += dt/2 a(x);  x += dt v;  a, phi <- forces(x);  v += dt/2 a(x)
+ *   pos, vel in/out: double[3][n]     mass in: double[n]
+ *   acc, pot in/out: on entry a(x) and phi(x) at the current positions (from
+ *                    nbody_forces or an earlier step); on exit at the final ones
+ *   diag out (may be NULL): double[nsteps][n_clusters][9], after each step the
+ *                    nbody_energy values of every cluster
+ * Steps are replayed from a captured CUDA graph unless NBODY_FLAG_NO_GRAPH.
+ */
+int nbody_step(nbody_ctx *ctx, double *pos, double *vel, const double *mass, double *acc,
+               double *pot, double dt, int32_t nsteps, double *diag, void *stream);
+
+/*
+ * Per-cluster diagnostics, FP64, fixed summation order (bitwise reproducible):
+ *   out_host[c*9 + 0..8] = K, W, E, Px, Py, Pz, Lx, Ly, Lz with
+ *   K = 1/2 sum m|v|^2, W = 1/2 sum m phi, E = K + W, P = sum m v, L = sum m x cross v.
+ * out_host is host memory of n_clusters*9 doubles; the call synchronises `stream`.
+ */
+int nbody_energy(nbody_ctx *ctx, const double *pos, const double *vel, const double *mass,
+                 const double *pot, double *out_host, void *stream);
+
+/* Time the candidate tile shapes now and keep the fastest (see NBODY_FLAG_AUTOTUNE). */
+int nbody_tune(nbody_ctx *ctx, void *stream);
+
+/* The tile shape in use (F32C), or zeros in F64 mode. */
+int nbody_get_tiles(const nbody_ctx *ctx, nbody_tiles *out);
+
+/*
+ * Compiled (block, p, tj) shapes of the F32C kernel.  Writes up to `cap`
+ * entries (split = 0) and returns how many exist.
+ */
+int nbody_tiles_supported(nbody_tiles *out, int cap);
+
+/*
+ * With NBODY_FLAG_PROFILE: total device time (ms) of the force-kernel launches
+ * since the last reset and their count.  Waits for launches still in flight.
+ * reset != 0 clears the totals afterwards.
+ */
+int nbody_profile_read(nbody_ctx *ctx, double *ms_total, int64_t *launches, int reset);
+
+/* Number of kernels the library has launched on this context (eager and graph nodes). */
+int64_t nbody_kernel_launches(const nbody_ctx *ctx);
+
+/* Static description of a status code. */
+const char *nbody_strerror(int status);
+
+/* One-line description of the context's last error ("" if none). */
+const char *nbody_last_error_message(const nbody_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

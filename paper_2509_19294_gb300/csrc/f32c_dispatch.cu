@@ -1,0 +1,60 @@
+// f32c_dispatch.cu -- lookup, occupancy and launch of the compiled F32C shapes.
+#include <cuda_runtime.h>
+
+#include "f32c_shapes.h"
+#include "nbody_internal.h"
+
+namespace nbody {
+
+namespace {
+
+const F32CShape *find_shape(int block, int p, int tj, bool eps_zero) {
+    const F32CShape *tables[3] = {kShapesA, kShapesB, kShapesC};
+    const int counts[3] = {kNumShapesA, kNumShapesB, kNumShapesC};
+    for (int t = 0; t < 3; ++t)
+        for (int k = 0; k < counts[t]; ++k) {
+            const F32CShape &s = tables[t][k];
+            if (s.block == block && s.p == p && s.tj == tj && s.eps_zero == eps_zero) return &s;
+        }
+    return nullptr;
+}
+
+}  // namespace
+
+int f32c_shapes(int *block, int *p, int *tj, int cap) {
+    const F32CShape *tables[3] = {kShapesA, kShapesB, kShapesC};
+    const int counts[3] = {kNumShapesA, kNumShapesB, kNumShapesC};
+    int n = 0;
+    for (int t = 0; t < 3; ++t)
+        for (int k = 0; k < counts[t]; ++k) {
+            const F32CShape &s = tables[t][k];
+            if (s.eps_zero) continue;
+            if (n < cap) {
+                block[n] = s.block;
+                p[n] = s.p;
+                tj[n] = s.tj;
+            }
+            ++n;
+        }
+    return n;
+}
+
+int f32c_occupancy(int block, int p, int tj, bool eps_zero) {
+    const F32CShape *s = find_shape(block, p, tj, eps_zero);
+    if (!s) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, s->kernel, block, 0) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_f32c(int block, int p, int tj, bool eps_zero, int grid, const F32CParams &prm,
+                        cudaStream_t st) {
+    const F32CShape *s = find_shape(block, p, tj, eps_zero);
+    if (!s) return cudaErrorNotSupported;
+    if (grid <= 0) return cudaSuccess;
+    void *args[] = {(void *)&prm};
+    return cudaLaunchKernel(s->kernel, dim3(grid), dim3(block), args, 0, st);
+}
+
+}  // namespace nbody

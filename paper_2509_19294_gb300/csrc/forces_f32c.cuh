@@ -1,0 +1,304 @@
+// forces_f32c.cuh -- the FP32-compensated direct-summation force kernel (sm_103a).
+//
+// Computes the Sec. 3 force sum (divided by m_i, Plummer-softened) for every
+// packed i-slot of the work items it takes from a queue:
+//
+//   a_i   =  G sum_j m_j (r_j - r_i) (|r_j - r_i|^2 + eps^2)^(-3/2)
+//   phi_i = -G sum_j m_j             (|r_j - r_i|^2 + eps^2)^(-1/2)
+//
+// Design (GB300):
+//   * Persistent CTAs: each takes (cluster, i-tile, j-range) items from an
+//     atomic queue head until the queue is empty.  One i-tile = the CTA's
+//     block*p particles, which also share one FP64 centre.
+//   * Each thread holds p i-particles in registers.  j-particles stream through
+//     shared memory in tiles of tj as SoA float arrays (x, y, z, m), double
+//     buffered: the next tile's global loads are issued before the current
+//     tile is consumed.  All lanes read the same shared address (broadcast).
+//   * Paired FP32 arithmetic: two consecutive j-particles are processed by one
+//     f32x2 instruction (__fadd2_rn / __ffma2_rn / __fmul2_rn), so one issue
+//     slot drives two FP32 lanes and the per-pair issue budget leaves room for
+//     the MUFU rsqrt and the shared loads.  Per pair: 3 add (dx), 3 fma (r^2,
+//     eps^2 folded in), 1 rsqrt, 3 mul (m s, s^2, m s^3), 1 add (phi),
+//     3 fma (a) = 13 FP32 operations + 1 MUFU.
+//   * Precision: coordinates are FP32 offsets from each tile's FP64 centre.
+//     Per j-tile the FP64 difference of the two centres is rounded to FP32
+//     once and added to the i offsets, so close pairs keep their digits
+//     whatever the absolute position.  Each thread sums a tile's terms in
+//     FP32, then folds the tile sum into a Kahan-compensated FP32 accumulator;
+//     sum - compensation is converted to FP64 at the end.
+//   * Split j-ranges (small N or load balance): each split writes its FP64
+//     partials; the CTA that finishes last (atomic ticket, no waiting) adds
+//     them in split order, so the result is bitwise deterministic.
+//   * Epilogue in FP64: scale by G, remove the self term of phi that the
+//     unmasked diagonal added (exactly the FP32 value it added), scatter to the
+//     caller's row through perm, and optionally apply the closing half-kick.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nbody_internal.h"
+
+namespace nbody {
+
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+template <int BLOCK, int P, int TJ, bool EPS_ZERO>
+struct F32CKernel {
+    static constexpr int TC = BLOCK * P;
+    static constexpr int NV = TJ;  // float4 vectors per j-tile (4 arrays x TJ/4)
+    static constexpr int NLD = (NV + BLOCK - 1) / BLOCK;
+    static_assert(TJ % 8 == 0, "tj must be a multiple of 8");
+    static_assert(TC % TJ == 0, "a j-tile must not straddle two centre tiles");
+
+    struct Smem {
+        float4 j[2][4][TJ / 4];  // [buffer][x|y|z|m][TJ/4]
+        float shift[2][4];
+        int item;
+        int last;
+    };
+
+    __device__ static __forceinline__ void load_tile(const F32CParams &p, int gs, float4 (&r)[NLD]) {
+#pragma unroll
+        for (int q = 0; q < NLD; ++q) {
+            const int v = threadIdx.x + q * BLOCK;
+            if (NV % BLOCK == 0 || v < NV) {
+                const int arr = v / (TJ / 4);
+                const int off = (v % (TJ / 4)) * 4;
+                const float *base = arr == 0 ? p.px : arr == 1 ? p.py : arr == 2 ? p.pz : p.pm;
+                r[q] = __ldg(reinterpret_cast<const float4 *>(base + gs + off));
+            }
+        }
+    }
+
+    __device__ static __forceinline__ void store_tile(Smem &sm, int b, const float4 (&r)[NLD]) {
+#pragma unroll
+        for (int q = 0; q < NLD; ++q) {
+            const int v = threadIdx.x + q * BLOCK;
+            if (NV % BLOCK == 0 || v < NV) sm.j[b][v / (TJ / 4)][v % (TJ / 4)] = r[q];
+        }
+    }
+
+    __device__ static __forceinline__ void body(float2 xj, float2 yj, float2 zj, float2 mj,
+                                                const float2 e2, const float2 (&nx)[P],
+                                                const float2 (&ny)[P], const float2 (&nz)[P],
+                                                float2 (&ax)[P], float2 (&ay)[P], float2 (&az)[P],
+                                                float2 (&ph)[P]) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const float2 dx = __fadd2_rn(xj, nx[k]);
+            const float2 dy = __fadd2_rn(yj, ny[k]);
+            const float2 dz = __fadd2_rn(zj, nz[k]);
+            float2 r2 = __ffma2_rn(dx, dx, e2);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            float2 s;
+            if (EPS_ZERO) {
+                s.x = r2.x > 0.0f ? rsqrt_mufu(r2.x) : 0.0f;
+                s.y = r2.y > 0.0f ? rsqrt_mufu(r2.y) : 0.0f;
+            } else {
+                s.x = rsqrt_mufu(r2.x);
+                s.y = rsqrt_mufu(r2.y);
+            }
+            const float2 ms = __fmul2_rn(mj, s);
+            const float2 s2 = __fmul2_rn(s, s);
+            const float2 w3 = __fmul2_rn(ms, s2);
+            ph[k] = __fadd2_rn(ph[k], ms);
+            ax[k] = __ffma2_rn(w3, dx, ax[k]);
+            ay[k] = __ffma2_rn(w3, dy, ay[k]);
+            az[k] = __ffma2_rn(w3, dz, az[k]);
+        }
+    }
+
+    // FP64 epilogue for one i-slot: scale, self-term removal, scatter, kick.
+    __device__ static __forceinline__ void finalize(const F32CParams &p, const ClusterDev &cl,
+                                                    int slot, double sx, double sy, double sz,
+                                                    double sp, float mi) {
+        const int local = slot - cl.slot_begin;
+        if (local >= cl.n) return;
+        const int64_t u = p.perm[slot];
+        if (cl.eps2f > 0.0f) {
+            // the diagonal pair (dx = dy = dz = 0 exactly) added m_i * rsqrt(eps^2) to phi
+            sp -= (double)__fmul_rn(mi, rsqrt_mufu(cl.eps2f));
+        }
+        const double a0 = p.G * sx, a1 = p.G * sy, a2 = p.G * sz;
+        p.acc[u] = a0;
+        p.acc[p.n + u] = a1;
+        p.acc[2 * p.n + u] = a2;
+        if (p.pot) p.pot[u] = -p.G * sp;
+        if (p.vel) {
+            p.vel[u] += p.half_dt * a0;
+            p.vel[p.n + u] += p.half_dt * a1;
+            p.vel[2 * p.n + u] += p.half_dt * a2;
+        }
+    }
+
+    __device__ static void run(const F32CParams p) {
+        __shared__ Smem sm;
+        const float2 zero2 = make_float2(0.0f, 0.0f);
+        for (;;) {
+            if (threadIdx.x == 0) sm.item = atomicAdd(p.counters, 1);
+            __syncthreads();
+            const int item_idx = sm.item;
+            if (item_idx >= p.n_items) break;
+            const Item it = p.items[item_idx];
+            const ClusterDev cl = p.cl[it.cluster];
+            const int ibase = it.tile * TC;
+            const float2 e2 = make_float2(cl.eps2f, cl.eps2f);
+            const double cix = p.centre[4 * it.tile + 0];
+            const double ciy = p.centre[4 * it.tile + 1];
+            const double ciz = p.centre[4 * it.tile + 2];
+
+            float ox[P], oy[P], oz[P];
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int slot = ibase + threadIdx.x + k * BLOCK;
+                ox[k] = p.px[slot];
+                oy[k] = p.py[slot];
+                oz[k] = p.pz[slot];
+            }
+            float ksum[P][4], kcmp[P][4];
+#pragma unroll
+            for (int k = 0; k < P; ++k)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) ksum[k][c] = kcmp[k][c] = 0.0f;
+
+            const int ntj = it.jt1 - it.jt0;
+            float4 reg[NLD];
+            float nshift[3] = {0.0f, 0.0f, 0.0f};
+            {
+                const int gs = cl.slot_begin + it.jt0 * TJ;
+                load_tile(p, gs, reg);
+                store_tile(sm, 0, reg);
+                if (threadIdx.x == 0) {
+                    const int jc = gs / TC;
+                    sm.shift[0][0] = (float)(cix - p.centre[4 * jc + 0]);
+                    sm.shift[0][1] = (float)(ciy - p.centre[4 * jc + 1]);
+                    sm.shift[0][2] = (float)(ciz - p.centre[4 * jc + 2]);
+                }
+            }
+            __syncthreads();
+
+            for (int t = 0; t < ntj; ++t) {
+                const int b = t & 1;
+                const bool more = t + 1 < ntj;
+                const int gsn = cl.slot_begin + (it.jt0 + t + 1) * TJ;
+                if (more) load_tile(p, gsn, reg);
+                if (more && threadIdx.x == 0) {
+                    const int jc = gsn / TC;
+                    nshift[0] = (float)(cix - p.centre[4 * jc + 0]);
+                    nshift[1] = (float)(ciy - p.centre[4 * jc + 1]);
+                    nshift[2] = (float)(ciz - p.centre[4 * jc + 2]);
+                }
+                float2 nx[P], ny[P], nz[P];
+                {
+                    const float sx = sm.shift[b][0], sy = sm.shift[b][1], sz = sm.shift[b][2];
+#pragma unroll
+                    for (int k = 0; k < P; ++k) {
+                        const float qx = -__fadd_rn(ox[k], sx);
+                        const float qy = -__fadd_rn(oy[k], sy);
+                        const float qz = -__fadd_rn(oz[k], sz);
+                        nx[k] = make_float2(qx, qx);
+                        ny[k] = make_float2(qy, qy);
+                        nz[k] = make_float2(qz, qz);
+                    }
+                }
+                float2 ax[P], ay[P], az[P], ph[P];
+#pragma unroll
+                for (int k = 0; k < P; ++k) ax[k] = ay[k] = az[k] = ph[k] = zero2;
+
+                const float4 *jx = sm.j[b][0];
+                const float4 *jy = sm.j[b][1];
+                const float4 *jz = sm.j[b][2];
+                const float4 *jm = sm.j[b][3];
+#pragma unroll 2
+                for (int v = 0; v < TJ / 4; ++v) {
+                    const float4 X = jx[v], Y = jy[v], Z = jz[v], M = jm[v];
+                    body(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+                         make_float2(M.x, M.y), e2, nx, ny, nz, ax, ay, az, ph);
+                    body(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+                         make_float2(M.z, M.w), e2, nx, ny, nz, ax, ay, az, ph);
+                }
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    kahan_add(ksum[k][0], kcmp[k][0], __fadd_rn(ax[k].x, ax[k].y));
+                    kahan_add(ksum[k][1], kcmp[k][1], __fadd_rn(ay[k].x, ay[k].y));
+                    kahan_add(ksum[k][2], kcmp[k][2], __fadd_rn(az[k].x, az[k].y));
+                    kahan_add(ksum[k][3], kcmp[k][3], __fadd_rn(ph[k].x, ph[k].y));
+                }
+                if (more) {
+                    store_tile(sm, b ^ 1, reg);
+                    if (threadIdx.x == 0) {
+                        sm.shift[b ^ 1][0] = nshift[0];
+                        sm.shift[b ^ 1][1] = nshift[1];
+                        sm.shift[b ^ 1][2] = nshift[2];
+                    }
+                }
+                __syncthreads();
+            }
+
+            // compensated FP32 sums -> FP64 (sum - compensation is exact in FP64)
+            double res[P][4];
+#pragma unroll
+            for (int k = 0; k < P; ++k)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) res[k][c] = (double)ksum[k][c] - (double)kcmp[k][c];
+
+            if (it.nsplit <= 1) {
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    const int slot = ibase + threadIdx.x + k * BLOCK;
+                    finalize(p, cl, slot, res[k][0], res[k][1], res[k][2], res[k][3], p.pm[slot]);
+                }
+                continue;  // the loop head's __syncthreads orders sm.item reuse
+            }
+
+            double *mine = p.partial + (size_t)(it.pbase + it.split) * 4 * TC;
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int l = threadIdx.x + k * BLOCK;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) __stcg(mine + c * TC + l, res[k][c]);
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int prev = atomicAdd(p.counters + 1 + it.tile, 1);
+                sm.last = (prev == it.nsplit - 1);
+            }
+            __syncthreads();
+            if (!sm.last) continue;
+            __threadfence();
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int l = threadIdx.x + k * BLOCK;
+                double acc4[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int s = 0; s < it.nsplit; ++s) {
+                    const double *ps = p.partial + (size_t)(it.pbase + s) * 4 * TC;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc4[c] += __ldcg(ps + c * TC + l);
+                }
+                const int slot = ibase + l;
+                finalize(p, cl, slot, acc4[0], acc4[1], acc4[2], acc4[3], p.pm[slot]);
+            }
+        }
+    }
+};
+
+template <int BLOCK, int P, int TJ, bool EPS_ZERO>
+__global__ void __launch_bounds__(BLOCK) forces_f32c_kernel(const F32CParams p) {
+    F32CKernel<BLOCK, P, TJ, EPS_ZERO>::run(p);
+}
+
+}  // namespace nbody

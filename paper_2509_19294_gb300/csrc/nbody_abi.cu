@@ -1,0 +1,995 @@
+// nbody_abi.cu -- the C ABI of libnbody.so: contexts, work queue, staging of
+// host buffers, CUDA-graph capture of leapfrog steps, profiling and the
+// autotuner.  The arithmetic lives in the kernels; this file only plans and
+// enqueues them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "nbody.h"
+#include "nbody_internal.h"
+
+using namespace nbody;
+
+namespace {
+
+constexpr int kProfSlots = 2;
+
+struct GraphEntry {
+    const void *pos, *vel, *mass, *acc, *pot, *diag;
+    uint64_t dt_bits;
+    int reorder;
+    int slot;
+    cudaGraphExec_t exec;
+    int kernels;
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct nbody_ctx {
+    // configuration
+    int64_t n = 0;
+    int ncl = 1;
+    int mode = NBODY_F32C;
+    double G = 1.0;
+    int reorder_every = 0;
+    int flags = 0;
+    std::vector<int64_t> off;
+    std::vector<double> eps;
+    int device = 0;
+    int sms = 1;
+    std::string gpu_name;
+    bool eps_zero = false;
+    int64_t max_cluster = 0;
+
+    // F32C geometry
+    nbody_tiles tiles{0, 0, 0, 0};
+    int tc = 0;
+    int grid = 0;
+    std::vector<ClusterDev> hcl;
+    ClusterDev *dcl = nullptr;
+    int64_t n_pad = 0;
+    int n_tiles = 0;
+    int32_t *tile_cluster = nullptr;
+    Item *items = nullptr;
+    int n_items = 0;
+    int *counters = nullptr;
+    double *partial = nullptr;
+    float *px = nullptr, *py = nullptr, *pz = nullptr, *pm = nullptr;
+    double *centre = nullptr;
+    int32_t *perm = nullptr;
+
+    // F64
+    int2 *blocks64 = nullptr;
+    int n_blocks64 = 0;
+
+    // chunks (energy, bbox, keys)
+    Chunk *chunks = nullptr;
+    int n_chunks = 0;
+    int32_t *chunk_first = nullptr;
+    double *epart = nullptr;
+    double *edev = nullptr;
+    int *diag_counter = nullptr;
+    int *finite_flag = nullptr;
+
+    // reorder
+    double *bpart = nullptr, *bbox = nullptr;
+    unsigned long long *keys = nullptr;
+    uint32_t *vals = nullptr;
+    int64_t sort_n = 0;
+    int64_t evals = 0;
+
+    // staging of host arrays
+    DevBuf st_pos, st_vel, st_mass, st_acc, st_pot, st_diag;
+
+    // graphs
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphEntry> graphs;
+
+    // profiling
+    cudaEvent_t ev[kProfSlots][2] = {};
+    bool ev_pending[kProfSlots] = {};
+    int ev_next = 0;
+    double prof_ms = 0.0;
+    int64_t prof_count = 0;
+
+    int64_t launches = 0;
+    int sticky = NBODY_OK;
+    std::string msg;
+};
+
+namespace {
+
+int fail(nbody_ctx *c, int code, const std::string &what) {
+    if (c) {
+        if (c->sticky == NBODY_OK) c->sticky = code;
+        c->msg = what;
+    }
+    return code;
+}
+
+int cuda_fail(nbody_ctx *c, cudaError_t e, const char *where) {
+    cudaGetLastError();
+    return fail(c, NBODY_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define NB_CUDA(call)                                                 \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);      \
+    } while (0)
+
+template <class T>
+int dev_alloc(nbody_ctx *ctx, T **p, size_t count) {
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ctx, NBODY_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    return NBODY_OK;
+}
+
+template <class T>
+void dev_free(T **p) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+
+template <class T>
+int upload(nbody_ctx *ctx, T **p, const std::vector<T> &h) {
+    int rc = dev_alloc(ctx, p, h.size());
+    if (rc) return rc;
+    if (!h.empty()) NB_CUDA(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return NBODY_OK;
+}
+
+int64_t cluster_n(const nbody_ctx *c, int k) { return c->off[k + 1] - c->off[k]; }
+
+// ------------------------------------------------------------------ geometry
+
+// Makespan of greedy largest-first assignment of `cost` to `workers` queues,
+// the way the persistent CTAs drain the work queue.
+double lpt_makespan(std::vector<double> cost, int workers) {
+    std::sort(cost.begin(), cost.end(), std::greater<double>());
+    std::priority_queue<double, std::vector<double>, std::greater<double>> q;
+    for (int w = 0; w < workers; ++w) q.push(0.0);
+    for (double x : cost) {
+        double t = q.top();
+        q.pop();
+        q.push(t + x);
+    }
+    double m = 0.0;
+    while (!q.empty()) {
+        m = std::max(m, q.top());
+        q.pop();
+    }
+    return m;
+}
+
+struct Plan {
+    std::vector<ClusterDev> cl;
+    std::vector<int32_t> tile_cluster;
+    std::vector<Item> items;
+    int64_t n_pad = 0;
+    int n_tiles = 0;
+    int partial_slots = 0;
+};
+
+// Lay the clusters out in centre tiles of tc slots and cut every i-tile's
+// j-range into `split` pieces (fewer if the cluster has fewer j-tiles).
+// jfrac < 1 truncates every j-range (only used to shorten autotuner timings).
+Plan make_plan(const nbody_ctx *c, int tc, int tj, int split, double jfrac = 1.0) {
+    Plan pl;
+    int64_t slot = 0;
+    for (int k = 0; k < c->ncl; ++k) {
+        const int64_t nk = cluster_n(c, k);
+        ClusterDev d{};
+        d.user_begin = c->off[k];
+        d.n = (int32_t)nk;
+        d.slot_begin = (int32_t)slot;
+        d.n_jt = (int32_t)((nk + tj - 1) / tj);
+        d.eps2 = c->eps[k] * c->eps[k];
+        d.eps2f = (float)d.eps2;
+        const int64_t nit = (nk + tc - 1) / tc;
+        for (int64_t t = 0; t < nit; ++t) pl.tile_cluster.push_back(k);
+        slot += nit * tc;
+        pl.cl.push_back(d);
+    }
+    pl.n_pad = slot;
+    pl.n_tiles = (int)(slot / tc);
+    struct Costed {
+        Item it;
+        double cost;
+    };
+    std::vector<Costed> tmp;
+    int pslot = 0;
+    for (int k = 0; k < c->ncl; ++k) {
+        const ClusterDev &d = pl.cl[k];
+        if (d.n == 0) continue;
+        const int nit = (d.n + tc - 1) / tc;
+        const int sk = std::max(1, std::min(split, d.n_jt));
+        for (int t = 0; t < nit; ++t) {
+            const int tile = d.slot_begin / tc + t;
+            const int pbase = sk > 1 ? pslot : 0;
+            if (sk > 1) pslot += sk;
+            for (int s = 0; s < sk; ++s) {
+                Item it{};
+                it.tile = tile;
+                it.cluster = k;
+                it.jt0 = (int32_t)((int64_t)s * d.n_jt / sk);
+                it.jt1 = (int32_t)((int64_t)(s + 1) * d.n_jt / sk);
+                if (jfrac < 1.0) {
+                    const int len = std::max(1, (int)std::ceil((it.jt1 - it.jt0) * jfrac));
+                    it.jt1 = it.jt0 + len;
+                }
+                it.split = s;
+                it.nsplit = sk;
+                it.pbase = pbase;
+                const double cost = (double)(it.jt1 - it.jt0) * tj + 0.25 * tj + (sk > 1 ? 0.25 * tj : 0.0);
+                tmp.push_back({it, cost});
+            }
+        }
+    }
+    std::stable_sort(tmp.begin(), tmp.end(),
+                     [](const Costed &a, const Costed &b) { return a.cost > b.cost; });
+    for (auto &x : tmp) pl.items.push_back(x.it);
+    pl.partial_slots = pslot;
+    return pl;
+}
+
+// Split count that minimises the modelled makespan on `workers` CTAs.
+int choose_split(const nbody_ctx *c, int tc, int tj, int workers) {
+    int best = 1;
+    double best_t = 0.0;
+    for (int s : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
+        Plan pl = make_plan(c, tc, tj, s);
+        std::vector<double> cost;
+        cost.reserve(pl.items.size());
+        for (auto &it : pl.items)
+            cost.push_back((double)(it.jt1 - it.jt0) * tj + 0.25 * tj + (it.nsplit > 1 ? 0.25 * tj : 0.0));
+        const double t = lpt_makespan(cost, workers);
+        if (s == 1 || t < best_t * 0.995) {
+            best_t = t;
+            best = s;
+        }
+        if ((int64_t)pl.items.size() > 64LL * workers) break;
+    }
+    return best;
+}
+
+nbody_tiles default_tiles(const nbody_ctx *c) {
+    if (c->max_cluster >= 65536) return {128, 4, 256, 0};
+    if (c->max_cluster >= 8192) return {128, 2, 256, 0};
+    return {64, 2, 128, 0};
+}
+
+void free_f32c(nbody_ctx *ctx) {
+    dev_free(&ctx->dcl);
+    dev_free(&ctx->tile_cluster);
+    dev_free(&ctx->items);
+    dev_free(&ctx->counters);
+    dev_free(&ctx->partial);
+    dev_free(&ctx->px);
+    dev_free(&ctx->py);
+    dev_free(&ctx->pz);
+    dev_free(&ctx->pm);
+    dev_free(&ctx->centre);
+    dev_free(&ctx->perm);
+}
+
+void drop_graphs(nbody_ctx *ctx) {
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+}
+
+// (Re)build every F32C buffer for tile shape t.  jfrac < 1 only for timing.
+int build_f32c(nbody_ctx *ctx, nbody_tiles t, double jfrac = 1.0) {
+    const int occ = f32c_occupancy(t.block, t.p, t.tj, ctx->eps_zero);
+    if (occ <= 0)
+        return fail(ctx, NBODY_EUNSUPPORTED,
+                    "tile shape (" + std::to_string(t.block) + "," + std::to_string(t.p) + "," +
+                        std::to_string(t.tj) + ") is not compiled");
+    const int tc = t.block * t.p;
+    const int workers = occ * ctx->sms;
+    if (t.split <= 0) t.split = choose_split(ctx, tc, t.tj, workers);
+    Plan pl = make_plan(ctx, tc, t.tj, t.split, jfrac);
+    if (pl.n_pad >= (int64_t)1 << 31) return fail(ctx, NBODY_EINVAL, "padded size exceeds 2^31");
+    drop_graphs(ctx);
+    free_f32c(ctx);
+    ctx->tiles = t;
+    ctx->tc = tc;
+    ctx->hcl = pl.cl;
+    ctx->n_pad = pl.n_pad;
+    ctx->n_tiles = pl.n_tiles;
+    ctx->n_items = (int)pl.items.size();
+    ctx->grid = std::min(ctx->n_items, workers);
+    int rc;
+    if ((rc = upload(ctx, &ctx->dcl, pl.cl))) return rc;
+    if ((rc = upload(ctx, &ctx->tile_cluster, pl.tile_cluster))) return rc;
+    if ((rc = upload(ctx, &ctx->items, pl.items))) return rc;
+    if ((rc = dev_alloc(ctx, &ctx->counters, (size_t)ctx->n_tiles + 1))) return rc;
+    NB_CUDA(cudaMemset(ctx->counters, 0, ((size_t)ctx->n_tiles + 1) * sizeof(int)));
+    if ((rc = dev_alloc(ctx, &ctx->partial, (size_t)pl.partial_slots * 4 * tc))) return rc;
+    for (float **p : {&ctx->px, &ctx->py, &ctx->pz, &ctx->pm})
+        if ((rc = dev_alloc(ctx, p, (size_t)ctx->n_pad))) return rc;
+    if ((rc = dev_alloc(ctx, &ctx->centre, (size_t)ctx->n_tiles * 4))) return rc;
+    // identity permutation within each cluster, -1 on pads
+    std::vector<int32_t> perm((size_t)ctx->n_pad, -1);
+    for (const ClusterDev &d : pl.cl)
+        for (int32_t l = 0; l < d.n; ++l) perm[(size_t)d.slot_begin + l] = (int32_t)(d.user_begin + l);
+    if ((rc = upload(ctx, &ctx->perm, perm))) return rc;
+    ctx->evals = 0;  // the next evaluation re-sorts if reordering is on
+    return NBODY_OK;
+}
+
+int build_common(nbody_ctx *ctx) {
+    std::vector<Chunk> ch;
+    std::vector<int32_t> first;
+    for (int k = 0; k < ctx->ncl; ++k) {
+        first.push_back((int32_t)ch.size());
+        for (int64_t b = ctx->off[k]; b < ctx->off[k + 1]; b += kChunk)
+            ch.push_back({k, 0, b, std::min<int64_t>(b + kChunk, ctx->off[k + 1])});
+    }
+    first.push_back((int32_t)ch.size());
+    ctx->n_chunks = (int)ch.size();
+    int rc;
+    if ((rc = upload(ctx, &ctx->chunks, ch))) return rc;
+    if ((rc = upload(ctx, &ctx->chunk_first, first))) return rc;
+    if ((rc = dev_alloc(ctx, &ctx->epart, (size_t)ctx->n_chunks * 8))) return rc;
+    if ((rc = dev_alloc(ctx, &ctx->edev, (size_t)ctx->ncl * 9))) return rc;
+    if ((rc = dev_alloc(ctx, &ctx->diag_counter, 1))) return rc;
+    if ((rc = dev_alloc(ctx, &ctx->finite_flag, 1))) return rc;
+    if (ctx->mode == NBODY_F64) {
+        std::vector<int2> blocks;
+        for (int k = 0; k < ctx->ncl; ++k)
+            for (int64_t l = 0; l < cluster_n(ctx, k); l += kF64Block) blocks.push_back(make_int2(k, (int)l));
+        ctx->n_blocks64 = (int)blocks.size();
+        if ((rc = upload(ctx, &ctx->blocks64, blocks))) return rc;
+        std::vector<ClusterDev> cl;
+        for (int k = 0; k < ctx->ncl; ++k) {
+            ClusterDev d{};
+            d.user_begin = ctx->off[k];
+            d.n = (int32_t)cluster_n(ctx, k);
+            d.eps2 = ctx->eps[k] * ctx->eps[k];
+            d.eps2f = (float)d.eps2;
+            cl.push_back(d);
+        }
+        ctx->hcl = cl;
+        if ((rc = upload(ctx, &ctx->dcl, cl))) return rc;
+    }
+    if (ctx->mode == NBODY_F32C && ctx->reorder_every > 0 && ctx->n > 0) {
+        int64_t s = 1;
+        while (s < ctx->n) s <<= 1;
+        ctx->sort_n = s;
+        if ((rc = dev_alloc(ctx, &ctx->keys, (size_t)s))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->vals, (size_t)s))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->bpart, (size_t)ctx->n_chunks * 6))) return rc;
+        if ((rc = dev_alloc(ctx, &ctx->bbox, (size_t)ctx->ncl * 6))) return rc;
+    }
+    return NBODY_OK;
+}
+
+// ------------------------------------------------------------------ staging
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller array: the pointer itself, or a staging buffer
+// (filled from the host when copy_in).
+int resolve(nbody_ctx *ctx, const void *user, size_t bytes, DevBuf &st, bool copy_in,
+            cudaStream_t s, void **out, bool *staged) {
+    *staged = false;
+    if (!user || bytes == 0) {
+        *out = const_cast<void *>(user);
+        return NBODY_OK;
+    }
+    if (is_device_ptr(user)) {
+        *out = const_cast<void *>(user);
+        return NBODY_OK;
+    }
+    if (st.bytes < bytes) {
+        if (st.p) cudaFree(st.p);
+        st.p = nullptr;
+        st.bytes = 0;
+        if (cudaMalloc(&st.p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, NBODY_ENOMEM, "staging allocation failed");
+        }
+        st.bytes = bytes;
+        drop_graphs(ctx);
+    }
+    if (copy_in) NB_CUDA(cudaMemcpyAsync(st.p, user, bytes, cudaMemcpyHostToDevice, s));
+    *out = st.p;
+    *staged = true;
+    return NBODY_OK;
+}
+
+int check_ptr(nbody_ctx *ctx, const void *p, const char *name, bool required) {
+    if (!p) return required ? fail(ctx, NBODY_EINVAL, std::string(name) + " is NULL") : NBODY_OK;
+    if (((uintptr_t)p) % 8 != 0) return fail(ctx, NBODY_EINVAL, std::string(name) + " is not 8-byte aligned");
+    return NBODY_OK;
+}
+
+// ------------------------------------------------------------------ enqueue
+
+struct Arrays {
+    double *pos, *vel, *acc, *pot, *diag;
+    const double *mass;
+};
+
+int prof_drain(nbody_ctx *ctx, int slot) {
+    if (!ctx->ev_pending[slot]) return NBODY_OK;
+    NB_CUDA(cudaEventSynchronize(ctx->ev[slot][1]));
+    float ms = 0.0f;
+    NB_CUDA(cudaEventElapsedTime(&ms, ctx->ev[slot][0], ctx->ev[slot][1]));
+    ctx->prof_ms += ms;
+    ctx->prof_count += 1;
+    ctx->ev_pending[slot] = false;
+    return NBODY_OK;
+}
+
+int record(nbody_ctx *ctx, cudaEvent_t ev, cudaStream_t s, bool capturing) {
+    if (capturing) NB_CUDA(cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal));
+    else NB_CUDA(cudaEventRecord(ev, s));
+    return NBODY_OK;
+}
+
+// Force evaluation: [reorder] + pack + queue reset + force kernel (F32C), or
+// the FP64 kernel.  vel != null fuses the closing half-kick.  slot >= 0 brackets
+// the force kernel with that profiling slot's events.
+int enqueue_forces(nbody_ctx *ctx, const Arrays &a, double half_dt, bool reorder, int slot,
+                   bool capturing, cudaStream_t s, int *kernels) {
+    if (ctx->n == 0) return NBODY_OK;
+    if (ctx->mode == NBODY_F32C) {
+        if (reorder) {
+            NB_CUDA(launch_reorder(a.pos, ctx->n, ctx->chunks, ctx->n_chunks, ctx->chunk_first,
+                                   ctx->ncl, ctx->dcl, ctx->bpart, ctx->bbox, ctx->keys, ctx->vals,
+                                   ctx->sort_n, ctx->perm, s, kernels));
+        }
+        PackParams pp{a.pos, a.mass, ctx->perm, ctx->dcl, ctx->tile_cluster, ctx->tc, ctx->n,
+                      ctx->px, ctx->py, ctx->pz, ctx->pm, ctx->centre};
+        NB_CUDA(launch_pack(ctx->n_tiles, pp, s));
+        ++*kernels;
+        NB_CUDA(cudaMemsetAsync(ctx->counters, 0, ((size_t)ctx->n_tiles + 1) * sizeof(int), s));
+        F32CParams fp{};
+        fp.px = ctx->px;
+        fp.py = ctx->py;
+        fp.pz = ctx->pz;
+        fp.pm = ctx->pm;
+        fp.centre = ctx->centre;
+        fp.perm = ctx->perm;
+        fp.cl = ctx->dcl;
+        fp.items = ctx->items;
+        fp.n_items = ctx->n_items;
+        fp.tc = ctx->tc;
+        fp.counters = ctx->counters;
+        fp.partial = ctx->partial;
+        fp.acc = a.acc;
+        fp.pot = a.pot;
+        fp.vel = a.vel;
+        fp.n = ctx->n;
+        fp.G = ctx->G;
+        fp.half_dt = half_dt;
+        int rc;
+        if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
+        cudaError_t e = launch_f32c(ctx->tiles.block, ctx->tiles.p, ctx->tiles.tj, ctx->eps_zero,
+                                    ctx->grid, fp, s);
+        if (e == cudaErrorNotSupported) return fail(ctx, NBODY_EUNSUPPORTED, "tile shape not compiled");
+        NB_CUDA(e);
+        ++*kernels;
+        if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
+    } else {
+        F64Params fp{a.pos, a.mass, ctx->dcl, ctx->blocks64, a.acc, a.pot, a.vel, ctx->n, ctx->G, half_dt};
+        int rc;
+        if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
+        NB_CUDA(launch_f64(ctx->n_blocks64, fp, s));
+        ++*kernels;
+        if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
+    }
+    return NBODY_OK;
+}
+
+// One KDK step: kick + drift, forces with the closing kick fused, diagnostics.
+int enqueue_step(nbody_ctx *ctx, const Arrays &a, double dt, bool reorder, int slot, bool capturing,
+                 cudaStream_t s, int *kernels) {
+    if (ctx->n == 0) return NBODY_OK;
+    NB_CUDA(launch_kick_drift(3 * ctx->n, a.pos, a.vel, a.acc, 0.5 * dt, dt, s));
+    ++*kernels;
+    int rc = enqueue_forces(ctx, a, 0.5 * dt, reorder, slot, capturing, s, kernels);
+    if (rc) return rc;
+    if (a.diag) {
+        NB_CUDA(launch_energy(a.pos, a.vel, a.mass, a.pot, ctx->n, ctx->chunks, ctx->n_chunks,
+                              ctx->chunk_first, ctx->ncl, ctx->epart, a.diag, ctx->diag_counter, s));
+        *kernels += ctx->n_chunks > 0 ? 2 : 1;
+    }
+    return NBODY_OK;
+}
+
+bool want_reorder(const nbody_ctx *ctx) {
+    return ctx->mode == NBODY_F32C && ctx->reorder_every > 0 && ctx->evals % ctx->reorder_every == 0;
+}
+
+int next_slot(nbody_ctx *ctx) {
+    if (!(ctx->flags & NBODY_FLAG_PROFILE)) return -1;
+    const int slot = ctx->ev_next;
+    ctx->ev_next = (ctx->ev_next + 1) % kProfSlots;
+    int rc = prof_drain(ctx, slot);
+    return rc ? rc - 1000 : slot;  // callers check < -1
+}
+
+int check_finite(nbody_ctx *ctx, const double *acc, const double *pot, cudaStream_t s) {
+    if (!(ctx->flags & NBODY_FLAG_CHECK_FINITE) || ctx->n == 0) return NBODY_OK;
+    NB_CUDA(cudaMemsetAsync(ctx->finite_flag, 0, sizeof(int), s));
+    NB_CUDA(launch_check_finite(acc, 3 * ctx->n, pot, ctx->n, ctx->finite_flag, s));
+    ctx->launches += 1;
+    int h = 0;
+    NB_CUDA(cudaMemcpyAsync(&h, ctx->finite_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    if (h) return fail(ctx, NBODY_ENONFINITE, "non-finite acceleration or potential");
+    return NBODY_OK;
+}
+
+int guard(nbody_ctx *ctx) {
+    if (!ctx) return NBODY_EINVAL;
+    if (ctx->sticky != NBODY_OK) return NBODY_ESTATE;
+    return NBODY_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+
+std::string tune_key(const nbody_ctx *ctx) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|%d|%d|%d|%lld|%d|%lld", ctx->gpu_name.c_str(), ctx->sms, ctx->mode,
+             (int)ctx->eps_zero, (long long)ctx->n, ctx->ncl, (long long)ctx->max_cluster);
+    std::string k(buf);
+    for (char &ch : k)
+        if (ch == ' ') ch = '_';
+    return k;
+}
+
+bool tune_cache_lookup(const nbody_ctx *ctx, nbody_tiles *t) {
+    const char *path = getenv("NBODY_TUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    const std::string key = tune_key(ctx);
+    char kbuf[512];
+    int b, p, tj, s;
+    double ms;
+    bool found = false;
+    while (fscanf(f, "%511s %d %d %d %d %lf", kbuf, &b, &p, &tj, &s, &ms) == 6)
+        if (key == kbuf) {
+            *t = {b, p, tj, s};
+            found = true;
+        }
+    fclose(f);
+    return found;
+}
+
+void tune_cache_store(const nbody_ctx *ctx, nbody_tiles t, double ms) {
+    const char *path = getenv("NBODY_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d %.6f\n", tune_key(ctx).c_str(), t.block, t.p, t.tj, t.split, ms);
+    fclose(f);
+}
+
+// Fill the packed arrays with a synthetic uniform cube per cluster (the force
+// kernel's cost does not depend on the values, only on the shape).
+__global__ void tune_fill_kernel(float *px, float *py, float *pz, float *pm, int64_t n_pad) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_pad;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)q * 2654435761u;
+        px[q] = ((h >> 8) & 1023) / 1024.0f - 0.5f;
+        h = h * 2246822519u + 374761393u;
+        py[q] = ((h >> 8) & 1023) / 1024.0f - 0.5f;
+        h = h * 3266489917u + 668265263u;
+        pz[q] = ((h >> 8) & 1023) / 1024.0f - 0.5f;
+        pm[q] = 1.0e-3f;
+    }
+}
+
+int run_tuner(nbody_ctx *ctx, cudaStream_t s) {
+    if (ctx->mode != NBODY_F32C || ctx->n == 0) return NBODY_OK;
+    int blocks[64], ps[64], tjs[64];
+    const int ns = std::min(64, f32c_shapes(blocks, ps, tjs, 64));
+    double total_pairs = 0.0;
+    for (int k = 0; k < ctx->ncl; ++k) total_pairs += (double)cluster_n(ctx, k) * cluster_n(ctx, k);
+    // bound each timed launch to ~2e10 pairs by truncating the j-ranges
+    const double jfrac = std::min(1.0, 2.0e10 / std::max(total_pairs, 1.0));
+    double acc_scratch_bytes = (double)ctx->n * 4 * sizeof(double);
+    double *acc = nullptr;
+    NB_CUDA(cudaMalloc(&acc, (size_t)acc_scratch_bytes));
+    cudaEvent_t e0, e1;
+    NB_CUDA(cudaEventCreate(&e0));
+    NB_CUDA(cudaEventCreate(&e1));
+    nbody_tiles best{0, 0, 0, 0};
+    double best_ms = 1e30;
+    int rc = NBODY_OK;
+    for (int c = 0; c < ns && rc == NBODY_OK; ++c) {
+        nbody_tiles t{blocks[c], ps[c], tjs[c], 0};
+        if ((int64_t)t.block * t.p > 2 * std::max<int64_t>(ctx->max_cluster, 128)) continue;
+        for (int sv = 0; sv < 3 && rc == NBODY_OK; ++sv) {
+            nbody_tiles tt = t;
+            if (sv > 0) {
+                const int occ = f32c_occupancy(t.block, t.p, t.tj, ctx->eps_zero);
+                const int base = choose_split(ctx, t.block * t.p, t.tj, occ * ctx->sms);
+                tt.split = sv == 1 ? base * 2 : std::max(1, base / 2);
+                if (tt.split == base) continue;
+            }
+            if ((rc = build_f32c(ctx, tt, jfrac))) break;
+            tune_fill_kernel<<<256, 256, 0, s>>>(ctx->px, ctx->py, ctx->pz, ctx->pm, ctx->n_pad);
+            NB_CUDA(cudaMemsetAsync(ctx->centre, 0, (size_t)ctx->n_tiles * 4 * sizeof(double), s));
+            Arrays a{nullptr, nullptr, acc, acc + 3 * ctx->n, nullptr, nullptr};
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                F32CParams fp{};
+                fp.px = ctx->px; fp.py = ctx->py; fp.pz = ctx->pz; fp.pm = ctx->pm;
+                fp.centre = ctx->centre; fp.perm = ctx->perm; fp.cl = ctx->dcl;
+                fp.items = ctx->items; fp.n_items = ctx->n_items; fp.tc = ctx->tc;
+                fp.counters = ctx->counters; fp.partial = ctx->partial;
+                fp.acc = a.acc; fp.pot = a.pot; fp.vel = nullptr; fp.n = ctx->n; fp.G = 1.0;
+                NB_CUDA(cudaMemsetAsync(ctx->counters, 0, ((size_t)ctx->n_tiles + 1) * sizeof(int), s));
+                NB_CUDA(cudaEventRecord(e0, s));
+                NB_CUDA(launch_f32c(tt.block, tt.p, tt.tj, ctx->eps_zero, ctx->grid, fp, s));
+                NB_CUDA(cudaEventRecord(e1, s));
+                NB_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                NB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0) ms_best = std::min(ms_best, ms);
+                ctx->launches += 1;
+            }
+            if (ms_best < best_ms) {
+                best_ms = ms_best;
+                best = ctx->tiles;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(acc);
+    if (rc) return rc;
+    if (best.block == 0) return fail(ctx, NBODY_EUNSUPPORTED, "autotuner found no usable shape");
+    if ((rc = build_f32c(ctx, best))) return rc;
+    tune_cache_store(ctx, best, best_ms);
+    return NBODY_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+const char *nbody_strerror(int status) {
+    switch (status) {
+        case NBODY_OK: return "success";
+        case NBODY_EINVAL: return "invalid argument";
+        case NBODY_ENOMEM: return "out of memory";
+        case NBODY_ECUDA: return "CUDA runtime error";
+        case NBODY_ENONFINITE: return "non-finite result";
+        case NBODY_ETIMEOUT: return "device wait timed out";
+        case NBODY_ESTATE: return "context is in an error state";
+        case NBODY_EUNSUPPORTED: return "unsupported tile shape";
+        default: return "unknown status";
+    }
+}
+
+const char *nbody_last_error_message(const nbody_ctx *ctx) { return ctx ? ctx->msg.c_str() : ""; }
+
+int nbody_tiles_supported(nbody_tiles *out, int cap) {
+    int b[64], p[64], t[64];
+    const int n = f32c_shapes(b, p, t, 64);
+    for (int k = 0; k < n && k < cap && out; ++k) out[k] = {b[k], p[k], t[k], 0};
+    return n;
+}
+
+void nbody_destroy(nbody_ctx *ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    cudaGetLastError();
+    drop_graphs(ctx);
+    free_f32c(ctx);
+    dev_free(&ctx->blocks64);
+    dev_free(&ctx->chunks);
+    dev_free(&ctx->chunk_first);
+    dev_free(&ctx->epart);
+    dev_free(&ctx->edev);
+    dev_free(&ctx->diag_counter);
+    dev_free(&ctx->finite_flag);
+    dev_free(&ctx->bpart);
+    dev_free(&ctx->bbox);
+    dev_free(&ctx->keys);
+    dev_free(&ctx->vals);
+    for (DevBuf *b : {&ctx->st_pos, &ctx->st_vel, &ctx->st_mass, &ctx->st_acc, &ctx->st_pot, &ctx->st_diag})
+        if (b->p) cudaFree(b->p);
+    for (int s = 0; s < kProfSlots; ++s)
+        for (int k = 0; k < 2; ++k)
+            if (ctx->ev[s][k]) cudaEventDestroy(ctx->ev[s][k]);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    delete ctx;
+}
+
+int nbody_init(nbody_ctx **out, const nbody_config *cfg, void *stream) {
+    if (!out) return NBODY_EINVAL;
+    *out = nullptr;
+    if (!cfg) return NBODY_EINVAL;
+    if (cfg->n_total < 0 || cfg->n_total > ((int64_t)1 << 30)) return NBODY_EINVAL;
+    if (cfg->n_clusters < 1 || cfg->n_clusters > (1 << 24)) return NBODY_EINVAL;
+    if (cfg->mode != NBODY_F64 && cfg->mode != NBODY_F32C) return NBODY_EINVAL;
+    if (!cfg->eps || !std::isfinite(cfg->G) || cfg->reorder_every < 0) return NBODY_EINVAL;
+    if (cfg->n_clusters > 1 && !cfg->cluster_offsets) return NBODY_EINVAL;
+    nbody_ctx *ctx = new nbody_ctx();
+    ctx->n = cfg->n_total;
+    ctx->ncl = cfg->n_clusters;
+    ctx->mode = cfg->mode;
+    ctx->G = cfg->G;
+    ctx->reorder_every = cfg->reorder_every;
+    ctx->flags = cfg->flags;
+    ctx->off.assign(cfg->n_clusters + 1, 0);
+    if (cfg->cluster_offsets) {
+        for (int k = 0; k <= cfg->n_clusters; ++k) ctx->off[k] = cfg->cluster_offsets[k];
+    } else {
+        ctx->off[1] = cfg->n_total;
+    }
+    bool ok = ctx->off[0] == 0 && ctx->off[ctx->ncl] == ctx->n;
+    for (int k = 0; k < ctx->ncl && ok; ++k) ok = ctx->off[k + 1] >= ctx->off[k];
+    ctx->eps.assign(cfg->eps, cfg->eps + cfg->n_clusters);
+    for (double e : ctx->eps) ok = ok && std::isfinite(e) && e >= 0.0;
+    if (!ok) {
+        delete ctx;
+        return NBODY_EINVAL;
+    }
+    for (int k = 0; k < ctx->ncl; ++k) {
+        ctx->max_cluster = std::max(ctx->max_cluster, cluster_n(ctx, k));
+        if ((float)(ctx->eps[k] * ctx->eps[k]) == 0.0f) ctx->eps_zero = true;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = NBODY_OK;
+    do {
+        cudaDeviceProp prop;
+        cudaError_t e;
+        if ((e = cudaGetDevice(&ctx->device)) != cudaSuccess ||
+            (e = cudaGetDeviceProperties(&prop, ctx->device)) != cudaSuccess) {
+            rc = cuda_fail(ctx, e, "device query");
+            break;
+        }
+        ctx->sms = prop.multiProcessorCount;
+        ctx->gpu_name = prop.name;
+        if ((e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+            rc = cuda_fail(ctx, e, "stream create");
+            break;
+        }
+        for (int sl = 0; sl < kProfSlots && rc == NBODY_OK; ++sl)
+            for (int k = 0; k < 2; ++k)
+                if ((e = cudaEventCreate(&ctx->ev[sl][k])) != cudaSuccess) rc = cuda_fail(ctx, e, "event create");
+        if (rc) break;
+        if ((rc = build_common(ctx))) break;
+        if (ctx->mode == NBODY_F32C) {
+            nbody_tiles t = cfg->tiles;
+            const bool forced = t.block != 0 || t.p != 0 || t.tj != 0;
+            if (!forced) {
+                nbody_tiles cached;
+                if (tune_cache_lookup(ctx, &cached)) t = cached;
+                else if (cfg->flags & NBODY_FLAG_AUTOTUNE) t = {0, 0, 0, -1};
+                else t = default_tiles(ctx), t.split = cfg->tiles.split;
+            }
+            if (t.split == -1) {
+                if ((rc = build_f32c(ctx, default_tiles(ctx)))) break;
+                if ((rc = run_tuner(ctx, s))) break;
+            } else if ((rc = build_f32c(ctx, t))) {
+                break;
+            }
+        }
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_fail(ctx, e, "init sync");
+    } while (0);
+    if (rc != NBODY_OK) {
+        nbody_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return NBODY_OK;
+}
+
+int nbody_tune(nbody_ctx *ctx, void *stream) {
+    int rc = guard(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = run_tuner(ctx, s))) return rc;
+    NB_CUDA(cudaStreamSynchronize(s));
+    return NBODY_OK;
+}
+
+int nbody_get_tiles(const nbody_ctx *ctx, nbody_tiles *out) {
+    if (!ctx || !out) return NBODY_EINVAL;
+    *out = ctx->mode == NBODY_F32C ? ctx->tiles : nbody_tiles{0, 0, 0, 0};
+    return NBODY_OK;
+}
+
+int64_t nbody_kernel_launches(const nbody_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int nbody_profile_read(nbody_ctx *ctx, double *ms_total, int64_t *launches, int reset) {
+    if (!ctx) return NBODY_EINVAL;
+    for (int sl = 0; sl < kProfSlots; ++sl) {
+        int rc = prof_drain(ctx, sl);
+        if (rc) return rc;
+    }
+    if (ms_total) *ms_total = ctx->prof_ms;
+    if (launches) *launches = ctx->prof_count;
+    if (reset) {
+        ctx->prof_ms = 0.0;
+        ctx->prof_count = 0;
+    }
+    return NBODY_OK;
+}
+
+int nbody_forces(nbody_ctx *ctx, const double *pos, const double *mass, double *acc, double *pot,
+                 void *stream) {
+    int rc = guard(ctx);
+    if (rc) return rc;
+    if (ctx->n == 0) return NBODY_OK;
+    if ((rc = check_ptr(ctx, pos, "pos", true)) || (rc = check_ptr(ctx, mass, "mass", true)) ||
+        (rc = check_ptr(ctx, acc, "acc", true)) || (rc = check_ptr(ctx, pot, "pot", false)))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n3b = 3 * ctx->n * sizeof(double), nb = ctx->n * sizeof(double);
+    void *dpos, *dmass, *dacc, *dpot;
+    bool spos, smass, sacc, spot;
+    if ((rc = resolve(ctx, pos, n3b, ctx->st_pos, true, s, &dpos, &spos)) ||
+        (rc = resolve(ctx, mass, nb, ctx->st_mass, true, s, &dmass, &smass)) ||
+        (rc = resolve(ctx, acc, n3b, ctx->st_acc, false, s, &dacc, &sacc)) ||
+        (rc = resolve(ctx, pot, nb, ctx->st_pot, false, s, &dpot, &spot)))
+        return rc;
+    Arrays a{(double *)dpos, nullptr, (double *)dacc, (double *)dpot, nullptr, (const double *)dmass};
+    const int slot = next_slot(ctx);
+    if (slot < -1) return ctx->sticky;
+    int k = 0;
+    rc = enqueue_forces(ctx, a, 0.0, want_reorder(ctx), slot, false, s, &k);
+    ctx->launches += k;
+    if (rc) return rc;
+    if (slot >= 0) ctx->ev_pending[slot] = true;
+    ctx->evals += 1;
+    if (sacc) NB_CUDA(cudaMemcpyAsync(acc, dacc, n3b, cudaMemcpyDeviceToHost, s));
+    if (spot) NB_CUDA(cudaMemcpyAsync(pot, dpot, nb, cudaMemcpyDeviceToHost, s));
+    if (sacc || spot) NB_CUDA(cudaStreamSynchronize(s));
+    return check_finite(ctx, (const double *)dacc, (const double *)dpot, s);
+}
+
+int nbody_step(nbody_ctx *ctx, double *pos, double *vel, const double *mass, double *acc,
+               double *pot, double dt, int32_t nsteps, double *diag, void *stream) {
+    int rc = guard(ctx);
+    if (rc) return rc;
+    if (!std::isfinite(dt)) return fail(ctx, NBODY_EINVAL, "dt is not finite");
+    if (nsteps < 0) return fail(ctx, NBODY_EINVAL, "nsteps < 0");
+    if (ctx->n == 0 || nsteps == 0) return NBODY_OK;
+    if ((rc = check_ptr(ctx, pos, "pos", true)) || (rc = check_ptr(ctx, vel, "vel", true)) ||
+        (rc = check_ptr(ctx, mass, "mass", true)) || (rc = check_ptr(ctx, acc, "acc", true)) ||
+        (rc = check_ptr(ctx, pot, "pot", false)) || (rc = check_ptr(ctx, diag, "diag", false)))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n3b = 3 * ctx->n * sizeof(double), nb = ctx->n * sizeof(double);
+    const size_t db = (size_t)nsteps * ctx->ncl * 9 * sizeof(double);
+    void *dpos, *dvel, *dmass, *dacc, *dpot, *ddiag;
+    bool spos, svel, smass, sacc, spot, sdiag;
+    if ((rc = resolve(ctx, pos, n3b, ctx->st_pos, true, s, &dpos, &spos)) ||
+        (rc = resolve(ctx, vel, n3b, ctx->st_vel, true, s, &dvel, &svel)) ||
+        (rc = resolve(ctx, mass, nb, ctx->st_mass, true, s, &dmass, &smass)) ||
+        (rc = resolve(ctx, acc, n3b, ctx->st_acc, true, s, &dacc, &sacc)) ||
+        (rc = resolve(ctx, pot, nb, ctx->st_pot, true, s, &dpot, &spot)) ||
+        (rc = resolve(ctx, diag, db, ctx->st_diag, false, s, &ddiag, &sdiag)))
+        return rc;
+    Arrays a{(double *)dpos, (double *)dvel, (double *)dacc, (double *)dpot, (double *)ddiag,
+             (const double *)dmass};
+    if (a.diag) NB_CUDA(cudaMemsetAsync(ctx->diag_counter, 0, sizeof(int), s));
+    const bool use_graph = !(ctx->flags & NBODY_FLAG_NO_GRAPH);
+    uint64_t dt_bits;
+    memcpy(&dt_bits, &dt, sizeof dt);
+    for (int32_t step = 0; step < nsteps; ++step) {
+        const bool reorder = want_reorder(ctx);
+        const int slot = next_slot(ctx);
+        if (slot < -1) return ctx->sticky;
+        if (!use_graph) {
+            int k = 0;
+            rc = enqueue_step(ctx, a, dt, reorder, slot, false, s, &k);
+            ctx->launches += k;
+            if (rc) return rc;
+        } else {
+            GraphEntry *g = nullptr;
+            for (auto &e : ctx->graphs)
+                if (e.pos == a.pos && e.vel == a.vel && e.mass == a.mass && e.acc == a.acc &&
+                    e.pot == a.pot && e.diag == a.diag && e.dt_bits == dt_bits &&
+                    e.reorder == (int)reorder && e.slot == slot)
+                    g = &e;
+            if (!g) {
+                if (ctx->graphs.size() >= 16) drop_graphs(ctx);
+                GraphEntry ge{a.pos, a.vel, a.mass, a.acc, a.pot, a.diag, dt_bits, (int)reorder, slot, nullptr, 0};
+                NB_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+                int k = 0;
+                rc = enqueue_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k);
+                cudaGraph_t graph = nullptr;
+                cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+                if (rc) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return rc;
+                }
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+                e = cudaGraphInstantiate(&ge.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+                ge.kernels = k;
+                ctx->graphs.push_back(ge);
+                g = &ctx->graphs.back();
+            }
+            NB_CUDA(cudaGraphLaunch(g->exec, s));
+            ctx->launches += g->kernels;
+        }
+        if (slot >= 0) ctx->ev_pending[slot] = true;
+        ctx->evals += 1;
+    }
+    if (spos) NB_CUDA(cudaMemcpyAsync(pos, dpos, n3b, cudaMemcpyDeviceToHost, s));
+    if (svel) NB_CUDA(cudaMemcpyAsync(vel, dvel, n3b, cudaMemcpyDeviceToHost, s));
+    if (sacc) NB_CUDA(cudaMemcpyAsync(acc, dacc, n3b, cudaMemcpyDeviceToHost, s));
+    if (spot) NB_CUDA(cudaMemcpyAsync(pot, dpot, nb, cudaMemcpyDeviceToHost, s));
+    if (sdiag) NB_CUDA(cudaMemcpyAsync(diag, ddiag, db, cudaMemcpyDeviceToHost, s));
+    if (spos || svel || sacc || spot || sdiag) NB_CUDA(cudaStreamSynchronize(s));
+    return check_finite(ctx, (const double *)dacc, (const double *)dpot, s);
+}
+
+int nbody_energy(nbody_ctx *ctx, const double *pos, const double *vel, const double *mass,
+                 const double *pot, double *out_host, void *stream) {
+    int rc = guard(ctx);
+    if (rc) return rc;
+    if ((rc = check_ptr(ctx, out_host, "out_host", true))) return rc;
+    if (ctx->n == 0) {
+        for (int k = 0; k < 9 * ctx->ncl; ++k) out_host[k] = 0.0;
+        return NBODY_OK;
+    }
+    if ((rc = check_ptr(ctx, pos, "pos", true)) || (rc = check_ptr(ctx, vel, "vel", true)) ||
+        (rc = check_ptr(ctx, mass, "mass", true)) || (rc = check_ptr(ctx, pot, "pot", false)))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n3b = 3 * ctx->n * sizeof(double), nb = ctx->n * sizeof(double);
+    void *dpos, *dvel, *dmass, *dpot;
+    bool a1, a2, a3, a4;
+    if ((rc = resolve(ctx, pos, n3b, ctx->st_pos, true, s, &dpos, &a1)) ||
+        (rc = resolve(ctx, vel, n3b, ctx->st_vel, true, s, &dvel, &a2)) ||
+        (rc = resolve(ctx, mass, nb, ctx->st_mass, true, s, &dmass, &a3)) ||
+        (rc = resolve(ctx, pot, nb, ctx->st_pot, true, s, &dpot, &a4)))
+        return rc;
+    NB_CUDA(launch_energy((const double *)dpos, (const double *)dvel, (const double *)dmass,
+                          (const double *)dpot, ctx->n, ctx->chunks, ctx->n_chunks, ctx->chunk_first,
+                          ctx->ncl, ctx->epart, ctx->edev, nullptr, s));
+    ctx->launches += ctx->n_chunks > 0 ? 2 : 1;
+    NB_CUDA(cudaMemcpyAsync(out_host, ctx->edev, (size_t)ctx->ncl * 9 * sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    return NBODY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// nbody_internal.h -- shared declarations of the CUDA side of libnbody.so.
+//
+// Data layout in device memory (F32C mode):
+//   * Particles are regrouped into "centre tiles" of Tc = block * p packed slots.
+//     Every cluster starts on a tile boundary and is padded up to a multiple of
+//     Tc; pad slots carry mass 0 and a far offset so they add exactly nothing.
+//   * px/py/pz/pm: float[n_pad] SoA, the FP32 offset of each particle from its
+//     tile's FP64 centre, and its mass rounded to FP32.
+//   * centre: double[n_tiles][4] (x, y, z, unused).
+//   * perm: int32[n_pad], the caller's row of each packed slot (-1 for pads).
+//     Identity within each cluster unless Morton reordering is on.
+//   * items: the work queue of the force kernel, one entry per
+//     (cluster, i-tile, j-range), largest cost first.
+//   * partial: double[slots][4][Tc], FP64 partial sums of the split i-tiles.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nbody {
+
+constexpr float kPadOffset = 1.0e18f;  // offset of pad slots from their tile centre
+
+struct ClusterDev {
+    int64_t user_begin;  // first caller row of the cluster
+    int32_t n;           // real particles
+    int32_t slot_begin;  // first packed slot (multiple of Tc)
+    int32_t n_jt;        // j-tiles of size tj covering the real particles
+    float eps2f;         // eps^2 rounded to FP32
+    double eps2;         // eps^2 in FP64
+};
+
+struct Item {
+    int32_t tile;     // global i-tile (centre tile) index
+    int32_t cluster;  // owning cluster
+    int32_t jt0, jt1; // j-tile range [jt0, jt1), local to the cluster
+    int32_t split;    // index of this j-range among the tile's splits
+    int32_t nsplit;   // number of splits of this tile (1 = no partials)
+    int32_t pbase;    // first partial slot of the tile (when nsplit > 1)
+    int32_t pad;
+};
+
+// Parameters of the FP32-compensated force kernel (passed by value).
+struct F32CParams {
+    const float *px, *py, *pz, *pm;
+    const double *centre;
+    const int32_t *perm;
+    const ClusterDev *cl;
+    const Item *items;
+    int32_t n_items;
+    int32_t tc;        // centre-tile size (block * p)
+    int *counters;     // [0] queue head, [1 + tile] split tickets
+    double *partial;   // [slots][4][tc]
+    double *acc;       // [3][n] caller rows
+    double *pot;       // [n] or null
+    double *vel;       // [3][n] or null: fused closing half-kick v += half_dt * a
+    int64_t n;
+    double G;
+    double half_dt;
+};
+
+// Parameters of the plain FP64 kernel.
+struct F64Params {
+    const double *pos;      // [3][n]
+    const double *mass;     // [n]
+    const ClusterDev *cl;
+    const int2 *blocks;     // per CTA: (cluster, first local i)
+    double *acc, *pot, *vel;
+    int64_t n;
+    double G;
+    double half_dt;
+};
+
+struct PackParams {
+    const double *pos;  // [3][n]
+    const double *mass;
+    const int32_t *perm;
+    const ClusterDev *cl;
+    const int32_t *tile_cluster;  // [n_tiles]
+    int32_t tc;
+    int64_t n;
+    float *px, *py, *pz, *pm;
+    double *centre;
+};
+
+// A run of at most kChunk consecutive rows inside one cluster (energy, bbox, keys).
+constexpr int kChunk = 2048;
+struct Chunk {
+    int32_t cluster;
+    int32_t pad;
+    int64_t begin, end;  // caller rows [begin, end)
+};
+
+// ---- kernel launchers (all enqueue on `s`, return cudaGetLastError()) ----
+
+// The F32C force kernel for tile shape (block, p, tj); eps_zero selects the
+// variant that gives coincident pairs zero force (needed when some eps == 0).
+// Returns cudaErrorNotSupported if the shape is not compiled.  `grid` CTAs run
+// the persistent work loop.
+cudaError_t launch_f32c(int block, int p, int tj, bool eps_zero, int grid, const F32CParams &prm,
+                        cudaStream_t s);
+// Maximum resident CTAs per SM of the given shape (0 if not compiled).
+int f32c_occupancy(int block, int p, int tj, bool eps_zero);
+// Compiled shapes: fills up to cap triples (block, p, tj), returns the count.
+int f32c_shapes(int *block, int *p, int *tj, int cap);
+
+cudaError_t launch_f64(int grid, const F64Params &prm, cudaStream_t s);
+constexpr int kF64Block = 128;
+
+cudaError_t launch_pack(int n_tiles, const PackParams &prm, cudaStream_t s);
+
+cudaError_t launch_kick_drift(int64_t n3, double *pos, double *vel, const double *acc,
+                              double half_dt, double dt, cudaStream_t s);
+
+// Two-stage deterministic per-cluster reduction of K, W, P, L.
+// part: double[n_chunks][8]; out: double[ncl][9] at out_base + (*counter) * ncl * 9
+// when counter != null (the counter is then incremented), else at out_base.
+cudaError_t launch_energy(const double *pos, const double *vel, const double *mass,
+                          const double *pot, int64_t n, const Chunk *chunks, int n_chunks,
+                          const int32_t *chunk_first, int ncl, double *part, double *out_base,
+                          int *counter, cudaStream_t s);
+
+// Morton reordering: fills perm[slot] for every real slot.
+// keys/vals: scratch of sort_n (power of two >= n) entries; part: double[n_chunks][6];
+// bbox: double[ncl][6].
+cudaError_t launch_reorder(const double *pos, int64_t n, const Chunk *chunks, int n_chunks,
+                           const int32_t *chunk_first, int ncl, const ClusterDev *cl,
+                           double *part, double *bbox, unsigned long long *keys, uint32_t *vals,
+                           int64_t sort_n, int32_t *perm, cudaStream_t s, int *launches);
+
+// Sets *flag = 1 if any of the n3 + n values is not finite.
+cudaError_t launch_check_finite(const double *acc, int64_t n3, const double *pot, int64_t n,
+                                int *flag, cudaStream_t s);
+
+}  // namespace nbody
