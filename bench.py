@@ -64,9 +64,9 @@ def dist_env():
     return rank, world, local
 
 
-def workload():
+def workload(n_each=N_EACH):
     from paper_2509_19294_gb300 import ic
-    return ic.two_plummer(N_EACH, seed=SEED)
+    return ic.two_plummer(n_each, seed=SEED)
 
 
 def host_cores():
@@ -183,13 +183,16 @@ def run_ours(args):
         pg.barrier()            # the other ranks wait for rank 0's build
     nb.load()
 
-    pos, vel, mass = workload()
+    pos, vel, mass = workload(args.n_each)
     n = mass.shape[0]
     pairs_per_step = float(n) * n
     stream = torch.cuda.current_stream()
 
-    flags = nb.NBODY_FLAG_PROFILE | nb.NBODY_FLAG_AUTOTUNE
-    ctx = nb.nbody_init(n, EPS, mode=nb.NBODY_F32C, reorder_every=1, flags=flags)
+    flags = nb.NBODY_FLAG_PROFILE
+    forced = tuple(int(x) for x in args.tiles.split(",")) if args.tiles else None
+    if forced is None:
+        flags |= nb.NBODY_FLAG_AUTOTUNE
+    ctx = nb.nbody_init(n, EPS, mode=nb.NBODY_F32C, reorder_every=1, flags=flags, tiles=forced)
     tiles = nb.nbody_get_tiles(ctx)
     p = torch.from_numpy(pos).cuda()
     v = torch.from_numpy(vel).cuda()
@@ -349,13 +352,14 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "two Plummer spheres head-on, N=1048576 (2x524288), eps=1e-3, "
+        "config": {"workload": f"two Plummer spheres head-on, N={n} (2x{n // 2}), eps=1e-3, "
                                "KDK dt=1e-4, Morton reorder + pack + force + kick + diagnostics "
                                "per step",
                    "n": n, "eps": EPS, "dt": DT, "seed": SEED,
                    "precision": "FP32 pairwise (MUFU rsqrt), Kahan-compensated FP32 tile sums, "
                                 "FP64 positions/velocities/reduction",
-                   "tiles": {"block": tiles[0], "p": tiles[1], "tj": tiles[2], "split": tiles[3]},
+                   "tiles": {"block": tiles[0], "p": tiles[1], "tj": tiles[2], "split": tiles[3],
+                             "ctas_per_sm": tiles[4]},
                    "l2": "flushed between steps (512 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": int(launches),
@@ -420,6 +424,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-each", type=int, default=N_EACH,
+                    help="particles per sphere (default 524288: the N=1M workload)")
+    ap.add_argument("--tiles", default=None,
+                    help="force the tile shape block,p,tj,split instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

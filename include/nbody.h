@@ -16,7 +16,8 @@
  * Two arithmetic modes (chosen per context):
  *   NBODY_F64  -- every pairwise operation in IEEE double.
  *   NBODY_F32C -- positions stay FP64; each tile of particles is re-expressed
- *                 as FP32 offsets from its own FP64 centre, pairwise terms run
+ *                 as FP32 offsets from its own centre (the FP64 mean of its
+ *                 positions, kept as a float pair), pairwise terms run
  *                 in FP32 (hardware rsqrt), each particle's per-tile partial
  *                 sum is folded into a Kahan-compensated FP32 accumulator, and
  *                 the cross-CTA reduction, the final scaling by G and the
@@ -82,16 +83,20 @@ extern "C" {
 /*
  * Tile shape of the F32C force kernel.  block = threads per CTA, p = i-particles
  * held in registers by each thread (one CTA owns block*p consecutive packed
- * particles, which also form one FP64-centred tile), tj = j-particles staged in
- * shared memory per step, split = number of CTAs that share one i-tile's j-range
- * (their FP64 partial sums are reduced in a fixed order).  All zero = choose
- * automatically.  nbody_tiles_supported() lists the compiled (block, p, tj).
+ * particles, which also form one tile with its own centre), tj = j-particles
+ * staged in shared memory per step, split = number of CTAs that share one
+ * i-tile's j-range (their FP64 partial sums are reduced in a fixed order),
+ * ctas_per_sm = the resident-CTA target the kernel variant was compiled for
+ * (it caps registers per thread).  All zero = choose automatically; zero in
+ * split or ctas_per_sm alone = choose that field.  nbody_tiles_supported()
+ * lists the compiled (block, p, tj, ctas_per_sm).
  */
 typedef struct nbody_tiles {
     int32_t block;
     int32_t p;
     int32_t tj;
     int32_t split;
+    int32_t ctas_per_sm;
 } nbody_tiles;
 
 typedef struct nbody_config {
@@ -161,8 +166,8 @@ int nbody_tune(nbody_ctx *ctx, void *stream);
 int nbody_get_tiles(const nbody_ctx *ctx, nbody_tiles *out);
 
 /*
- * Compiled (block, p, tj) shapes of the F32C kernel.  Writes up to `cap`
- * entries (split = 0) and returns how many exist.
+ * Compiled (block, p, tj, ctas_per_sm) shapes of the F32C kernel.  Writes up to
+ * `cap` entries (split = 0) and returns how many exist.
  */
 int nbody_tiles_supported(nbody_tiles *out, int cap);
 

@@ -47,7 +47,7 @@ EXPORTED = ("nbody_init", "nbody_destroy", "nbody_forces", "nbody_step", "nbody_
 
 class NBodyTiles(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("p", ctypes.c_int32), ("tj", ctypes.c_int32),
-                ("split", ctypes.c_int32)]
+                ("split", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 class NBodyConfig(ctypes.Structure):
@@ -203,7 +203,7 @@ def nbody_init(n_total: int, eps, mode: int = NBODY_F32C, G: float = 1.0, cluste
     cfg.reorder_every = int(reorder_every)
     cfg.flags = int(flags)
     if tiles is not None:
-        t = tuple(tiles) + (0,) * (4 - len(tiles))
+        t = tuple(tiles) + (0,) * (5 - len(tiles))
         cfg.tiles = NBodyTiles(*[int(x) for x in t])
     h = ctypes.c_void_p()
     rc = lib.nbody_init(ctypes.byref(h), ctypes.byref(cfg), _stream(stream))
@@ -257,17 +257,19 @@ def nbody_tune(ctx: Context, stream=None) -> None:
 
 
 def nbody_get_tiles(ctx: Context):
+    """(block, p, tj, split, ctas_per_sm) of the F32C kernel in use."""
     t = NBodyTiles()
     _check(ctx, load().nbody_get_tiles(ctx.handle, ctypes.byref(t)), "nbody_get_tiles")
-    return (t.block, t.p, t.tj, t.split)
+    return (t.block, t.p, t.tj, t.split, t.ctas_per_sm)
 
 
 def nbody_tiles_supported():
+    """Compiled (block, p, tj, ctas_per_sm) shapes."""
     lib = load()
     n = lib.nbody_tiles_supported(None, 0)
     arr = (NBodyTiles * n)()
     lib.nbody_tiles_supported(arr, n)
-    return [(t.block, t.p, t.tj) for t in arr]
+    return [(t.block, t.p, t.tj, t.ctas_per_sm) for t in arr]
 
 
 def nbody_profile_read(ctx: Context, reset: bool = False):

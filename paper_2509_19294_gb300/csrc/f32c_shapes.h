@@ -4,7 +4,7 @@
 namespace nbody {
 
 struct F32CShape {
-    int block, p, tj;
+    int block, p, tj, minb;
     bool eps_zero;
     const void *kernel;  // __global__ void(F32CParams)
 };
@@ -15,5 +15,7 @@ extern const F32CShape kShapesB[];
 extern const int kNumShapesB;
 extern const F32CShape kShapesC[];
 extern const int kNumShapesC;
+extern const F32CShape kShapesD[];
+extern const int kNumShapesD;
 
 }  // namespace nbody

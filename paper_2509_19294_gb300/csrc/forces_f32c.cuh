@@ -9,7 +9,7 @@
 // Design (GB300):
 //   * Persistent CTAs: each takes (cluster, i-tile, j-range) items from an
 //     atomic queue head until the queue is empty.  One i-tile = the CTA's
-//     block*p particles, which also share one FP64 centre.
+//     block*p particles, which also share one centre.
 //   * Each thread holds p i-particles in registers.  j-particles stream through
 //     shared memory in tiles of tj as SoA float arrays (x, y, z, m), double
 //     buffered: the next tile's global loads are issued before the current
@@ -20,10 +20,12 @@
 //     the MUFU rsqrt and the shared loads.  Per pair: 3 add (dx), 3 fma (r^2,
 //     eps^2 folded in), 1 rsqrt, 3 mul (m s, s^2, m s^3), 1 add (phi),
 //     3 fma (a) = 13 FP32 operations + 1 MUFU.
-//   * Precision: coordinates are FP32 offsets from each tile's FP64 centre.
-//     Per j-tile the FP64 difference of the two centres is rounded to FP32
-//     once and added to the i offsets, so close pairs keep their digits
-//     whatever the absolute position.  Each thread sums a tile's terms in
+//   * Precision: coordinates are FP32 offsets from each tile's centre, which
+//     is held as an unevaluated float pair hi + lo (48 significant bits).  Per
+//     j-tile the centre difference (hi_I - hi_J) + (lo_I - lo_J) is rounded to
+//     FP32 once (exactly 0 on the diagonal tile) and added to the i offsets, so
+//     close pairs keep their digits whatever the absolute position, and the
+//     tile loop runs no FP64 instruction.  Each thread sums a tile's terms in
 //     FP32, then folds the tile sum into a Kahan-compensated FP32 accumulator;
 //     sum - compensation is converted to FP64 at the end.
 //   * Split j-ranges (small N or load balance): each split writes its FP64
@@ -88,6 +90,15 @@ struct F32CKernel {
             const int v = threadIdx.x + q * BLOCK;
             if (NV % BLOCK == 0 || v < NV) sm.j[b][v / (TJ / 4)][v % (TJ / 4)] = r[q];
         }
+    }
+
+    // FP32 offset that moves i-tile coordinates into the j-tile's frame:
+    // (hi_I - hi_J) + (lo_I - lo_J), rounded once more to FP32.
+    __device__ static __forceinline__ void store_shift(Smem &sm, int b, float4 ih, float4 il,
+                                                       float4 jh, float4 jl) {
+        sm.shift[b][0] = __fadd_rn(__fsub_rn(ih.x, jh.x), __fsub_rn(il.x, jl.x));
+        sm.shift[b][1] = __fadd_rn(__fsub_rn(ih.y, jh.y), __fsub_rn(il.y, jl.y));
+        sm.shift[b][2] = __fadd_rn(__fsub_rn(ih.z, jh.z), __fsub_rn(il.z, jl.z));
     }
 
     __device__ static __forceinline__ void body(float2 xj, float2 yj, float2 zj, float2 mj,
@@ -156,9 +167,8 @@ struct F32CKernel {
             const ClusterDev cl = p.cl[it.cluster];
             const int ibase = it.tile * TC;
             const float2 e2 = make_float2(cl.eps2f, cl.eps2f);
-            const double cix = p.centre[4 * it.tile + 0];
-            const double ciy = p.centre[4 * it.tile + 1];
-            const double ciz = p.centre[4 * it.tile + 2];
+            const float4 cih = p.chl[2 * it.tile + 0];  // centre of the i-tile, hi part
+            const float4 cil = p.chl[2 * it.tile + 1];  // lo part
 
             float ox[P], oy[P], oz[P];
 #pragma unroll
@@ -176,16 +186,14 @@ struct F32CKernel {
 
             const int ntj = it.jt1 - it.jt0;
             float4 reg[NLD];
-            float nshift[3] = {0.0f, 0.0f, 0.0f};
+            float4 cjh = make_float4(0.f, 0.f, 0.f, 0.f), cjl = cjh;
             {
                 const int gs = cl.slot_begin + it.jt0 * TJ;
                 load_tile(p, gs, reg);
                 store_tile(sm, 0, reg);
                 if (threadIdx.x == 0) {
                     const int jc = gs / TC;
-                    sm.shift[0][0] = (float)(cix - p.centre[4 * jc + 0]);
-                    sm.shift[0][1] = (float)(ciy - p.centre[4 * jc + 1]);
-                    sm.shift[0][2] = (float)(ciz - p.centre[4 * jc + 2]);
+                    store_shift(sm, 0, cih, cil, p.chl[2 * jc], p.chl[2 * jc + 1]);
                 }
             }
             __syncthreads();
@@ -196,10 +204,9 @@ struct F32CKernel {
                 const int gsn = cl.slot_begin + (it.jt0 + t + 1) * TJ;
                 if (more) load_tile(p, gsn, reg);
                 if (more && threadIdx.x == 0) {
-                    const int jc = gsn / TC;
-                    nshift[0] = (float)(cix - p.centre[4 * jc + 0]);
-                    nshift[1] = (float)(ciy - p.centre[4 * jc + 1]);
-                    nshift[2] = (float)(ciz - p.centre[4 * jc + 2]);
+                    const int jc = gsn / TC;  // loads issued now, used after the tile
+                    cjh = p.chl[2 * jc];
+                    cjl = p.chl[2 * jc + 1];
                 }
                 float2 nx[P], ny[P], nz[P];
                 {
@@ -239,11 +246,7 @@ struct F32CKernel {
                 }
                 if (more) {
                     store_tile(sm, b ^ 1, reg);
-                    if (threadIdx.x == 0) {
-                        sm.shift[b ^ 1][0] = nshift[0];
-                        sm.shift[b ^ 1][1] = nshift[1];
-                        sm.shift[b ^ 1][2] = nshift[2];
-                    }
+                    if (threadIdx.x == 0) store_shift(sm, b ^ 1, cih, cil, cjh, cjl);
                 }
                 __syncthreads();
             }
@@ -296,8 +299,8 @@ struct F32CKernel {
     }
 };
 
-template <int BLOCK, int P, int TJ, bool EPS_ZERO>
-__global__ void __launch_bounds__(BLOCK) forces_f32c_kernel(const F32CParams p) {
+template <int BLOCK, int P, int TJ, int MINB, bool EPS_ZERO>
+__global__ void __launch_bounds__(BLOCK, MINB) forces_f32c_kernel(const F32CParams p) {
     F32CKernel<BLOCK, P, TJ, EPS_ZERO>::run(p);
 }
 

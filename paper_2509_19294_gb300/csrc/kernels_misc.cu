@@ -37,8 +37,9 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*scratch)[NV]
     for (int k = 0; k < NV; ++k) v[k] = scratch[0][k];
 }
 
-// One CTA per centre tile: FP64 centre = mean of the tile's real particles,
+// One CTA per centre tile: centre = FP64 mean of the tile's real particles,
 // FP32 offsets from it, FP32 masses; pad slots get mass 0 and a far offset.
+// The centre is stored as a float pair hi + lo for the force kernel.
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(const PackParams p) {
     __shared__ double red[kPackThreads / 32][4];
     const int t = blockIdx.x;
@@ -89,10 +90,9 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const PackParams p) 
         }
     }
     if (threadIdx.x == 0) {
-        p.centre[4 * t + 0] = cx;
-        p.centre[4 * t + 1] = cy;
-        p.centre[4 * t + 2] = cz;
-        p.centre[4 * t + 3] = 0.0;
+        const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
+        p.chl[2 * t + 0] = make_float4(hx, hy, hz, 0.0f);
+        p.chl[2 * t + 1] = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), 0.0f);
     }
 }
 

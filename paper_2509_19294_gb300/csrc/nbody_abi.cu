@@ -56,7 +56,7 @@ struct nbody_ctx {
     int64_t max_cluster = 0;
 
     // F32C geometry
-    nbody_tiles tiles{0, 0, 0, 0};
+    nbody_tiles tiles{0, 0, 0, 0, 0};
     int tc = 0;
     int grid = 0;
     std::vector<ClusterDev> hcl;
@@ -69,7 +69,7 @@ struct nbody_ctx {
     int *counters = nullptr;
     double *partial = nullptr;
     float *px = nullptr, *py = nullptr, *pz = nullptr, *pm = nullptr;
-    double *centre = nullptr;
+    float4 *chl = nullptr;
     int32_t *perm = nullptr;
 
     // F64
@@ -277,9 +277,9 @@ int choose_split(const nbody_ctx *c, int tc, int tj, int workers) {
 }
 
 nbody_tiles default_tiles(const nbody_ctx *c) {
-    if (c->max_cluster >= 65536) return {128, 4, 256, 0};
-    if (c->max_cluster >= 8192) return {128, 2, 256, 0};
-    return {64, 2, 128, 0};
+    if (c->max_cluster >= 65536) return {256, 4, 512, 0, 1};
+    if (c->max_cluster >= 8192) return {128, 2, 256, 0, 4};
+    return {64, 2, 128, 0, 8};
 }
 
 void free_f32c(nbody_ctx *ctx) {
@@ -292,7 +292,7 @@ void free_f32c(nbody_ctx *ctx) {
     dev_free(&ctx->py);
     dev_free(&ctx->pz);
     dev_free(&ctx->pm);
-    dev_free(&ctx->centre);
+    dev_free(&ctx->chl);
     dev_free(&ctx->perm);
 }
 
@@ -303,7 +303,8 @@ void drop_graphs(nbody_ctx *ctx) {
 
 // (Re)build every F32C buffer for tile shape t.  jfrac < 1 only for timing.
 int build_f32c(nbody_ctx *ctx, nbody_tiles t, double jfrac = 1.0) {
-    const int occ = f32c_occupancy(t.block, t.p, t.tj, ctx->eps_zero);
+    t.ctas_per_sm = f32c_resolve_minb(t.block, t.p, t.tj, t.ctas_per_sm, ctx->eps_zero);
+    const int occ = t.ctas_per_sm ? f32c_occupancy(t.block, t.p, t.tj, t.ctas_per_sm, ctx->eps_zero) : 0;
     if (occ <= 0)
         return fail(ctx, NBODY_EUNSUPPORTED,
                     "tile shape (" + std::to_string(t.block) + "," + std::to_string(t.p) + "," +
@@ -331,7 +332,7 @@ int build_f32c(nbody_ctx *ctx, nbody_tiles t, double jfrac = 1.0) {
     if ((rc = dev_alloc(ctx, &ctx->partial, (size_t)pl.partial_slots * 4 * tc))) return rc;
     for (float **p : {&ctx->px, &ctx->py, &ctx->pz, &ctx->pm})
         if ((rc = dev_alloc(ctx, p, (size_t)ctx->n_pad))) return rc;
-    if ((rc = dev_alloc(ctx, &ctx->centre, (size_t)ctx->n_tiles * 4))) return rc;
+    if ((rc = dev_alloc(ctx, &ctx->chl, (size_t)ctx->n_tiles * 2))) return rc;
     // identity permutation within each cluster, -1 on pads
     std::vector<int32_t> perm((size_t)ctx->n_pad, -1);
     for (const ClusterDev &d : pl.cl)
@@ -472,7 +473,7 @@ int enqueue_forces(nbody_ctx *ctx, const Arrays &a, double half_dt, bool reorder
                                    ctx->sort_n, ctx->perm, s, kernels));
         }
         PackParams pp{a.pos, a.mass, ctx->perm, ctx->dcl, ctx->tile_cluster, ctx->tc, ctx->n,
-                      ctx->px, ctx->py, ctx->pz, ctx->pm, ctx->centre};
+                      ctx->px, ctx->py, ctx->pz, ctx->pm, ctx->chl};
         NB_CUDA(launch_pack(ctx->n_tiles, pp, s));
         ++*kernels;
         NB_CUDA(cudaMemsetAsync(ctx->counters, 0, ((size_t)ctx->n_tiles + 1) * sizeof(int), s));
@@ -481,7 +482,7 @@ int enqueue_forces(nbody_ctx *ctx, const Arrays &a, double half_dt, bool reorder
         fp.py = ctx->py;
         fp.pz = ctx->pz;
         fp.pm = ctx->pm;
-        fp.centre = ctx->centre;
+        fp.chl = ctx->chl;
         fp.perm = ctx->perm;
         fp.cl = ctx->dcl;
         fp.items = ctx->items;
@@ -497,8 +498,8 @@ int enqueue_forces(nbody_ctx *ctx, const Arrays &a, double half_dt, bool reorder
         fp.half_dt = half_dt;
         int rc;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
-        cudaError_t e = launch_f32c(ctx->tiles.block, ctx->tiles.p, ctx->tiles.tj, ctx->eps_zero,
-                                    ctx->grid, fp, s);
+        cudaError_t e = launch_f32c(ctx->tiles.block, ctx->tiles.p, ctx->tiles.tj,
+                                    ctx->tiles.ctas_per_sm, ctx->eps_zero, ctx->grid, fp, s);
         if (e == cudaErrorNotSupported) return fail(ctx, NBODY_EUNSUPPORTED, "tile shape not compiled");
         NB_CUDA(e);
         ++*kernels;
@@ -579,12 +580,12 @@ bool tune_cache_lookup(const nbody_ctx *ctx, nbody_tiles *t) {
     if (!f) return false;
     const std::string key = tune_key(ctx);
     char kbuf[512];
-    int b, p, tj, s;
+    int b, p, tj, s, m;
     double ms;
     bool found = false;
-    while (fscanf(f, "%511s %d %d %d %d %lf", kbuf, &b, &p, &tj, &s, &ms) == 6)
+    while (fscanf(f, "%511s %d %d %d %d %d %lf", kbuf, &b, &p, &tj, &s, &m, &ms) == 7)
         if (key == kbuf) {
-            *t = {b, p, tj, s};
+            *t = {b, p, tj, s, m};
             found = true;
         }
     fclose(f);
@@ -596,7 +597,8 @@ void tune_cache_store(const nbody_ctx *ctx, nbody_tiles t, double ms) {
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %.6f\n", tune_key(ctx).c_str(), t.block, t.p, t.tj, t.split, ms);
+    fprintf(f, "%s %d %d %d %d %d %.6f\n", tune_key(ctx).c_str(), t.block, t.p, t.tj, t.split,
+            t.ctas_per_sm, ms);
     fclose(f);
 }
 
@@ -617,47 +619,48 @@ __global__ void tune_fill_kernel(float *px, float *py, float *pz, float *pm, int
 
 int run_tuner(nbody_ctx *ctx, cudaStream_t s) {
     if (ctx->mode != NBODY_F32C || ctx->n == 0) return NBODY_OK;
-    int blocks[64], ps[64], tjs[64];
-    const int ns = std::min(64, f32c_shapes(blocks, ps, tjs, 64));
+    int blocks[64], ps[64], tjs[64], mbs[64];
+    const int ns = std::min(64, f32c_shapes(blocks, ps, tjs, mbs, 64));
     double total_pairs = 0.0;
     for (int k = 0; k < ctx->ncl; ++k) total_pairs += (double)cluster_n(ctx, k) * cluster_n(ctx, k);
-    // bound each timed launch to ~2e10 pairs by truncating the j-ranges
-    const double jfrac = std::min(1.0, 2.0e10 / std::max(total_pairs, 1.0));
+    // bound each timed launch to ~1e11 pairs (~40 ms) by truncating the j-ranges
+    const double jfrac = std::min(1.0, 1.0e11 / std::max(total_pairs, 1.0));
     double acc_scratch_bytes = (double)ctx->n * 4 * sizeof(double);
     double *acc = nullptr;
     NB_CUDA(cudaMalloc(&acc, (size_t)acc_scratch_bytes));
     cudaEvent_t e0, e1;
     NB_CUDA(cudaEventCreate(&e0));
     NB_CUDA(cudaEventCreate(&e1));
-    nbody_tiles best{0, 0, 0, 0};
+    nbody_tiles best{0, 0, 0, 0, 0};
     double best_ms = 1e30;
     int rc = NBODY_OK;
     for (int c = 0; c < ns && rc == NBODY_OK; ++c) {
-        nbody_tiles t{blocks[c], ps[c], tjs[c], 0};
+        nbody_tiles t{blocks[c], ps[c], tjs[c], 0, mbs[c]};
         if ((int64_t)t.block * t.p > 2 * std::max<int64_t>(ctx->max_cluster, 128)) continue;
         for (int sv = 0; sv < 3 && rc == NBODY_OK; ++sv) {
             nbody_tiles tt = t;
             if (sv > 0) {
-                const int occ = f32c_occupancy(t.block, t.p, t.tj, ctx->eps_zero);
+                const int occ = f32c_occupancy(t.block, t.p, t.tj, t.ctas_per_sm, ctx->eps_zero);
                 const int base = choose_split(ctx, t.block * t.p, t.tj, occ * ctx->sms);
                 tt.split = sv == 1 ? base * 2 : std::max(1, base / 2);
                 if (tt.split == base) continue;
             }
             if ((rc = build_f32c(ctx, tt, jfrac))) break;
             tune_fill_kernel<<<256, 256, 0, s>>>(ctx->px, ctx->py, ctx->pz, ctx->pm, ctx->n_pad);
-            NB_CUDA(cudaMemsetAsync(ctx->centre, 0, (size_t)ctx->n_tiles * 4 * sizeof(double), s));
+            NB_CUDA(cudaMemsetAsync(ctx->chl, 0, (size_t)ctx->n_tiles * 2 * sizeof(float4), s));
             Arrays a{nullptr, nullptr, acc, acc + 3 * ctx->n, nullptr, nullptr};
             float ms_best = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 F32CParams fp{};
                 fp.px = ctx->px; fp.py = ctx->py; fp.pz = ctx->pz; fp.pm = ctx->pm;
-                fp.centre = ctx->centre; fp.perm = ctx->perm; fp.cl = ctx->dcl;
+                fp.chl = ctx->chl; fp.perm = ctx->perm; fp.cl = ctx->dcl;
                 fp.items = ctx->items; fp.n_items = ctx->n_items; fp.tc = ctx->tc;
                 fp.counters = ctx->counters; fp.partial = ctx->partial;
                 fp.acc = a.acc; fp.pot = a.pot; fp.vel = nullptr; fp.n = ctx->n; fp.G = 1.0;
                 NB_CUDA(cudaMemsetAsync(ctx->counters, 0, ((size_t)ctx->n_tiles + 1) * sizeof(int), s));
                 NB_CUDA(cudaEventRecord(e0, s));
-                NB_CUDA(launch_f32c(tt.block, tt.p, tt.tj, ctx->eps_zero, ctx->grid, fp, s));
+                NB_CUDA(launch_f32c(tt.block, tt.p, tt.tj, tt.ctas_per_sm, ctx->eps_zero, ctx->grid,
+                                    fp, s));
                 NB_CUDA(cudaEventRecord(e1, s));
                 NB_CUDA(cudaEventSynchronize(e1));
                 float ms = 0.0f;
@@ -704,9 +707,9 @@ const char *nbody_strerror(int status) {
 const char *nbody_last_error_message(const nbody_ctx *ctx) { return ctx ? ctx->msg.c_str() : ""; }
 
 int nbody_tiles_supported(nbody_tiles *out, int cap) {
-    int b[64], p[64], t[64];
-    const int n = f32c_shapes(b, p, t, 64);
-    for (int k = 0; k < n && k < cap && out; ++k) out[k] = {b[k], p[k], t[k], 0};
+    int b[64], p[64], t[64], m[64];
+    const int n = f32c_shapes(b, p, t, m, 64);
+    for (int k = 0; k < n && k < cap && out; ++k) out[k] = {b[k], p[k], t[k], 0, m[k]};
     return n;
 }
 
@@ -797,8 +800,12 @@ int nbody_init(nbody_ctx **out, const nbody_config *cfg, void *stream) {
             if (!forced) {
                 nbody_tiles cached;
                 if (tune_cache_lookup(ctx, &cached)) t = cached;
-                else if (cfg->flags & NBODY_FLAG_AUTOTUNE) t = {0, 0, 0, -1};
-                else t = default_tiles(ctx), t.split = cfg->tiles.split;
+                else if (cfg->flags & NBODY_FLAG_AUTOTUNE) t = {0, 0, 0, -1, 0};
+                else {
+                    t = default_tiles(ctx);
+                    t.split = cfg->tiles.split;
+                    if (cfg->tiles.ctas_per_sm) t.ctas_per_sm = cfg->tiles.ctas_per_sm;
+                }
             }
             if (t.split == -1) {
                 if ((rc = build_f32c(ctx, default_tiles(ctx)))) break;
@@ -828,7 +835,7 @@ int nbody_tune(nbody_ctx *ctx, void *stream) {
 
 int nbody_get_tiles(const nbody_ctx *ctx, nbody_tiles *out) {
     if (!ctx || !out) return NBODY_EINVAL;
-    *out = ctx->mode == NBODY_F32C ? ctx->tiles : nbody_tiles{0, 0, 0, 0};
+    *out = ctx->mode == NBODY_F32C ? ctx->tiles : nbody_tiles{0, 0, 0, 0, 0};
     return NBODY_OK;
 }
 

@@ -5,8 +5,10 @@
 //     Every cluster starts on a tile boundary and is padded up to a multiple of
 //     Tc; pad slots carry mass 0 and a far offset so they add exactly nothing.
 //   * px/py/pz/pm: float[n_pad] SoA, the FP32 offset of each particle from its
-//     tile's FP64 centre, and its mass rounded to FP32.
-//   * centre: double[n_tiles][4] (x, y, z, unused).
+//     tile's centre, and its mass rounded to FP32.
+//   * chl: float4[n_tiles][2], each tile's centre as an unevaluated float pair
+//     (hi.x + lo.x, ...): the FP64 mean of the tile's positions split into
+//     hi = fl32(c) and lo = fl32(c - hi).
 //   * perm: int32[n_pad], the caller's row of each packed slot (-1 for pads).
 //     Identity within each cluster unless Morton reordering is on.
 //   * items: the work queue of the force kernel, one entry per
@@ -43,7 +45,7 @@ struct Item {
 // Parameters of the FP32-compensated force kernel (passed by value).
 struct F32CParams {
     const float *px, *py, *pz, *pm;
-    const double *centre;
+    const float4 *chl;
     const int32_t *perm;
     const ClusterDev *cl;
     const Item *items;
@@ -80,7 +82,7 @@ struct PackParams {
     int32_t tc;
     int64_t n;
     float *px, *py, *pz, *pm;
-    double *centre;
+    float4 *chl;
 };
 
 // A run of at most kChunk consecutive rows inside one cluster (energy, bbox, keys).
@@ -93,16 +95,19 @@ struct Chunk {
 
 // ---- kernel launchers (all enqueue on `s`, return cudaGetLastError()) ----
 
-// The F32C force kernel for tile shape (block, p, tj); eps_zero selects the
-// variant that gives coincident pairs zero force (needed when some eps == 0).
-// Returns cudaErrorNotSupported if the shape is not compiled.  `grid` CTAs run
-// the persistent work loop.
-cudaError_t launch_f32c(int block, int p, int tj, bool eps_zero, int grid, const F32CParams &prm,
-                        cudaStream_t s);
+// The F32C force kernel for tile shape (block, p, tj) compiled for minb resident
+// CTAs per SM (0 = the first compiled variant); eps_zero selects the variant that
+// gives coincident pairs zero force (needed when some eps == 0).  Returns
+// cudaErrorNotSupported if the shape is not compiled.  `grid` CTAs run the
+// persistent work loop.
+cudaError_t launch_f32c(int block, int p, int tj, int minb, bool eps_zero, int grid,
+                        const F32CParams &prm, cudaStream_t s);
 // Maximum resident CTAs per SM of the given shape (0 if not compiled).
-int f32c_occupancy(int block, int p, int tj, bool eps_zero);
-// Compiled shapes: fills up to cap triples (block, p, tj), returns the count.
-int f32c_shapes(int *block, int *p, int *tj, int cap);
+int f32c_occupancy(int block, int p, int tj, int minb, bool eps_zero);
+// The minb of the variant that (block, p, tj, minb) selects (0 if none).
+int f32c_resolve_minb(int block, int p, int tj, int minb, bool eps_zero);
+// Compiled shapes: fills up to cap (block, p, tj, minb), returns the count.
+int f32c_shapes(int *block, int *p, int *tj, int *minb, int cap);
 
 cudaError_t launch_f64(int grid, const F64Params &prm, cudaStream_t s);
 constexpr int kF64Block = 128;

@@ -51,8 +51,8 @@ def test_status_strings(lib):
 def test_tile_table_is_consistent(lib):
     shapes = nb.nbody_tiles_supported()
     assert len(shapes) >= 4
-    for block, p, tj in shapes:
-        assert block % 32 == 0 and tj % 8 == 0 and (block * p) % tj == 0
+    for block, p, tj, minb in shapes:
+        assert block % 32 == 0 and tj % 8 == 0 and (block * p) % tj == 0 and minb >= 1
 
 
 def test_init_rejects_bad_configs_before_touching_the_device(lib):

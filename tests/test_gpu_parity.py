@@ -116,11 +116,11 @@ def test_every_tile_shape_and_split(oracle):
     n = 3001
     pos, _, mass = ic.plummer(n, seed=7)
     ra, rp = oracle.forces(pos, mass, 0.01)
-    for block, p_, tj in nb.nbody_tiles_supported():
+    for block, p_, tj, minb in nb.nbody_tiles_supported():
         for split in (1, 3):
-            a, p = forces(pos, mass, 0.01, tiles=(block, p_, tj, split))
+            a, p = forces(pos, mass, 0.01, tiles=(block, p_, tj, split, minb))
             s = metrics.summary(a, ra, p, rp)
-            assert s["median"] <= F32C_MEDIAN and s["max"] <= F32C_MAX, (block, p_, tj, split, s)
+            assert s["median"] <= F32C_MEDIAN and s["max"] <= F32C_MAX, (block, p_, tj, minb, split, s)
 
 
 def test_translation_invariance_of_f32c(oracle):
