@@ -69,6 +69,7 @@ extern "C" {
 #define NBODY_ETIMEOUT (-5)     /* a bounded device-side wait gave up */
 #define NBODY_ESTATE (-6)       /* the context holds an earlier error */
 #define NBODY_EUNSUPPORTED (-7) /* no kernel instantiation for the requested tiles */
+#define NBODY_ETOOBIG (-8)      /* n exceeds the fixed scratch of nbody_forces_noalloc */
 
 /* arithmetic modes */
 #define NBODY_F64 0
@@ -180,6 +181,42 @@ int nbody_profile_read(nbody_ctx *ctx, double *ms_total, int64_t *launches, int 
 
 /* Number of kernels the library has launched on this context (eager and graph nodes). */
 int64_t nbody_kernel_launches(const nbody_ctx *ctx);
+
+/*
+ * nbody_forces_noalloc -- the F32C force evaluation of ONE system with no
+ * memory allocation at all.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need forces
+ * (code running inside a memory pool or arena it does not own, loops that must
+ * not pay allocation latency, plug-ins in a host process that has already
+ * reserved the GPU's memory).  nbody_init allocates a context's scratch with
+ * cudaMalloc, so those callers cannot use the other entry points.
+ *
+ * Instead, the scratch (packed tiles, permutation, work queue, partial sums) is
+ * a fixed array of NBODY_NOALLOC_SCRATCH_BYTES compiled into libnbody.so; every
+ * GPU that loads the library holds it until the process exits.  The call makes
+ * no cudaMalloc, cudaFree or other allocating call.
+ *
+ *   n          particles, 0 <= n <= NBODY_NOALLOC_MAX_N (larger n: NBODY_ETOOBIG)
+ *   pos  in  : device double[3][n]      mass in : device double[n]
+ *   acc  out : device double[3][n]      pot  out: device double[n] or NULL
+ *   eps, G   : softening length (finite, >= 0) and gravitational constant
+ * Host pointers are rejected (NBODY_EINVAL): staging them would need buffers.
+ *
+ * The result equals nbody_forces on a single-cluster NBODY_F32C context without
+ * reordering, using tile shape (128, 2, 256) and a split chosen from n.
+ * The work is enqueued on `stream`; the call does not synchronise.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current), so make the first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents (each call re-initialises what must start from zero): two calls
+ * whose work overlaps on the GPU -- e.g. on different streams without ordering
+ * -- race and corrupt each other's results.  Serialise them.
+ */
+#define NBODY_NOALLOC_MAX_N 262144
+#define NBODY_NOALLOC_SCRATCH_BYTES 10297856
+int nbody_forces_noalloc(int64_t n, const double *pos, const double *mass, double eps, double G,
+                         double *acc, double *pot, void *stream);
 
 /* Static description of a status code. */
 const char *nbody_strerror(int status);

@@ -31,6 +31,8 @@ NBODY_ENONFINITE = -4
 NBODY_ETIMEOUT = -5
 NBODY_ESTATE = -6
 NBODY_EUNSUPPORTED = -7
+NBODY_ETOOBIG = -8
+NBODY_NOALLOC_MAX_N = 262144
 
 NBODY_F64 = 0
 NBODY_F32C = 1
@@ -42,7 +44,8 @@ NBODY_FLAG_NO_GRAPH = 8
 
 EXPORTED = ("nbody_init", "nbody_destroy", "nbody_forces", "nbody_step", "nbody_energy",
             "nbody_tune", "nbody_get_tiles", "nbody_tiles_supported", "nbody_profile_read",
-            "nbody_kernel_launches", "nbody_strerror", "nbody_last_error_message")
+            "nbody_kernel_launches", "nbody_strerror", "nbody_last_error_message",
+            "nbody_forces_noalloc")
 
 
 class NBodyTiles(ctypes.Structure):
@@ -105,6 +108,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.nbody_strerror.restype = ctypes.c_char_p
         lib.nbody_last_error_message.argtypes = [vp]
         lib.nbody_last_error_message.restype = ctypes.c_char_p
+        lib.nbody_forces_noalloc.argtypes = [i64, vp, vp, d, d, vp, vp, vp]
+        lib.nbody_forces_noalloc.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -283,3 +288,21 @@ def nbody_profile_read(ctx: Context, reset: bool = False):
 
 def nbody_kernel_launches(ctx: Context) -> int:
     return int(load().nbody_kernel_launches(ctx.handle))
+
+
+def nbody_forces_noalloc(pos, mass, eps: float, acc, pot=None, G: float = 1.0, stream=None) -> None:
+    """Forces of one system without any allocation (see nbody_forces_noalloc in nbody.h).
+
+    For callers that cannot allocate device memory when they compute forces:
+    the library uses a fixed scratch array compiled into libnbody.so instead of
+    a context.  All arrays must already be on the device; n is at most
+    NBODY_NOALLOC_MAX_N.  Calls share the scratch, so do not let two of them
+    run concurrently on the GPU.
+    """
+    n = int(mass.shape[0])
+    keep = []
+    rc = load().nbody_forces_noalloc(n, _ptr(pos, (3, n), "pos", keep),
+                                     _ptr(mass, (n,), "mass", keep), float(eps), float(G),
+                                     _ptr(acc, (3, n), "acc", keep), _ptr(pot, (n,), "pot", keep),
+                                     _stream(stream))
+    _check(None, rc, "nbody_forces_noalloc")

@@ -700,6 +700,7 @@ const char *nbody_strerror(int status) {
         case NBODY_ETIMEOUT: return "device wait timed out";
         case NBODY_ESTATE: return "context is in an error state";
         case NBODY_EUNSUPPORTED: return "unsupported tile shape";
+        case NBODY_ETOOBIG: return "n exceeds NBODY_NOALLOC_MAX_N, the fixed scratch of nbody_forces_noalloc";
         default: return "unknown status";
     }
 }
