@@ -179,6 +179,19 @@ int nbody_tiles_supported(nbody_tiles *out, int cap);
  */
 int nbody_profile_read(nbody_ctx *ctx, double *ms_total, int64_t *launches, int reset);
 
+/*
+ * Per-SM issue rates of this GPU behind the force kernel's roofline, measured
+ * with one CTA of 1024 threads per SM and clock64() cycles (so they do not
+ * depend on the clock frequency).  out (host, n_out >= 4):
+ *   out[0] FP32 lane-operations per clock per SM with paired (f32x2) FMA
+ *   out[1] MUFU rsqrt results per clock per SM
+ *   out[2] pairwise interactions per clock per SM of the F32C kernel's per-pair
+ *          arithmetic alone (register-resident operands, no shared-memory loads)
+ *   out[3] FP64 FMA per clock per SM
+ * Allocates and frees a small device buffer and synchronises the device.
+ */
+int nbody_measure_pipes(double *out, int n_out);
+
 /* Number of kernels the library has launched on this context (eager and graph nodes). */
 int64_t nbody_kernel_launches(const nbody_ctx *ctx);
 

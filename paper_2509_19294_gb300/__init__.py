@@ -45,7 +45,7 @@ NBODY_FLAG_NO_GRAPH = 8
 EXPORTED = ("nbody_init", "nbody_destroy", "nbody_forces", "nbody_step", "nbody_energy",
             "nbody_tune", "nbody_get_tiles", "nbody_tiles_supported", "nbody_profile_read",
             "nbody_kernel_launches", "nbody_strerror", "nbody_last_error_message",
-            "nbody_forces_noalloc")
+            "nbody_forces_noalloc", "nbody_measure_pipes")
 
 
 class NBodyTiles(ctypes.Structure):
@@ -110,6 +110,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.nbody_last_error_message.restype = ctypes.c_char_p
         lib.nbody_forces_noalloc.argtypes = [i64, vp, vp, d, d, vp, vp, vp]
         lib.nbody_forces_noalloc.restype = ctypes.c_int
+        lib.nbody_measure_pipes.argtypes = [ctypes.POINTER(d), ctypes.c_int]
+        lib.nbody_measure_pipes.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -284,6 +286,15 @@ def nbody_profile_read(ctx: Context, reset: bool = False):
     rc = load().nbody_profile_read(ctx.handle, ctypes.byref(ms), ctypes.byref(cnt), int(reset))
     _check(ctx, rc, "nbody_profile_read")
     return ms.value, cnt.value
+
+
+def nbody_measure_pipes() -> dict:
+    """Measured per-SM-per-clock rates: FP32 f32x2 lanes, MUFU rsqrt, force-kernel
+    pair arithmetic (pairs), FP64 FMA (see nbody_measure_pipes in nbody.h)."""
+    out = (ctypes.c_double * 4)()
+    _check(None, load().nbody_measure_pipes(out, 4), "nbody_measure_pipes")
+    return {"fp32_lanes_per_clk_sm": out[0], "mufu_rsqrt_per_clk_sm": out[1],
+            "pair_arith_pairs_per_clk_sm": out[2], "fp64_fma_per_clk_sm": out[3]}
 
 
 def nbody_kernel_launches(ctx: Context) -> int:

@@ -1,0 +1,162 @@
+"""The five reference workloads through the CUDA path, checked against the oracle (GPU).
+
+C1  Plummer N=1024, eps=0.01, KDK dt=1e-3, 10 steps, FP64 path: a, phi and E
+    each step against the oracle's own leapfrog.
+C2  N=16384 uniform sphere and Plummer, log-uniform masses, eps=0.005
+    (covered in test_gpu_parity.py::test_f32c_16384_log_uniform_masses).
+C3  Plummer N=131072, eps=1e-3, dt=1e-4, graph-replayed steps: the FP32C and
+    FP64 GPU paths agree step by step on E, P and L (the long 1000-step run is
+    opt-in with NBODY_LONG=1, it takes about 13 minutes of FP64 work).
+C4  512 clusters, N_c ~ U{256..8192}, eps_c = 0.01 N_c^(-1/3): every cluster's
+    forces against the oracle, then steps with per-cluster diagnostics.
+C5  two Plummer spheres of 524288 on a head-on approach, eps=1e-3: sampled rows
+    of the full-size launch (the configuration bench.py times) against the
+    oracle row by row.
+
+FP32C tolerance: per-particle relative acceleration error median <= 1e-6 and
+max <= 1e-4, potential likewise, and the paper's 0.05 % bound (each component
+against the particle's own force magnitude; see tests/metrics.py).
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2509_19294_gb300 as nb
+from paper_2509_19294_gb300 import ic
+from tests import metrics
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_19294_gb300 import build
+    build.build()
+    nb.load()
+    torch.cuda.init()
+
+
+def check_f32c(a, p, ra, rp):
+    s = metrics.summary(a, ra, p, rp)
+    assert s["median"] <= 1e-6 and s["max"] <= 1e-4, s
+    assert s["pot_median"] <= 1e-6 and s["pot_max"] <= 1e-4, s
+    assert s["paper"] <= 5e-4, s
+    return s
+
+
+def test_c1_fp64_steps_match_oracle_each_step(oracle):
+    pos, vel, mass = ic.plummer(1024, seed=1)
+    n = 1024
+    with nb.nbody_init(n, 0.01, mode=nb.NBODY_F64) as ctx:
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        pot = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_forces(ctx, p, m, acc, pot)
+        rp, rv, ra, rpot = pos, vel, None, None
+        for step in range(10):
+            d = torch.empty((1, 1, 9), dtype=torch.float64, device="cuda")
+            nb.nbody_step(ctx, p, v, m, acc, pot, 1e-3, 1, d)
+            rp, rv, ra, rpot, rd = oracle.kdk(rp, rv, mass, 0.01, 1e-3, 1, acc=ra, pot=rpot,
+                                             diag=True)
+            assert metrics.rel_acc_errors(host(acc), ra).max() <= 1e-11, step
+            assert metrics.rel_pot_errors(host(pot), rpot).max() <= 1e-11, step
+            np.testing.assert_allclose(host(d)[0, 0], rd[1], rtol=1e-11, atol=1e-14)
+
+
+def test_c3_fp32c_tracks_fp64_each_step():
+    n = 131072
+    pos, vel, mass = ic.plummer(n, seed=3)
+    tracks = {}
+    for mode in (nb.NBODY_F32C, nb.NBODY_F64):
+        with nb.nbody_init(n, 1e-3, mode=mode, reorder_every=10) as ctx:
+            p, v, m = dev(pos), dev(vel), dev(mass)
+            acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+            pot = torch.empty(n, dtype=torch.float64, device="cuda")
+            nb.nbody_forces(ctx, p, m, acc, pot)
+            e0 = nb.nbody_energy(ctx, p, v, m, pot)[0]
+            d = torch.empty((10, 1, 9), dtype=torch.float64, device="cuda")
+            nb.nbody_step(ctx, p, v, m, acc, pot, 1e-4, 10, d)
+            tracks[mode] = np.concatenate([e0[None], host(d)[:, 0, :]])
+    e32, e64 = tracks[nb.NBODY_F32C], tracks[nb.NBODY_F64]
+    np.testing.assert_allclose(e32[:, 2], e64[:, 2], rtol=1e-6)       # E via W inherits 1e-6
+    assert np.abs(e32[:, 3:6] - e64[:, 3:6]).max() <= 1e-9              # P
+    drift32 = np.abs(e32[:, 2] - e32[0, 2]).max() / abs(e32[0, 2])
+    drift64 = np.abs(e64[:, 2] - e64[0, 2]).max() / abs(e64[0, 2])
+    assert drift32 <= 2 * drift64 + 2e-7, (drift32, drift64)
+
+
+@pytest.mark.skipif(os.environ.get("NBODY_LONG") != "1", reason="13-minute run; NBODY_LONG=1")
+def test_c3_full_1000_steps_drift_within_twice_fp64():
+    n = 131072
+    pos, vel, mass = ic.plummer(n, seed=3)
+    drift = {}
+    for mode in (nb.NBODY_F32C, nb.NBODY_F64):
+        with nb.nbody_init(n, 1e-3, mode=mode, reorder_every=10) as ctx:
+            p, v, m = dev(pos), dev(vel), dev(mass)
+            acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+            pot = torch.empty(n, dtype=torch.float64, device="cuda")
+            nb.nbody_forces(ctx, p, m, acc, pot)
+            e0 = nb.nbody_energy(ctx, p, v, m, pot)[0]
+            d = torch.empty((1000, 1, 9), dtype=torch.float64, device="cuda")
+            nb.nbody_step(ctx, p, v, m, acc, pot, 1e-4, 1000, d)
+            e = host(d)[:, 0, :]
+            drift[mode] = (np.abs(e[:, 2] - e0[2]).max() / abs(e0[2]),
+                           np.abs(e[:, 3:6] - e0[3:6]).max())
+    assert drift[nb.NBODY_F32C][0] <= 2 * drift[nb.NBODY_F64][0], drift
+    print("C3 drift", drift)
+
+
+def test_c4_ensemble_all_clusters_match_oracle(oracle):
+    ens = ic.ensemble(512, seed=4)
+    n = ens.mass.shape[0]
+    with nb.nbody_init(n, ens.eps, cluster_offsets=ens.offsets, reorder_every=1) as ctx:
+        p, v, m = dev(ens.pos), dev(ens.vel), dev(ens.mass)
+        acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        pot = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_forces(ctx, p, m, acc, pot)
+        a, ph = host(acc), host(pot)
+        worst = {"median": 0.0, "max": 0.0}
+        for c in range(512):
+            b, e = ens.offsets[c], ens.offsets[c + 1]
+            ra, rp = oracle.forces(ens.pos[:, b:e], ens.mass[b:e], ens.eps[c])
+            s = check_f32c(a[:, b:e], ph[b:e], ra, rp)
+            worst = {k: max(worst[k], s[k]) for k in worst}
+        d = torch.empty((20, 512, 9), dtype=torch.float64, device="cuda")
+        nb.nbody_step(ctx, p, v, m, acc, pot, 1e-3, 20, d)
+        dg = host(d)
+    # per-cluster momentum: FP32 pair terms break Newton's third law only at the
+    # rounding level, so |dP| <= steps * dt * (max rel. error 1e-4) * sum m|a|
+    assert np.all(np.isfinite(dg)) and np.all(dg[:, :, 2] < 0)
+    for c in range(512):
+        b, e = ens.offsets[c], ens.offsets[c + 1]
+        bound = 20 * 1e-3 * 1e-4 * (ens.mass[b:e] * np.linalg.norm(a[:, b:e], axis=0)).sum()
+        assert np.abs(dg[:, c, 3:6]).max() <= bound, c
+
+
+def test_c5_full_size_sampled_rows(oracle):
+    pos, vel, mass = ic.two_plummer(524288, seed=5)
+    n = mass.shape[0]
+    with nb.nbody_init(n, 1e-3, reorder_every=1, flags=nb.NBODY_FLAG_AUTOTUNE) as ctx:
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        pot = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_forces(ctx, p, m, acc, pot)
+        rows = ic.sample_rows(n, 1024, 77)
+        ra, rp = oracle.forces_rows(pos, mass, 1e-3, rows)
+        check_f32c(host(acc)[:, rows], host(pot)[rows], ra, rp)
+        # one graph-replayed step, then the same check at the new positions
+        nb.nbody_step(ctx, p, v, m, acc, pot, 1e-4, 1)
+        ph = host(p)
+        ra, rp = oracle.forces_rows(ph, mass, 1e-3, rows)
+        check_f32c(host(acc)[:, rows], host(pot)[rows], ra, rp)
+
+
+def test_measured_pipe_rates_are_plausible():
+    r = nb.nbody_measure_pipes()
+    assert 32 <= r["fp32_lanes_per_clk_sm"] <= 260, r
+    assert 4 <= r["mufu_rsqrt_per_clk_sm"] <= 64, r
+    assert 1 <= r["pair_arith_pairs_per_clk_sm"] <= 20, r
+    assert 0 < r["fp64_fma_per_clk_sm"] <= 64, r

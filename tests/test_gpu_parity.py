@@ -6,7 +6,7 @@ Tolerances:
   * NBODY_F32C against the oracle: median relative acceleration error <= 1e-6
     and max <= 1e-4, potential median <= 1e-6 and max <= 1e-4, and the paper's
     own bound (each component within 0.05 % of a typical force magnitude,
-    Sec. 3 validation paragraph).
+    Sec. 3 validation paragraph; "typical" read as the particle's own |a_i|).
 """
 import numpy as np
 import pytest
