@@ -9,8 +9,7 @@ namespace nbody {
 
 namespace {
 
-constexpr int kPackThreads = 128;
-constexpr int kPackMaxPer = 8;  // tc <= 1024
+constexpr int kPackWarps = 8;
 
 // Deterministic block sum of NV doubles (fixed shuffle tree, then warps in order).
 template <int NT, int NV>
@@ -37,59 +36,53 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*scratch)[NV]
     for (int k = 0; k < NV; ++k) v[k] = scratch[0][k];
 }
 
-// One CTA per centre tile: centre = FP64 mean of the tile's real particles,
-// FP32 offsets from it, FP32 masses; pad slots get mass 0 and a far offset.
-// The centre is stored as a float pair hi + lo for the force kernel.
-__global__ void __launch_bounds__(kPackThreads) pack_kernel(const PackParams p) {
-    __shared__ double red[kPackThreads / 32][4];
-    const int t = blockIdx.x;
+// One warp per centre tile: centre = FP64 mean of the tile's real particles
+// (fixed-order shuffle tree, so bitwise reproducible), FP32 offsets from it,
+// FP32 masses; pad slots get mass 0 and a far offset.  The centre is stored as
+// a float pair hi + lo for the force kernel.  No block barriers: a CTA of
+// kPackWarps warps packs kPackWarps independent tiles.
+__global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(const PackParams p, int n_tiles) {
+    const int lane = threadIdx.x % 32;
+    const int t = blockIdx.x * kPackWarps + threadIdx.x / 32;
+    if (t >= n_tiles) return;  // warp-uniform
     const ClusterDev cl = p.cl[p.tile_cluster[t]];
     const int base = t * p.tc;
-    const int per = p.tc / kPackThreads;
-    double x[kPackMaxPer], y[kPackMaxPer], z[kPackMaxPer], m[kPackMaxPer];
-    bool real[kPackMaxPer];
+    const int per = p.tc / 32;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-    for (int r = 0; r < kPackMaxPer; ++r) {
-        real[r] = false;
-        x[r] = y[r] = z[r] = m[r] = 0.0;
-        if (r < per) {
-            const int slot = base + threadIdx.x + r * kPackThreads;
-            if (slot - cl.slot_begin < cl.n) {
-                const int64_t u = p.perm[slot];
-                x[r] = p.pos[u];
-                y[r] = p.pos[p.n + u];
-                z[r] = p.pos[2 * p.n + u];
-                m[r] = p.mass[u];
-                real[r] = true;
-                s[0] += x[r];
-                s[1] += y[r];
-                s[2] += z[r];
-                s[3] += 1.0;
-            }
+#pragma unroll 4
+    for (int r = 0; r < per; ++r) {
+        const int slot = base + lane + 32 * r;
+        if (slot - cl.slot_begin < cl.n) {
+            const int64_t u = p.perm[slot];
+            s[0] += p.pos[u];
+            s[1] += p.pos[p.n + u];
+            s[2] += p.pos[2 * p.n + u];
+            s[3] += 1.0;
         }
     }
-    block_sum<kPackThreads, 4>(s, red);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
     const double cnt = s[3] > 0.0 ? s[3] : 1.0;
     const double cx = s[0] / cnt, cy = s[1] / cnt, cz = s[2] / cnt;
-#pragma unroll
-    for (int r = 0; r < kPackMaxPer; ++r) {
-        if (r < per) {
-            const int slot = base + threadIdx.x + r * kPackThreads;
-            if (real[r]) {
-                p.px[slot] = (float)(x[r] - cx);
-                p.py[slot] = (float)(y[r] - cy);
-                p.pz[slot] = (float)(z[r] - cz);
-                p.pm[slot] = (float)m[r];
-            } else {
-                p.px[slot] = kPadOffset;
-                p.py[slot] = kPadOffset;
-                p.pz[slot] = kPadOffset;
-                p.pm[slot] = 0.0f;
-            }
+#pragma unroll 4
+    for (int r = 0; r < per; ++r) {
+        const int slot = base + lane + 32 * r;
+        if (slot - cl.slot_begin < cl.n) {
+            const int64_t u = p.perm[slot];
+            p.px[slot] = (float)(p.pos[u] - cx);
+            p.py[slot] = (float)(p.pos[p.n + u] - cy);
+            p.pz[slot] = (float)(p.pos[2 * p.n + u] - cz);
+            p.pm[slot] = (float)p.mass[u];
+        } else {
+            p.px[slot] = kPadOffset;
+            p.py[slot] = kPadOffset;
+            p.pz[slot] = kPadOffset;
+            p.pm[slot] = 0.0f;
         }
     }
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
         const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
         p.chl[2 * t + 0] = make_float4(hx, hy, hz, 0.0f);
         p.chl[2 * t + 1] = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), 0.0f);
@@ -117,6 +110,7 @@ __global__ void __launch_bounds__(kEnergyThreads)
     __shared__ double red[kEnergyThreads / 32][8];
     const Chunk ch = chunks[blockIdx.x];
     double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 4
     for (int64_t i = ch.begin + threadIdx.x; i < ch.end; i += kEnergyThreads) {
         const double m = mass[i];
         const double x = pos[i], y = pos[n + i], z = pos[2 * n + i];
@@ -180,9 +174,8 @@ int grid_for(int64_t work, int threads) {
 
 cudaError_t launch_pack(int n_tiles, const PackParams &prm, cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
-    if (prm.tc % kPackThreads != 0 || prm.tc / kPackThreads > kPackMaxPer)
-        return cudaErrorInvalidValue;
-    pack_kernel<<<n_tiles, kPackThreads, 0, s>>>(prm);
+    if (prm.tc % 32 != 0) return cudaErrorInvalidValue;
+    pack_kernel<<<(n_tiles + kPackWarps - 1) / kPackWarps, kPackWarps * 32, 0, s>>>(prm, n_tiles);
     return cudaGetLastError();
 }
 

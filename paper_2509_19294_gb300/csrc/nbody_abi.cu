@@ -377,7 +377,8 @@ int build_common(nbody_ctx *ctx) {
         ctx->hcl = cl;
         if ((rc = upload(ctx, &ctx->dcl, cl))) return rc;
     }
-    if (ctx->mode == NBODY_F32C && ctx->reorder_every > 0 && ctx->n > 0) {
+    if (ctx->mode == NBODY_F32C && ctx->reorder_every > 0 && ctx->n > 0 &&
+        !reorder_in_smem(ctx->max_cluster)) {
         int64_t s = 1;
         while (s < ctx->n) s <<= 1;
         ctx->sort_n = s;
@@ -470,7 +471,7 @@ int enqueue_forces(nbody_ctx *ctx, const Arrays &a, double half_dt, bool reorder
         if (reorder) {
             NB_CUDA(launch_reorder(a.pos, ctx->n, ctx->chunks, ctx->n_chunks, ctx->chunk_first,
                                    ctx->ncl, ctx->dcl, ctx->bpart, ctx->bbox, ctx->keys, ctx->vals,
-                                   ctx->sort_n, ctx->perm, s, kernels));
+                                   ctx->sort_n, ctx->max_cluster, ctx->perm, s, kernels));
         }
         PackParams pp{a.pos, a.mass, ctx->perm, ctx->dcl, ctx->tile_cluster, ctx->tc, ctx->n,
                       ctx->px, ctx->py, ctx->pz, ctx->pm, ctx->chl};

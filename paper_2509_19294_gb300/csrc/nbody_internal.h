@@ -125,13 +125,18 @@ cudaError_t launch_energy(const double *pos, const double *vel, const double *ma
                           const int32_t *chunk_first, int ncl, double *part, double *out_base,
                           int *counter, cudaStream_t s);
 
-// Morton reordering: fills perm[slot] for every real slot.
-// keys/vals: scratch of sort_n (power of two >= n) entries; part: double[n_chunks][6];
-// bbox: double[ncl][6].
+// Morton reordering: fills perm[slot] for every real slot.  Clusters of at most
+// kSmemSortMax particles are sorted one CTA per cluster in shared memory (then
+// keys/vals/part/bbox are unused and may be null); otherwise keys/vals are
+// scratch of sort_n (power of two >= n) entries, part double[n_chunks][6] and
+// bbox double[ncl][6].
+constexpr int64_t kSmemSortMax = 16384;
+bool reorder_in_smem(int64_t max_cluster);
 cudaError_t launch_reorder(const double *pos, int64_t n, const Chunk *chunks, int n_chunks,
                            const int32_t *chunk_first, int ncl, const ClusterDev *cl,
                            double *part, double *bbox, unsigned long long *keys, uint32_t *vals,
-                           int64_t sort_n, int32_t *perm, cudaStream_t s, int *launches);
+                           int64_t sort_n, int64_t max_cluster, int32_t *perm, cudaStream_t s,
+                           int *launches);
 
 // Sets *flag = 1 if any of the n3 + n values is not finite.
 cudaError_t launch_check_finite(const double *acc, int64_t n3, const double *pot, int64_t n,

@@ -10,6 +10,10 @@
 // (10 bits per axis) with the cluster id in the high word, a bitonic sort of
 // (key, row) pairs (all pairs distinct, so the order is unique), then
 // perm[slot] = row for every real slot.
+//
+// When every cluster has at most kSmemSortMax particles (ensembles of small
+// systems) one CTA per cluster does all four steps in shared memory, sorting
+// (key << 32 | local index); that gives the same order as the global sort.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -188,6 +192,76 @@ __global__ void perm_kernel(int64_t n, const unsigned long long *__restrict__ ke
     }
 }
 
+constexpr int kSmemSortThreads = 1024;
+
+__global__ void __launch_bounds__(kSmemSortThreads)
+    cluster_reorder_kernel(const double *__restrict__ pos, int64_t n,
+                           const ClusterDev *__restrict__ cl, int32_t *__restrict__ perm,
+                           int pow2) {
+    extern __shared__ unsigned long long sk[];  // pow2 keys
+    __shared__ double red[kSmemSortThreads / 32][6];
+    __shared__ double box[6];
+    const ClusterDev d = cl[blockIdx.x];
+    if (d.n == 0) return;
+    double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int k = threadIdx.x; k < d.n; k += blockDim.x) {
+        const int64_t i = d.user_begin + k;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const double x = pos[q * n + i];
+            v[q] = fmin(v[q], x);
+            v[3 + q] = fmax(v[3 + q], x);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            v[q] = fmin(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+            v[3 + q] = fmax(v[3 + q], __shfl_xor_sync(0xffffffffu, v[3 + q], o));
+        }
+    if (threadIdx.x % 32 == 0)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) red[threadIdx.x / 32][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int q = threadIdx.x;
+        double r = red[0][q];
+        for (int w = 1; w < (int)(blockDim.x / 32); ++w) r = q < 3 ? fmin(r, red[w][q]) : fmax(r, red[w][q]);
+        box[q] = r;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < pow2; k += blockDim.x) {
+        unsigned long long key = ~0ull;
+        if (k < d.n) {
+            const int64_t i = d.user_begin + k;
+            const uint32_t m = (spread10(cell10(pos[i], box[0], box[3])) << 2) |
+                               (spread10(cell10(pos[n + i], box[1], box[4])) << 1) |
+                               spread10(cell10(pos[2 * n + i], box[2], box[5]));
+            key = ((unsigned long long)m << 32) | (uint32_t)k;
+        }
+        sk[k] = key;
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= pow2; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < pow2 / 2; t += blockDim.x) {
+                const int i = 2 * j * (t / j) + (t % j);
+                const int l = i + j;
+                const bool up = (i & kk) == 0;
+                const unsigned long long a = sk[i], b = sk[l];
+                if ((a > b) == up) {
+                    sk[i] = b;
+                    sk[l] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int k = threadIdx.x; k < d.n; k += blockDim.x)
+        perm[d.slot_begin + k] = (int32_t)(d.user_begin + (uint32_t)(sk[k] & 0xffffffffu));
+}
+
 int grid_cap(int64_t work, int threads) {
     int64_t g = (work + threads - 1) / threads;
     if (g > 152 * 16) g = 152 * 16;
@@ -197,10 +271,13 @@ int grid_cap(int64_t work, int threads) {
 
 }  // namespace
 
+bool reorder_in_smem(int64_t max_cluster) { return max_cluster <= kSmemSortMax; }
+
 cudaError_t launch_reorder(const double *pos, int64_t n, const Chunk *chunks, int n_chunks,
                            const int32_t *chunk_first, int ncl, const ClusterDev *cl,
                            double *part, double *bbox, unsigned long long *keys, uint32_t *vals,
-                           int64_t sort_n, int32_t *perm, cudaStream_t s, int *launches) {
+                           int64_t sort_n, int64_t max_cluster, int32_t *perm, cudaStream_t s,
+                           int *launches) {
     if (n <= 0 || n_chunks <= 0) return cudaSuccess;
     cudaError_t e;
 #define NB_CHECK()                             \
@@ -209,6 +286,19 @@ cudaError_t launch_reorder(const double *pos, int64_t n, const Chunk *chunks, in
         if (e != cudaSuccess) return e;        \
         if (launches) ++*launches;             \
     } while (0)
+    if (reorder_in_smem(max_cluster)) {
+        int pow2 = 1;
+        while (pow2 < max_cluster) pow2 <<= 1;
+        const size_t smem = sizeof(unsigned long long) * pow2;
+        e = cudaFuncSetAttribute(cluster_reorder_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        const int threads = pow2 / 2 < kSmemSortThreads ? (pow2 / 2 < 32 ? 32 : pow2 / 2)
+                                                         : kSmemSortThreads;
+        cluster_reorder_kernel<<<ncl, threads, smem, s>>>(pos, n, cl, perm, pow2);
+        NB_CHECK();
+        return cudaSuccess;
+    }
     bbox_chunk_kernel<<<n_chunks, kBoxThreads, 0, s>>>(pos, n, chunks, part);
     NB_CHECK();
     bbox_cluster_kernel<<<grid_cap(ncl, 128), 128, 0, s>>>(part, chunk_first, ncl, bbox);

@@ -247,3 +247,21 @@ def test_profile_counts_force_launches():
         ms, cnt = nb.nbody_profile_read(ctx, reset=True)
         assert cnt == 5 and ms > 0.0
         assert nb.nbody_kernel_launches(ctx) >= 10
+
+
+def test_reorder_paths_give_the_same_order():
+    # a context whose largest cluster exceeds the shared-memory sort limit takes
+    # the global bitonic path; a cluster's own results do not depend on the other
+    # clusters, so they must equal (bitwise) those of a context that holds only
+    # that cluster and takes the per-cluster shared-memory path
+    big = ic.plummer(20000, seed=31)
+    small = ic.plummer(3000, seed=32)
+    pos = np.concatenate([big[0], small[0]], axis=1)
+    mass = np.concatenate([big[2], small[2]])
+    offs = np.array([0, 20000, 23000])
+    tiles = (128, 2, 256, 1, 4)
+    a1, p1 = forces(pos, mass, [0.002, 0.004], offsets=offs, tiles=tiles, reorder_every=1)
+    a2, p2 = forces(small[0], small[2], 0.004, tiles=tiles, reorder_every=1)
+    assert np.array_equal(a1[:, 20000:], a2) and np.array_equal(p1[20000:], p2)
+    a3, p3 = forces(big[0], big[2], 0.002, tiles=tiles, reorder_every=1)
+    assert np.array_equal(a1[:, :20000], a3) and np.array_equal(p1[:20000], p3)
