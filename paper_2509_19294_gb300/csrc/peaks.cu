@@ -7,7 +7,9 @@
 //   * FP32: independent chains of paired FMA (__ffma2_rn), lane-operations.
 //   * MUFU: independent chains of rsqrt.approx.ftz.f32.
 //   * pair: the force kernel's own per-pair arithmetic (F32CKernel::body) on
-//           register-resident data, i.e. its ceiling without shared loads.
+//           register-resident data whose j operands change every iteration
+//           (4 extra paired ops per 8 pairs), i.e. a lower bound on its
+//           ceiling without shared loads.
 //   * FP64: independent chains of fma(double).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -103,7 +105,12 @@ __global__ void __launch_bounds__(kProbeThreads) pair_probe(int iters, float *si
     const long long t0 = clock64();
     for (int i = 0; i < iters; ++i) {
         PairK::body(xj, yj, zj, mj, e2, nx, ny, nz, ax, ay, az, ph);
-        xj = __fadd2_rn(xj, dj);  // one extra paired add per 2 * kPairP pairs
+        // every j operand changes each iteration, so nothing can be hoisted;
+        // these 4 paired adds per 2 * kPairP pairs make the figure a lower bound
+        xj = __fadd2_rn(xj, dj);
+        yj = __fadd2_rn(yj, dj);
+        zj = __fadd2_rn(zj, dj);
+        mj = __fmul2_rn(mj, make_float2(1.0001f, 0.9999f));
     }
     __syncthreads();
     const long long t1 = clock64();
