@@ -64,9 +64,29 @@ def dist_env():
     return rank, world, local
 
 
+def workload_name(n: int) -> str:
+    return (f"two Plummer spheres head-on, N={n} (2x{n // 2}), eps=1e-3, KDK dt=1e-4, "
+            "Morton reorder + pack + force + kick + diagnostics per step")
+
+
 def workload(n_each=N_EACH):
     from paper_2509_19294_gb300 import ic
     return ic.two_plummer(n_each, seed=SEED)
+
+
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The slowest rank's value (the bench times every rank and keeps the max)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: float, steps: int, world: int, seconds: float) -> float:
+    """Units processed by all ranks over the timed steps / the slowest rank's time."""
+    return units_per_rank_step * steps * world / seconds
 
 
 def host_cores():
@@ -234,10 +254,7 @@ def run_ours(args):
     ms_total = float(sum(step_ms))
     kern_ms, kern_n = nb.nbody_profile_read(ctx, reset=True)
     e_last = nb.nbody_energy(ctx, p, v, m, pot)[0]
-    if pg:
-        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, pg, device="cuda")
 
     # accuracy of the timed configuration: sampled rows against the FP64 oracle
     # (the state after the timed steps; rows computed one by one on the host)
@@ -343,14 +360,10 @@ def run_ours(args):
                 nb.nbody_step(ce, ph, vh, mh, ah, poth, DT, 1, dh)   # H2D, step, D2H, sync
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-        secs = t1 - t0
-        if pg:
-            t = torch.tensor([secs], dtype=torch.float64, device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            secs = float(t.item())
+        secs = max_over_ranks(t1 - t0, pg, device="cuda")
         bi = 8 * (3 * n + 3 * n + n + 3 * n + n)
         bo = 8 * (3 * n + 3 * n + 3 * n + n + 9)
-        e2e = {"value": pairs_per_step * args.steps * world / secs, "unit": UNIT,
+        e2e = {"value": whole_job_rate(pairs_per_step, args.steps, world, secs), "unit": UNIT,
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
     nb.nbody_destroy(ctx)
@@ -370,7 +383,7 @@ def run_ours(args):
             sm_max = float(json.load(f).get("sm_max_mhz", 2070.0))
     except (OSError, ValueError):
         sm_max = 2070.0
-    value = pairs_per_step * args.steps * world / (ms_total / 1e3)
+    value = whole_job_rate(pairs_per_step, args.steps, world, ms_total / 1e3)
     kern_avg_s = kern_ms / max(kern_n, 1) / 1e3
     achieved = pairs_per_step / kern_avg_s / 1e9
     peak_fp32 = FP32_LANES_PER_SM * sms * sm_max * 1e6 / FP32_OPS_PER_PAIR / 1e9
@@ -400,9 +413,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"two Plummer spheres head-on, N={n} (2x{n // 2}), eps=1e-3, "
-                               "KDK dt=1e-4, Morton reorder + pack + force + kick + diagnostics "
-                               "per step",
+        "config": {"workload": workload_name(n),
                    "n": n, "eps": EPS, "dt": DT, "seed": SEED,
                    "precision": "FP32 pairwise (MUFU rsqrt), Kahan-compensated FP32 tile sums, "
                                 "FP64 positions/velocities/reduction",
@@ -453,8 +464,11 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "two Plummer spheres head-on, N=1048576 (2x524288), eps=1e-3",
-                   "n": n, "eps": EPS, "seed": SEED, "parallelism": "host cores"},
+        "config": {"workload": workload_name(n), "n": n, "eps": EPS, "dt": DT, "seed": SEED,
+                   "parallelism": "host cores",
+                   "reference_step": "FP64 oracle forces of a bounded random sample of rows "
+                                     "against all N particles (the full O(N^2) step would take "
+                                     "~11 minutes on the host cores)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
