@@ -148,7 +148,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
@@ -159,6 +159,10 @@ class ClockSampler:
                     mx.append(float(parts[1]))
                 except ValueError:
                     continue
+                try:
+                    pw.append(float(parts[2]))
+                except ValueError:
+                    pass
                 for name, val in zip(self.NAMES, parts[4:8]):
                     if val.lower() == "active":
                         reasons.add(name)
@@ -166,7 +170,8 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_mean": statistics.fmean(pw) if pw else None,
+                "power_w_max": max(pw) if pw else None}
 
 
 def traffic_for_current_kernel():
@@ -405,6 +410,15 @@ def run_ours(args):
                                            / (FP32_LANES_PER_SM / FP32_OPS_PER_PAIR))
     if fp64 is not None:
         fp64["ratio_f32c_over_f64"] = value / fp64["value"]
+    # energy to solution (the paper's second metric): GPU board power sampled by
+    # nvidia-smi every 200 ms during the timed steps, times the timed wall time
+    energy = None
+    if clocks and clocks.get("power_w_mean"):
+        joules = clocks["power_w_mean"] * (wall1 - wall0)
+        energy = {"gpu_power_w_mean": clocks["power_w_mean"], "gpu_power_w_max": clocks["power_w_max"],
+                  "joules_per_step": joules / args.steps,
+                  "interactions_per_joule": pairs_per_step * args.steps / joules,
+                  "scope": "GPU board power only (nvidia-smi power.draw), host excluded"}
     if ensemble is not None:
         ek = ensemble["pairs_per_step"] / (ensemble["force_kernel_ms"] / 1e3) / 1e9
         ensemble["roofline_frac"] = ek / peak
@@ -427,6 +441,7 @@ def run_ours(args):
         "e2e": e2e,
         "fp64_gpu": fp64,
         "ensemble": ensemble,
+        "energy": energy,
         "accuracy": accuracy,
         "clocks": clocks,
         "wall_s_timed": wall1 - wall0,

@@ -14,6 +14,10 @@ no fast-math).  This module only builds it and marshals numpy arrays:
 * ``kdk``          -- kick-drift-kick leapfrog in FP64 (the paper keeps the
   integration in double precision on the host, Sec. 3).
 * ``energy``       -- K, W, E, P, L.
+* ``forces_jerk``  -- a_i, its time derivative (jerk) and phi_i, which the paper
+  computes together (Sec. 3).
+* ``hermite``      -- the fourth-order Hermite predictor-corrector integrator
+  that uses the jerk (shared time step).
 
 Layouts follow the C ABI: positions/velocities/accelerations are ``[3, n]``
 float64 arrays, masses and potentials ``[n]``.
@@ -78,6 +82,10 @@ class Oracle:
         lib.oracle_energy.restype = None
         lib.oracle_kdk.argtypes = [i64, vp, vp, vp, d, d, d, i64, vp, vp, ctypes.c_int, vp]
         lib.oracle_kdk.restype = None
+        lib.oracle_forces_jerk.argtypes = [i64, vp, vp, vp, d, d, vp, vp, vp]
+        lib.oracle_forces_jerk.restype = None
+        lib.oracle_hermite.argtypes = [i64, vp, vp, vp, d, d, d, i64, vp, vp, vp, ctypes.c_int, vp]
+        lib.oracle_hermite.restype = None
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
         self.lib = lib
@@ -141,6 +149,44 @@ class Oracle:
                             int(nsteps), _p(acc), _p(pot), int(have),
                             _p(dg) if dg is not None else None)
         return pos, vel, acc, pot, dg
+
+
+def _forces_jerk(self, pos, vel, mass, eps: float, G: float = 1.0):
+    """Return (acc[3, n], jerk[3, n], pot[n]) in FP64."""
+    mass = _c(mass)
+    n = mass.shape[0]
+    pos = _c(pos, (3, n))
+    vel = _c(vel, (3, n))
+    acc = np.empty((3, n), np.float64)
+    jerk = np.empty((3, n), np.float64)
+    pot = np.empty(n, np.float64)
+    self.lib.oracle_forces_jerk(n, _p(pos), _p(vel), _p(mass), float(eps), float(G), _p(acc),
+                                _p(jerk), _p(pot))
+    return acc, jerk, pot
+
+
+def _hermite(self, pos, vel, mass, eps: float, dt: float, nsteps: int, G: float = 1.0,
+             diag: bool = False):
+    """Advance copies of (pos, vel) by ``nsteps`` Hermite steps.
+
+    Returns (pos, vel, acc, jerk, pot, diag[nsteps + 1, 9] or None).
+    """
+    mass = _c(mass)
+    n = mass.shape[0]
+    pos = _c(pos, (3, n)).copy()
+    vel = _c(vel, (3, n)).copy()
+    acc = np.empty((3, n), np.float64)
+    jerk = np.empty((3, n), np.float64)
+    pot = np.empty(n, np.float64)
+    dg = np.empty((nsteps + 1, 9), np.float64) if diag else None
+    self.lib.oracle_hermite(n, _p(pos), _p(vel), _p(mass), float(eps), float(G), float(dt),
+                            int(nsteps), _p(acc), _p(jerk), _p(pot), 0,
+                            _p(dg) if dg is not None else None)
+    return pos, vel, acc, jerk, pot, dg
+
+
+Oracle.forces_jerk = _forces_jerk
+Oracle.hermite = _hermite
 
 
 def default() -> Oracle:

@@ -31,6 +31,19 @@
  * Diagnostics: K = 1/2 sum m |v|^2, W = 1/2 sum m phi, E = K + W,
  * P = sum m v, L = sum m (x cross v).
  *
+ * Jerk (the time derivative of the acceleration, which the paper computes
+ * together with it, Sec. 3): with r = r_j - r_i, v = v_j - v_i, d2 = |r|^2 + eps^2,
+ *
+ *     jerk_i = G sum_{j != i} m_j [ v / d2^(3/2) - 3 (r . v) r / d2^(5/2) ]
+ *
+ * and the fourth-order Hermite predictor-corrector scheme that uses it
+ * (Makino & Aarseth 1992), with one shared time step:
+ *
+ *     x_p = x + v dt + a dt^2/2 + j dt^3/6,   v_p = v + a dt + j dt^2/2
+ *     a1, j1 <- forces and jerks at (x_p, v_p)
+ *     v1 = v + (a + a1) dt/2 + (j - j1) dt^2/12
+ *     x1 = x + (v + v1) dt/2 + (a - a1) dt^2/12
+ *
  * Layout: positions, velocities and accelerations are structure-of-arrays
  * [3][n] (x row, then y row, then z row), masses and potentials are [n].
  */
@@ -169,4 +182,81 @@ void oracle_kdk(int64_t n, double *pos, double *vel, const double *mass, double 
         for (int64_t q = 0; q < 3 * n; ++q) vel[q] += h * acc[q]; /* kick */
         if (diag) oracle_energy(n, pos, vel, mass, pot, diag + 9 * (s + 1));
     }
+}
+
+/* Acceleration, jerk and potential on particle i (the definitions above). */
+static void oracle_one_jerk(int64_t n, const double *pos, const double *vel, const double *mass,
+                            double eps, double G, int64_t i, double out[7]) {
+    const double *x = pos, *y = pos + n, *z = pos + 2 * n;
+    const double *vx = vel, *vy = vel + n, *vz = vel + 2 * n;
+    csum s[7] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    const double eps2 = eps * eps;
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        double rx = x[j] - x[i], ry = y[j] - y[i], rz = z[j] - z[i];
+        double ux = vx[j] - vx[i], uy = vy[j] - vy[i], uz = vz[j] - vz[i];
+        double d2 = rx * rx + ry * ry + rz * rz + eps2;
+        if (d2 == 0.0) continue;
+        double d = sqrt(d2);
+        double d3 = d2 * d;      /* d2^(3/2) */
+        double d5 = d3 * d2;     /* d2^(5/2) */
+        double rv = rx * ux + ry * uy + rz * uz;
+        csum_add(&s[0], mass[j] * rx / d3);
+        csum_add(&s[1], mass[j] * ry / d3);
+        csum_add(&s[2], mass[j] * rz / d3);
+        csum_add(&s[3], mass[j] * (ux / d3 - 3.0 * rv * rx / d5));
+        csum_add(&s[4], mass[j] * (uy / d3 - 3.0 * rv * ry / d5));
+        csum_add(&s[5], mass[j] * (uz / d3 - 3.0 * rv * rz / d5));
+        csum_add(&s[6], mass[j] / d);
+    }
+    for (int k = 0; k < 6; ++k) out[k] = G * csum_get(&s[k]);
+    out[6] = -G * csum_get(&s[6]);
+}
+
+/* acc, jerk: [3][n]; pot: [n] (pot may be NULL). */
+void oracle_forces_jerk(int64_t n, const double *pos, const double *vel, const double *mass,
+                        double eps, double G, double *acc, double *jerk, double *pot) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double o[7];
+        oracle_one_jerk(n, pos, vel, mass, eps, G, i, o);
+        for (int d = 0; d < 3; ++d) {
+            acc[d * n + i] = o[d];
+            jerk[d * n + i] = o[3 + d];
+        }
+        if (pot) pot[i] = o[6];
+    }
+}
+
+/*
+ * nsteps Hermite steps in place on pos and vel; acc/jerk/pot as in oracle_kdk
+ * (computed first unless have != 0), diag as in oracle_kdk.
+ */
+void oracle_hermite(int64_t n, double *pos, double *vel, const double *mass, double eps, double G,
+                    double dt, int64_t nsteps, double *acc, double *jerk, double *pot, int have,
+                    double *diag) {
+    if (!have) oracle_forces_jerk(n, pos, vel, mass, eps, G, acc, jerk, pot);
+    if (diag) oracle_energy(n, pos, vel, mass, pot, diag);
+    double *xp = malloc(sizeof(double) * 3 * n), *vp = malloc(sizeof(double) * 3 * n);
+    double *a1 = malloc(sizeof(double) * 3 * n), *j1 = malloc(sizeof(double) * 3 * n);
+    const double dt2 = dt * dt, dt3 = dt2 * dt;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        for (int64_t q = 0; q < 3 * n; ++q) {  /* predictor */
+            xp[q] = pos[q] + vel[q] * dt + acc[q] * dt2 / 2.0 + jerk[q] * dt3 / 6.0;
+            vp[q] = vel[q] + acc[q] * dt + jerk[q] * dt2 / 2.0;
+        }
+        oracle_forces_jerk(n, xp, vp, mass, eps, G, a1, j1, pot);
+        for (int64_t q = 0; q < 3 * n; ++q) {  /* corrector */
+            double v1 = vel[q] + (acc[q] + a1[q]) * dt / 2.0 + (jerk[q] - j1[q]) * dt2 / 12.0;
+            pos[q] = pos[q] + (vel[q] + v1) * dt / 2.0 + (acc[q] - a1[q]) * dt2 / 12.0;
+            vel[q] = v1;
+            acc[q] = a1[q];
+            jerk[q] = j1[q];
+        }
+        if (diag) oracle_energy(n, pos, vel, mass, pot, diag + 9 * (s + 1));
+    }
+    free(xp);
+    free(vp);
+    free(a1);
+    free(j1);
 }

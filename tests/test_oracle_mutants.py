@@ -15,6 +15,7 @@ import tempfile
 import pytest
 
 import oracle as oracle_pkg
+from tests import test_oracle_jerk_pins as jpins
 from tests import test_oracle_pins as pins
 
 MUTANTS = {
@@ -24,7 +25,7 @@ MUTANTS = {
     "flipped_separation": ("double dx = x[j] - x[i];", "double dx = x[i] - x[j];"),
     "transposed_operand": ("double dy = y[j] - y[i];", "double dy = y[j] - x[i];"),
     "mass_of_i": ("csum_add(&ax, mass[j] * dx / r3);", "csum_add(&ax, mass[i] * dx / r3);"),
-    "self_term_kept": ("if (j == i) continue;", ""),
+    "self_term_kept": ("if (j == i) continue; /* the sum excludes j = i */", ""),
     "potential_sign": ("out[3] = -G * csum_get(&ph);", "out[3] = G * csum_get(&ph);"),
     "potential_unsoftened": ("csum_add(&ph, mass[j] / r);",
                              "csum_add(&ph, mass[j] / sqrt(dx * dx + dy * dy + dz * dz));"),
@@ -36,6 +37,16 @@ MUTANTS = {
                               "csum_add(&l[2], m * (y * vx - x * vy));"),
     "dropped_term": ("double r2 = dx * dx + dy * dy + dz * dz + eps2;",
                      "double r2 = dx * dx + dy * dy + eps2;"),
+    "jerk_factor_three": ("csum_add(&s[3], mass[j] * (ux / d3 - 3.0 * rv * rx / d5));",
+                          "csum_add(&s[3], mass[j] * (ux / d3 - rv * rx / d5));"),
+    "jerk_sign": ("csum_add(&s[4], mass[j] * (uy / d3 - 3.0 * rv * ry / d5));",
+                  "csum_add(&s[4], mass[j] * (uy / d3 + 3.0 * rv * ry / d5));"),
+    "jerk_exponent": ("double d5 = d3 * d2;     /* d2^(5/2) */", "double d5 = d3 * d;"),
+    "jerk_velocity_order": ("double ux = vx[j] - vx[i], uy = vy[j] - vy[i], uz = vz[j] - vz[i];",
+                            "double ux = vx[i] - vx[j], uy = vy[i] - vy[j], uz = vz[i] - vz[j];"),
+    "jerk_self_term_kept": ("        if (j == i) continue;\n        double rx", "        double rx"),
+    "hermite_corrector": ("(jerk[q] - j1[q]) * dt2 / 12.0;", "(jerk[q] - j1[q]) * dt2 / 6.0;"),
+    "hermite_predictor": ("+ jerk[q] * dt3 / 6.0;", "+ 0.0 * dt3;"),
 }
 
 
@@ -61,6 +72,11 @@ def _pin_calls(orc):
         lambda: pins.test_kdk_time_reversible(orc),
         lambda: pins.test_energy_of_static_pair(orc),
         lambda: pins.test_plummer_virial_and_henon_energy(orc),
+        lambda: jpins.test_two_body_jerk_closed_forms(orc, 0.0),
+        lambda: jpins.test_two_body_jerk_closed_forms(orc, 0.7),
+        lambda: jpins.test_jerk_is_the_time_derivative_of_the_acceleration(orc, 0.05),
+        lambda: jpins.test_jerk_newton_third_law_and_scaling(orc),
+        lambda: jpins.test_hermite_is_fourth_order(orc),
     ]
     return calls
 
