@@ -51,6 +51,9 @@ EPS = 1.0e-3
 DT = 1.0e-4
 SEED = 5
 FP32_OPS_PER_PAIR = 13      # 3 add (dx), 3 fma (r^2), 3 mul, 1 add (phi), 3 fma (a)
+JERK_OPS_PER_PAIR = 27      # + 3 add (u), 3 (r.u), 2 mul (beta), 6 fma (jerk)
+PAPER_N = 102400            # the paper's run: 102 400 particles, ten time cycles (Sec. 4)
+PAPER_SECONDS = {"wormhole_n300": 301.40, "cpu_2x_epyc_9124_32_threads": 672.90}
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
@@ -344,6 +347,42 @@ def run_ours(args):
                     "tiles": {"block": et[0], "p": et[1], "tj": et[2], "split": et[3],
                               "ctas_per_sm": et[4]}}
 
+    # the paper's workload size with its force payload (acceleration + jerk):
+    # N = 102 400 Plummer sphere, ten fourth-order Hermite steps
+    paper_scale = None
+    if rank == 0 and not args.no_paper_scale:
+        from paper_2509_19294_gb300 import ic
+        pp_, pv_, pm_ = ic.plummer(PAPER_N, seed=6)
+        with nb.nbody_init(PAPER_N, 1e-3, mode=nb.NBODY_F32C, reorder_every=1,
+                           flags=nb.NBODY_FLAG_PROFILE) as cj:
+            p_, v_, m_ = (torch.from_numpy(x.copy()).cuda() for x in (pp_, pv_, pm_))
+            a_ = torch.empty((3, PAPER_N), dtype=torch.float64, device="cuda")
+            j_ = torch.empty((3, PAPER_N), dtype=torch.float64, device="cuda")
+            po_ = torch.empty(PAPER_N, dtype=torch.float64, device="cuda")
+            nb.nbody_forces_jerk(cj, p_, v_, m_, a_, j_, po_)
+            nb.nbody_step_hermite(cj, p_, v_, m_, a_, j_, po_, 1e-4, 3)   # warm-up, graph capture
+            torch.cuda.synchronize()
+            nb.nbody_profile_read(cj, reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nb.nbody_step_hermite(cj, p_, v_, m_, a_, j_, po_, 1e-4, 10)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            jms, jn = nb.nbody_profile_read(cj, reset=True)
+            jt = nb.nbody_get_jerk_tiles(cj)
+        pairs_j = float(PAPER_N) ** 2
+        paper_scale = {
+            "workload": "Plummer sphere N=102400 (seed 6), eps=1e-3, 10 Hermite steps dt=1e-4, "
+                        "acceleration + jerk each step (Morton reorder, pack, predictor, "
+                        "force+jerk kernel, corrector)",
+            "seconds_10_steps": sec, "interactions_per_s": pairs_j * 10 / sec,
+            "force_jerk_kernel_ms": jms / max(jn, 1),
+            "tiles": {"block": jt[0], "p": jt[1], "tj": jt[2], "split": jt[3], "ctas_per_sm": jt[4]},
+            "paper_time_to_solution_s": PAPER_SECONDS,
+            "note": "context only: the paper's times are whole-application runs of its own code "
+                    "and initial conditions on other hardware (Sec. 4)"}
+
     # end to end through the same C ABI call with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -419,6 +458,12 @@ def run_ours(args):
                   "joules_per_step": joules / args.steps,
                   "interactions_per_joule": pairs_per_step * args.steps / joules,
                   "scope": "GPU board power only (nvidia-smi power.draw), host excluded"}
+    if paper_scale is not None:
+        jpeak = FP32_LANES_PER_SM * sms * sm_max * 1e6 / JERK_OPS_PER_PAIR / 1e9
+        jach = float(PAPER_N) ** 2 / (paper_scale["force_jerk_kernel_ms"] / 1e3) / 1e9
+        paper_scale["jerk_roofline"] = {"achieved": jach, "peak": jpeak, "unit": "Ginteractions/s",
+                                        "frac": jach / jpeak,
+                                        "basis": f"{JERK_OPS_PER_PAIR} FP32 ops per pair"}
     if ensemble is not None:
         ek = ensemble["pairs_per_step"] / (ensemble["force_kernel_ms"] / 1e3) / 1e9
         ensemble["roofline_frac"] = ek / peak
@@ -441,6 +486,7 @@ def run_ours(args):
         "e2e": e2e,
         "fp64_gpu": fp64,
         "ensemble": ensemble,
+        "paper_scale": paper_scale,
         "energy": energy,
         "accuracy": accuracy,
         "clocks": clocks,
@@ -503,6 +549,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-paper-scale", action="store_true")
     ap.add_argument("--n-each", type=int, default=N_EACH,
                     help="particles per sphere (default 524288: the N=1M workload)")
     ap.add_argument("--tiles", default=None,

@@ -152,6 +152,41 @@ int nbody_step(nbody_ctx *ctx, double *pos, double *vel, const double *mass, dou
                double *pot, double dt, int32_t nsteps, double *diag, void *stream);
 
 /*
+ * Acceleration, jerk (its time derivative) and potential of every particle.
+ * The paper's device kernel computes the acceleration together with the jerk
+ * (Sec. 3); with r = r_j - r_i, u = v_j - v_i and d2 = |r|^2 + eps^2:
+ *     jerk_i = G sum_{j != i} m_j [ u / d2^(3/2) - 3 (r . u) r / d2^(5/2) ]
+ *   pos, vel in : double[3][n]     mass in : double[n]
+ *   acc, jerk out: double[3][n]    pot  out: double[n], or NULL
+ * In NBODY_F32C mode velocities, like positions, are FP32 offsets from FP64
+ * tile means; the call uses its own tile geometry (built on first use, shape
+ * set by nbody_set_jerk_tiles or chosen from n).
+ */
+int nbody_forces_jerk(nbody_ctx *ctx, const double *pos, const double *vel, const double *mass,
+                      double *acc, double *jerk, double *pot, void *stream);
+
+/*
+ * nsteps >= 0 fourth-order Hermite predictor-corrector steps of size dt, one
+ * shared step for all particles:
+ *   x_p = x + v dt + a dt^2/2 + j dt^3/6,  v_p = v + a dt + j dt^2/2
+ *   a1, j1, phi <- nbody_forces_jerk(x_p, v_p)
+ *   v <- v + (a + a1) dt/2 + (j - j1) dt^2/12,  x <- x + (v_old + v) dt/2 + (a - a1) dt^2/12
+ *   pos, vel, acc, jerk in/out (acc, jerk on entry at the current state, e.g.
+ *   from nbody_forces_jerk); pot out (at the predicted positions of the last
+ *   step); diag as in nbody_step (W from that pot).  Graph-replayed unless
+ *   NBODY_FLAG_NO_GRAPH.
+ */
+int nbody_step_hermite(nbody_ctx *ctx, double *pos, double *vel, const double *mass, double *acc,
+                       double *jerk, double *pot, double dt, int32_t nsteps, double *diag,
+                       void *stream);
+
+/* Tile shape of the acceleration + jerk kernel in use (zeros before its first use or in F64). */
+int nbody_get_jerk_tiles(const nbody_ctx *ctx, nbody_tiles *out);
+
+/* Choose the acceleration + jerk kernel's tile shape (rebuilds its geometry). */
+int nbody_set_jerk_tiles(nbody_ctx *ctx, const nbody_tiles *tiles);
+
+/*
  * Per-cluster diagnostics, FP64, fixed summation order (bitwise reproducible):
  *   out_host[c*9 + 0..8] = K, W, E, Px, Py, Pz, Lx, Ly, Lz with
  *   K = 1/2 sum m|v|^2, W = 1/2 sum m phi, E = K + W, P = sum m v, L = sum m x cross v.

@@ -45,7 +45,8 @@ NBODY_FLAG_NO_GRAPH = 8
 EXPORTED = ("nbody_init", "nbody_destroy", "nbody_forces", "nbody_step", "nbody_energy",
             "nbody_tune", "nbody_get_tiles", "nbody_tiles_supported", "nbody_profile_read",
             "nbody_kernel_launches", "nbody_strerror", "nbody_last_error_message",
-            "nbody_forces_noalloc", "nbody_measure_pipes")
+            "nbody_forces_noalloc", "nbody_measure_pipes", "nbody_forces_jerk",
+            "nbody_step_hermite", "nbody_get_jerk_tiles", "nbody_set_jerk_tiles")
 
 
 class NBodyTiles(ctypes.Structure):
@@ -110,6 +111,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.nbody_last_error_message.restype = ctypes.c_char_p
         lib.nbody_forces_noalloc.argtypes = [i64, vp, vp, d, d, vp, vp, vp]
         lib.nbody_forces_noalloc.restype = ctypes.c_int
+        lib.nbody_forces_jerk.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.nbody_forces_jerk.restype = ctypes.c_int
+        lib.nbody_step_hermite.argtypes = [vp, vp, vp, vp, vp, vp, vp, d, i32, vp, vp]
+        lib.nbody_step_hermite.restype = ctypes.c_int
+        lib.nbody_get_jerk_tiles.argtypes = [vp, ctypes.POINTER(NBodyTiles)]
+        lib.nbody_get_jerk_tiles.restype = ctypes.c_int
+        lib.nbody_set_jerk_tiles.argtypes = [vp, ctypes.POINTER(NBodyTiles)]
+        lib.nbody_set_jerk_tiles.restype = ctypes.c_int
         lib.nbody_measure_pipes.argtypes = [ctypes.POINTER(d), ctypes.c_int]
         lib.nbody_measure_pipes.restype = ctypes.c_int
         _lib = lib
@@ -244,6 +253,43 @@ def nbody_step(ctx: Context, pos, vel, mass, acc, pot, dt: float, nsteps: int, d
                            _ptr(diag, (int(nsteps), ctx.n_clusters, 9), "diag", keep),
                            _stream(stream))
     _check(ctx, rc, "nbody_step")
+
+
+def nbody_forces_jerk(ctx: Context, pos, vel, mass, acc, jerk, pot=None, stream=None) -> None:
+    """Acceleration, jerk and potential (see nbody_forces_jerk in nbody.h)."""
+    n = ctx.n
+    keep = []
+    rc = load().nbody_forces_jerk(ctx.handle, _ptr(pos, (3, n), "pos", keep),
+                                  _ptr(vel, (3, n), "vel", keep), _ptr(mass, (n,), "mass", keep),
+                                  _ptr(acc, (3, n), "acc", keep), _ptr(jerk, (3, n), "jerk", keep),
+                                  _ptr(pot, (n,), "pot", keep), _stream(stream))
+    _check(ctx, rc, "nbody_forces_jerk")
+
+
+def nbody_step_hermite(ctx: Context, pos, vel, mass, acc, jerk, pot, dt: float, nsteps: int,
+                       diag=None, stream=None) -> None:
+    """Fourth-order Hermite steps (see nbody_step_hermite in nbody.h)."""
+    n = ctx.n
+    keep = []
+    rc = load().nbody_step_hermite(ctx.handle, _ptr(pos, (3, n), "pos", keep),
+                                   _ptr(vel, (3, n), "vel", keep), _ptr(mass, (n,), "mass", keep),
+                                   _ptr(acc, (3, n), "acc", keep), _ptr(jerk, (3, n), "jerk", keep),
+                                   _ptr(pot, (n,), "pot", keep), float(dt), int(nsteps),
+                                   _ptr(diag, (int(nsteps), ctx.n_clusters, 9), "diag", keep),
+                                   _stream(stream))
+    _check(ctx, rc, "nbody_step_hermite")
+
+
+def nbody_get_jerk_tiles(ctx: Context):
+    t = NBodyTiles()
+    _check(ctx, load().nbody_get_jerk_tiles(ctx.handle, ctypes.byref(t)), "nbody_get_jerk_tiles")
+    return (t.block, t.p, t.tj, t.split, t.ctas_per_sm)
+
+
+def nbody_set_jerk_tiles(ctx: Context, tiles) -> None:
+    t = tuple(tiles) + (0,) * (5 - len(tiles))
+    tt = NBodyTiles(*[int(x) for x in t])
+    _check(ctx, load().nbody_set_jerk_tiles(ctx.handle, ctypes.byref(tt)), "nbody_set_jerk_tiles")
 
 
 def nbody_energy(ctx: Context, pos, vel, mass, pot, stream=None) -> np.ndarray:

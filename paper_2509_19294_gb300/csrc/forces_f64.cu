@@ -65,11 +65,71 @@ __global__ void __launch_bounds__(kF64Block) forces_f64_kernel(const F64Params p
     }
 }
 
+// Acceleration, jerk and potential in FP64 (same structure; velocities from velin).
+__global__ void __launch_bounds__(kF64Block) forces_jerk_f64_kernel(const F64Params p) {
+    __shared__ double sj[7][kF64Block];
+    const int2 blk = p.blocks[blockIdx.x];
+    const ClusterDev cl = p.cl[blk.x];
+    const int li = blk.y + threadIdx.x;
+    const bool active = li < cl.n;
+    const int64_t i = cl.user_begin + (active ? li : 0);
+    const double xi = p.pos[i], yi = p.pos[p.n + i], zi = p.pos[2 * p.n + i];
+    const double vxi = p.velin[i], vyi = p.velin[p.n + i], vzi = p.velin[2 * p.n + i];
+    double ax = 0.0, ay = 0.0, az = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, ph = 0.0;
+    for (int j0 = 0; j0 < cl.n; j0 += kF64Block) {
+        const int lj = j0 + threadIdx.x;
+        __syncthreads();
+        if (lj < cl.n) {
+            const int64_t j = cl.user_begin + lj;
+            sj[0][threadIdx.x] = p.pos[j];
+            sj[1][threadIdx.x] = p.pos[p.n + j];
+            sj[2][threadIdx.x] = p.pos[2 * p.n + j];
+            sj[3][threadIdx.x] = p.mass[j];
+            sj[4][threadIdx.x] = p.velin[j];
+            sj[5][threadIdx.x] = p.velin[p.n + j];
+            sj[6][threadIdx.x] = p.velin[2 * p.n + j];
+        }
+        __syncthreads();
+        const int cnt = min(kF64Block, cl.n - j0);
+        for (int k = 0; k < cnt; ++k) {
+            const double dx = sj[0][k] - xi, dy = sj[1][k] - yi, dz = sj[2][k] - zi;
+            const double ux = sj[4][k] - vxi, uy = sj[5][k] - vyi, uz = sj[6][k] - vzi;
+            const double r2 = dx * dx + dy * dy + dz * dz + cl.eps2;
+            const bool skip = (j0 + k == li) || !(r2 > 0.0);
+            const double s = skip ? 0.0 : rsqrt(r2);
+            const double ms = sj[3][k] * s;
+            const double s2 = s * s;
+            const double w3 = ms * s2;
+            const double beta = -3.0 * (dx * ux + dy * uy + dz * uz) * s2;
+            ph += ms;
+            ax += w3 * dx;
+            ay += w3 * dy;
+            az += w3 * dz;
+            jx += w3 * (ux + beta * dx);
+            jy += w3 * (uy + beta * dy);
+            jz += w3 * (uz + beta * dz);
+        }
+    }
+    if (!active) return;
+    p.acc[i] = p.G * ax;
+    p.acc[p.n + i] = p.G * ay;
+    p.acc[2 * p.n + i] = p.G * az;
+    p.jerk[i] = p.G * jx;
+    p.jerk[p.n + i] = p.G * jy;
+    p.jerk[2 * p.n + i] = p.G * jz;
+    if (p.pot) p.pot[i] = -p.G * ph;
+}
+
 }  // namespace
 
 cudaError_t launch_f64(int grid, const F64Params &prm, cudaStream_t s) {
     if (grid <= 0) return cudaSuccess;
-    forces_f64_kernel<<<grid, kF64Block, 0, s>>>(prm);
+    if (prm.jerk) {
+        if (!prm.velin) return cudaErrorInvalidValue;
+        forces_jerk_f64_kernel<<<grid, kF64Block, 0, s>>>(prm);
+    } else {
+        forces_f64_kernel<<<grid, kF64Block, 0, s>>>(prm);
+    }
     return cudaGetLastError();
 }
 

@@ -89,6 +89,84 @@ __global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(const PackParams 
     }
 }
 
+// Velocity half of the jerk path's packing (one warp per tile, as pack_kernel).
+__global__ void __launch_bounds__(kPackWarps * 32)
+    pack_vel_kernel(const double *__restrict__ vel, const int32_t *__restrict__ perm,
+                    const ClusterDev *__restrict__ cls, const int32_t *__restrict__ tile_cluster,
+                    int tc, int64_t n, int n_tiles, float *pvx, float *pvy, float *pvz,
+                    float4 *vchl) {
+    const int lane = threadIdx.x % 32;
+    const int t = blockIdx.x * kPackWarps + threadIdx.x / 32;
+    if (t >= n_tiles) return;
+    const ClusterDev cl = cls[tile_cluster[t]];
+    const int base = t * tc;
+    const int per = tc / 32;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int r = 0; r < per; ++r) {
+        const int slot = base + lane + 32 * r;
+        if (slot - cl.slot_begin < cl.n) {
+            const int64_t u = perm[slot];
+            s[0] += vel[u];
+            s[1] += vel[n + u];
+            s[2] += vel[2 * n + u];
+            s[3] += 1.0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    const double cnt = s[3] > 0.0 ? s[3] : 1.0;
+    const double cx = s[0] / cnt, cy = s[1] / cnt, cz = s[2] / cnt;
+#pragma unroll 4
+    for (int r = 0; r < per; ++r) {
+        const int slot = base + lane + 32 * r;
+        if (slot - cl.slot_begin < cl.n) {
+            const int64_t u = perm[slot];
+            pvx[slot] = (float)(vel[u] - cx);
+            pvy[slot] = (float)(vel[n + u] - cy);
+            pvz[slot] = (float)(vel[2 * n + u] - cz);
+        } else {
+            pvx[slot] = pvy[slot] = pvz[slot] = 0.0f;
+        }
+    }
+    if (lane == 0) {
+        const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
+        vchl[2 * t + 0] = make_float4(hx, hy, hz, 0.0f);
+        vchl[2 * t + 1] = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), 0.0f);
+    }
+}
+
+__global__ void hermite_predict_kernel(int64_t n3, const double *__restrict__ pos,
+                                       const double *__restrict__ vel,
+                                       const double *__restrict__ acc,
+                                       const double *__restrict__ jerk, double dt,
+                                       double *__restrict__ xp, double *__restrict__ vp) {
+    const double dt2 = dt * dt, dt3 = dt2 * dt;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n3;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        xp[q] = pos[q] + vel[q] * dt + acc[q] * dt2 / 2.0 + jerk[q] * dt3 / 6.0;
+        vp[q] = vel[q] + acc[q] * dt + jerk[q] * dt2 / 2.0;
+    }
+}
+
+__global__ void hermite_correct_kernel(int64_t n3, double *__restrict__ pos,
+                                       double *__restrict__ vel, double *__restrict__ acc,
+                                       double *__restrict__ jerk, const double *__restrict__ a1,
+                                       const double *__restrict__ j1, double dt) {
+    const double dt2 = dt * dt;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n3;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const double a0 = acc[q], j0 = jerk[q], v0 = vel[q];
+        const double v1 = v0 + (a0 + a1[q]) * dt / 2.0 + (j0 - j1[q]) * dt2 / 12.0;
+        pos[q] = pos[q] + (v0 + v1) * dt / 2.0 + (a0 - a1[q]) * dt2 / 12.0;
+        vel[q] = v1;
+        acc[q] = a1[q];
+        jerk[q] = j1[q];
+    }
+}
+
 // v += half_dt * a; x += dt * v over the 3n entries of the SoA arrays.
 __global__ void kick_drift_kernel(int64_t n3, double *__restrict__ pos, double *__restrict__ vel,
                                   const double *__restrict__ acc, double half_dt, double dt) {
@@ -176,6 +254,31 @@ cudaError_t launch_pack(int n_tiles, const PackParams &prm, cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
     if (prm.tc % 32 != 0) return cudaErrorInvalidValue;
     pack_kernel<<<(n_tiles + kPackWarps - 1) / kPackWarps, kPackWarps * 32, 0, s>>>(prm, n_tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_vel(int n_tiles, const double *vel, const int32_t *perm,
+                            const ClusterDev *cl, const int32_t *tile_cluster, int tc, int64_t n,
+                            float *pvx, float *pvy, float *pvz, float4 *vchl, cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
+    if (tc % 32 != 0) return cudaErrorInvalidValue;
+    pack_vel_kernel<<<(n_tiles + kPackWarps - 1) / kPackWarps, kPackWarps * 32, 0, s>>>(
+        vel, perm, cl, tile_cluster, tc, n, n_tiles, pvx, pvy, pvz, vchl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hermite_predict(int64_t n3, const double *pos, const double *vel,
+                                   const double *acc, const double *jerk, double dt, double *xp,
+                                   double *vp, cudaStream_t s) {
+    if (n3 <= 0) return cudaSuccess;
+    hermite_predict_kernel<<<grid_for(n3, 256), 256, 0, s>>>(n3, pos, vel, acc, jerk, dt, xp, vp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hermite_correct(int64_t n3, double *pos, double *vel, double *acc, double *jerk,
+                                   const double *a1, const double *j1, double dt, cudaStream_t s) {
+    if (n3 <= 0) return cudaSuccess;
+    hermite_correct_kernel<<<grid_for(n3, 256), 256, 0, s>>>(n3, pos, vel, acc, jerk, a1, j1, dt);
     return cudaGetLastError();
 }
 

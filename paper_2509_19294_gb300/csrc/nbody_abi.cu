@@ -24,7 +24,8 @@ namespace {
 constexpr int kProfSlots = 2;
 
 struct GraphEntry {
-    const void *pos, *vel, *mass, *acc, *pot, *diag;
+    const void *pos, *vel, *mass, *acc, *pot, *diag, *jerk;
+    int kind;  // 0 = KDK leapfrog step, 1 = Hermite step
     uint64_t dt_bits;
     int reorder;
     int slot;
@@ -35,6 +36,25 @@ struct GraphEntry {
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+};
+
+// Acceleration + jerk path: its own tile geometry, queue and packed positions
+// and velocities (built on first use), plus the Hermite step's scratch.
+struct JerkPath {
+    bool built = false;
+    nbody_tiles tiles{0, 0, 0, 0, 0};
+    int tc = 0, grid = 0, n_items = 0, n_tiles = 0;
+    int64_t n_pad = 0;
+    ClusterDev *dcl = nullptr;
+    int32_t *tile_cluster = nullptr;
+    Item *items = nullptr;
+    int *counters = nullptr;
+    double *partial = nullptr;
+    float *px = nullptr, *py = nullptr, *pz = nullptr, *pm = nullptr;
+    float *pvx = nullptr, *pvy = nullptr, *pvz = nullptr;
+    float4 *chl = nullptr, *vchl = nullptr;
+    int32_t *perm = nullptr;
+    double *xp = nullptr, *vp = nullptr, *a1 = nullptr, *j1 = nullptr;
 };
 
 }  // namespace
@@ -93,7 +113,10 @@ struct nbody_ctx {
     int64_t evals = 0;
 
     // staging of host arrays
-    DevBuf st_pos, st_vel, st_mass, st_acc, st_pot, st_diag;
+    DevBuf st_pos, st_vel, st_mass, st_acc, st_pot, st_diag, st_jerk;
+
+    // acceleration + jerk path
+    JerkPath jp;
 
     // graphs
     cudaStream_t cap_stream = nullptr;
@@ -442,6 +465,7 @@ int check_ptr(nbody_ctx *ctx, const void *p, const char *name, bool required) {
 struct Arrays {
     double *pos, *vel, *acc, *pot, *diag;
     const double *mass;
+    double *jerk = nullptr;
 };
 
 int prof_drain(nbody_ctx *ctx, int slot) {
@@ -559,6 +583,151 @@ int check_finite(nbody_ctx *ctx, const double *acc, const double *pot, cudaStrea
 int guard(nbody_ctx *ctx) {
     if (!ctx) return NBODY_EINVAL;
     if (ctx->sticky != NBODY_OK) return NBODY_ESTATE;
+    return NBODY_OK;
+}
+
+// ------------------------------------------------------------------ jerk path
+
+void free_jerk(nbody_ctx *ctx) {
+    JerkPath &j = ctx->jp;
+    dev_free(&j.dcl);
+    dev_free(&j.tile_cluster);
+    dev_free(&j.items);
+    dev_free(&j.counters);
+    dev_free(&j.partial);
+    for (float **q : {&j.px, &j.py, &j.pz, &j.pm, &j.pvx, &j.pvy, &j.pvz}) dev_free(q);
+    dev_free(&j.chl);
+    dev_free(&j.vchl);
+    dev_free(&j.perm);
+    for (double **q : {&j.xp, &j.vp, &j.a1, &j.j1}) dev_free(q);
+    j.built = false;
+}
+
+nbody_tiles default_jerk_tiles(const nbody_ctx *c) {
+    if (c->max_cluster >= 65536) return {256, 2, 256, 0, 1};
+    if (c->max_cluster >= 8192) return {128, 2, 256, 0, 2};
+    return {64, 2, 128, 0, 4};
+}
+
+// Build the jerk path's geometry for tile shape t (F32C) and the Hermite scratch.
+int build_jerk(nbody_ctx *ctx, nbody_tiles t, double jfrac = 1.0) {
+    drop_graphs(ctx);
+    free_jerk(ctx);
+    JerkPath &j = ctx->jp;
+    int rc;
+    for (double **q : {&j.xp, &j.vp, &j.a1, &j.j1})
+        if ((rc = dev_alloc(ctx, q, (size_t)3 * ctx->n))) return rc;
+    if (ctx->mode == NBODY_F32C) {
+        t.ctas_per_sm = f32c_jerk_resolve_minb(t.block, t.p, t.tj, t.ctas_per_sm, ctx->eps_zero);
+        const int occ = t.ctas_per_sm
+                            ? f32c_jerk_occupancy(t.block, t.p, t.tj, t.ctas_per_sm, ctx->eps_zero)
+                            : 0;
+        if (occ <= 0) return fail(ctx, NBODY_EUNSUPPORTED, "jerk tile shape is not compiled");
+        const int tc = t.block * t.p;
+        const int workers = occ * ctx->sms;
+        if (t.split <= 0) t.split = choose_split(ctx, tc, t.tj, workers);
+        Plan pl = make_plan(ctx, tc, t.tj, t.split, jfrac);
+        if (pl.n_pad >= (int64_t)1 << 31) return fail(ctx, NBODY_EINVAL, "padded size exceeds 2^31");
+        j.tiles = t;
+        j.tc = tc;
+        j.n_pad = pl.n_pad;
+        j.n_tiles = pl.n_tiles;
+        j.n_items = (int)pl.items.size();
+        j.grid = std::min(j.n_items, workers);
+        if ((rc = upload(ctx, &j.dcl, pl.cl))) return rc;
+        if ((rc = upload(ctx, &j.tile_cluster, pl.tile_cluster))) return rc;
+        if ((rc = upload(ctx, &j.items, pl.items))) return rc;
+        if ((rc = dev_alloc(ctx, &j.counters, (size_t)j.n_tiles + 1))) return rc;
+        if ((rc = dev_alloc(ctx, &j.partial, (size_t)pl.partial_slots * 7 * tc))) return rc;
+        for (float **q : {&j.px, &j.py, &j.pz, &j.pm, &j.pvx, &j.pvy, &j.pvz})
+            if ((rc = dev_alloc(ctx, q, (size_t)j.n_pad))) return rc;
+        if ((rc = dev_alloc(ctx, &j.chl, (size_t)j.n_tiles * 2))) return rc;
+        if ((rc = dev_alloc(ctx, &j.vchl, (size_t)j.n_tiles * 2))) return rc;
+        std::vector<int32_t> perm((size_t)j.n_pad, -1);
+        for (const ClusterDev &d : pl.cl)
+            for (int32_t l = 0; l < d.n; ++l) perm[(size_t)d.slot_begin + l] = (int32_t)(d.user_begin + l);
+        if ((rc = upload(ctx, &j.perm, perm))) return rc;
+    }
+    j.built = true;
+    ctx->evals = 0;
+    return NBODY_OK;
+}
+
+int ensure_jerk(nbody_ctx *ctx) {
+    if (ctx->jp.built) return NBODY_OK;
+    return build_jerk(ctx, default_jerk_tiles(ctx));
+}
+
+F32CJerkParams jerk_params(const nbody_ctx *ctx, double *acc, double *jerk, double *pot) {
+    const JerkPath &j = ctx->jp;
+    F32CJerkParams fp{};
+    fp.px = j.px; fp.py = j.py; fp.pz = j.pz; fp.pm = j.pm;
+    fp.pvx = j.pvx; fp.pvy = j.pvy; fp.pvz = j.pvz;
+    fp.chl = j.chl; fp.vchl = j.vchl; fp.perm = j.perm; fp.cl = j.dcl;
+    fp.items = j.items; fp.n_items = j.n_items; fp.tc = j.tc;
+    fp.counters = j.counters; fp.partial = j.partial;
+    fp.acc = acc; fp.jerk = jerk; fp.pot = pot; fp.n = ctx->n; fp.G = ctx->G;
+    return fp;
+}
+
+// Acceleration, jerk and potential at (pos, vel): [reorder] + pack + velocity
+// pack + queue reset + jerk kernel (F32C), or the FP64 jerk kernel.
+int enqueue_forces_jerk(nbody_ctx *ctx, const double *pos, const double *vel, const double *mass,
+                        double *acc, double *jerk, double *pot, bool reorder, int slot,
+                        bool capturing, cudaStream_t s, int *kernels) {
+    if (ctx->n == 0) return NBODY_OK;
+    JerkPath &j = ctx->jp;
+    int rc;
+    if (ctx->mode == NBODY_F32C) {
+        if (reorder) {
+            NB_CUDA(launch_reorder(pos, ctx->n, ctx->chunks, ctx->n_chunks, ctx->chunk_first, ctx->ncl,
+                                   j.dcl, ctx->bpart, ctx->bbox, ctx->keys, ctx->vals, ctx->sort_n,
+                                   ctx->max_cluster, j.perm, s, kernels));
+        }
+        PackParams pp{pos, mass, j.perm, j.dcl, j.tile_cluster, j.tc, ctx->n,
+                      j.px, j.py, j.pz, j.pm, j.chl};
+        NB_CUDA(launch_pack(j.n_tiles, pp, s));
+        NB_CUDA(launch_pack_vel(j.n_tiles, vel, j.perm, j.dcl, j.tile_cluster, j.tc, ctx->n, j.pvx,
+                                j.pvy, j.pvz, j.vchl, s));
+        *kernels += 2;
+        NB_CUDA(cudaMemsetAsync(j.counters, 0, ((size_t)j.n_tiles + 1) * sizeof(int), s));
+        const F32CJerkParams fp = jerk_params(ctx, acc, jerk, pot);
+        if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
+        cudaError_t e = launch_f32c_jerk(j.tiles.block, j.tiles.p, j.tiles.tj, j.tiles.ctas_per_sm,
+                                         ctx->eps_zero, j.grid, fp, s);
+        if (e == cudaErrorNotSupported) return fail(ctx, NBODY_EUNSUPPORTED, "jerk tile shape not compiled");
+        NB_CUDA(e);
+        ++*kernels;
+        if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
+    } else {
+        F64Params fp{pos, mass, ctx->dcl, ctx->blocks64, acc, pot, nullptr, ctx->n, ctx->G, 0.0,
+                     vel, jerk};
+        if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
+        NB_CUDA(launch_f64(ctx->n_blocks64, fp, s));
+        ++*kernels;
+        if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
+    }
+    return NBODY_OK;
+}
+
+// One Hermite step: predict, forces + jerks at the prediction, correct, diagnostics.
+int enqueue_hermite_step(nbody_ctx *ctx, const Arrays &a, double dt, bool reorder, int slot,
+                         bool capturing, cudaStream_t s, int *kernels) {
+    if (ctx->n == 0) return NBODY_OK;
+    JerkPath &j = ctx->jp;
+    const int64_t n3 = 3 * ctx->n;
+    NB_CUDA(launch_hermite_predict(n3, a.pos, a.vel, a.acc, a.jerk, dt, j.xp, j.vp, s));
+    ++*kernels;
+    int rc = enqueue_forces_jerk(ctx, j.xp, j.vp, a.mass, j.a1, j.j1, a.pot, reorder, slot,
+                                 capturing, s, kernels);
+    if (rc) return rc;
+    NB_CUDA(launch_hermite_correct(n3, a.pos, a.vel, a.acc, a.jerk, j.a1, j.j1, dt, s));
+    ++*kernels;
+    if (a.diag) {
+        NB_CUDA(launch_energy(a.pos, a.vel, a.mass, a.pot, ctx->n, ctx->chunks, ctx->n_chunks,
+                              ctx->chunk_first, ctx->ncl, ctx->epart, a.diag, ctx->diag_counter, s));
+        *kernels += ctx->n_chunks > 0 ? 2 : 1;
+    }
     return NBODY_OK;
 }
 
@@ -721,6 +890,7 @@ void nbody_destroy(nbody_ctx *ctx) {
     cudaGetLastError();
     drop_graphs(ctx);
     free_f32c(ctx);
+    free_jerk(ctx);
     dev_free(&ctx->blocks64);
     dev_free(&ctx->chunks);
     dev_free(&ctx->chunk_first);
@@ -732,7 +902,8 @@ void nbody_destroy(nbody_ctx *ctx) {
     dev_free(&ctx->bbox);
     dev_free(&ctx->keys);
     dev_free(&ctx->vals);
-    for (DevBuf *b : {&ctx->st_pos, &ctx->st_vel, &ctx->st_mass, &ctx->st_acc, &ctx->st_pot, &ctx->st_diag})
+    for (DevBuf *b : {&ctx->st_pos, &ctx->st_vel, &ctx->st_mass, &ctx->st_acc, &ctx->st_pot,
+                      &ctx->st_diag, &ctx->st_jerk})
         if (b->p) cudaFree(b->p);
     for (int s = 0; s < kProfSlots; ++s)
         for (int k = 0; k < 2; ++k)
@@ -890,8 +1061,14 @@ int nbody_forces(nbody_ctx *ctx, const double *pos, const double *mass, double *
     return check_finite(ctx, (const double *)dacc, (const double *)dpot, s);
 }
 
-int nbody_step(nbody_ctx *ctx, double *pos, double *vel, const double *mass, double *acc,
-               double *pot, double dt, int32_t nsteps, double *diag, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// KDK (kind 0) or Hermite (kind 1, jerk != null) steps, eager or graph-replayed.
+int step_common(nbody_ctx *ctx, double *pos, double *vel, const double *mass, double *acc,
+                double *jerk, double *pot, double dt, int32_t nsteps, double *diag, void *stream,
+                int kind) {
     int rc = guard(ctx);
     if (rc) return rc;
     if (!std::isfinite(dt)) return fail(ctx, NBODY_EINVAL, "dt is not finite");
@@ -899,22 +1076,25 @@ int nbody_step(nbody_ctx *ctx, double *pos, double *vel, const double *mass, dou
     if (ctx->n == 0 || nsteps == 0) return NBODY_OK;
     if ((rc = check_ptr(ctx, pos, "pos", true)) || (rc = check_ptr(ctx, vel, "vel", true)) ||
         (rc = check_ptr(ctx, mass, "mass", true)) || (rc = check_ptr(ctx, acc, "acc", true)) ||
-        (rc = check_ptr(ctx, pot, "pot", false)) || (rc = check_ptr(ctx, diag, "diag", false)))
+        (rc = check_ptr(ctx, pot, "pot", false)) || (rc = check_ptr(ctx, diag, "diag", false)) ||
+        (rc = check_ptr(ctx, jerk, "jerk", kind == 1)))
         return rc;
+    if (kind == 1 && (rc = ensure_jerk(ctx))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n3b = 3 * ctx->n * sizeof(double), nb = ctx->n * sizeof(double);
     const size_t db = (size_t)nsteps * ctx->ncl * 9 * sizeof(double);
-    void *dpos, *dvel, *dmass, *dacc, *dpot, *ddiag;
-    bool spos, svel, smass, sacc, spot, sdiag;
+    void *dpos, *dvel, *dmass, *dacc, *dpot, *ddiag, *djerk = nullptr;
+    bool spos, svel, smass, sacc, spot, sdiag, sjerk = false;
     if ((rc = resolve(ctx, pos, n3b, ctx->st_pos, true, s, &dpos, &spos)) ||
         (rc = resolve(ctx, vel, n3b, ctx->st_vel, true, s, &dvel, &svel)) ||
         (rc = resolve(ctx, mass, nb, ctx->st_mass, true, s, &dmass, &smass)) ||
         (rc = resolve(ctx, acc, n3b, ctx->st_acc, true, s, &dacc, &sacc)) ||
         (rc = resolve(ctx, pot, nb, ctx->st_pot, true, s, &dpot, &spot)) ||
-        (rc = resolve(ctx, diag, db, ctx->st_diag, false, s, &ddiag, &sdiag)))
+        (rc = resolve(ctx, diag, db, ctx->st_diag, false, s, &ddiag, &sdiag)) ||
+        (rc = resolve(ctx, jerk, n3b, ctx->st_jerk, true, s, &djerk, &sjerk)))
         return rc;
     Arrays a{(double *)dpos, (double *)dvel, (double *)dacc, (double *)dpot, (double *)ddiag,
-             (const double *)dmass};
+             (const double *)dmass, (double *)djerk};
     if (a.diag) NB_CUDA(cudaMemsetAsync(ctx->diag_counter, 0, sizeof(int), s));
     const bool use_graph = !(ctx->flags & NBODY_FLAG_NO_GRAPH);
     uint64_t dt_bits;
@@ -925,22 +1105,25 @@ int nbody_step(nbody_ctx *ctx, double *pos, double *vel, const double *mass, dou
         if (slot < -1) return ctx->sticky;
         if (!use_graph) {
             int k = 0;
-            rc = enqueue_step(ctx, a, dt, reorder, slot, false, s, &k);
+            rc = kind == 1 ? enqueue_hermite_step(ctx, a, dt, reorder, slot, false, s, &k)
+                           : enqueue_step(ctx, a, dt, reorder, slot, false, s, &k);
             ctx->launches += k;
             if (rc) return rc;
         } else {
             GraphEntry *g = nullptr;
             for (auto &e : ctx->graphs)
                 if (e.pos == a.pos && e.vel == a.vel && e.mass == a.mass && e.acc == a.acc &&
-                    e.pot == a.pot && e.diag == a.diag && e.dt_bits == dt_bits &&
-                    e.reorder == (int)reorder && e.slot == slot)
+                    e.pot == a.pot && e.diag == a.diag && e.jerk == a.jerk && e.kind == kind &&
+                    e.dt_bits == dt_bits && e.reorder == (int)reorder && e.slot == slot)
                     g = &e;
             if (!g) {
                 if (ctx->graphs.size() >= 16) drop_graphs(ctx);
-                GraphEntry ge{a.pos, a.vel, a.mass, a.acc, a.pot, a.diag, dt_bits, (int)reorder, slot, nullptr, 0};
+                GraphEntry ge{a.pos, a.vel, a.mass, a.acc, a.pot, a.diag, a.jerk, kind, dt_bits,
+                              (int)reorder, slot, nullptr, 0};
                 NB_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
                 int k = 0;
-                rc = enqueue_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k);
+                rc = kind == 1 ? enqueue_hermite_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k)
+                               : enqueue_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k);
                 cudaGraph_t graph = nullptr;
                 cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
                 if (rc) {
@@ -966,8 +1149,76 @@ int nbody_step(nbody_ctx *ctx, double *pos, double *vel, const double *mass, dou
     if (sacc) NB_CUDA(cudaMemcpyAsync(acc, dacc, n3b, cudaMemcpyDeviceToHost, s));
     if (spot) NB_CUDA(cudaMemcpyAsync(pot, dpot, nb, cudaMemcpyDeviceToHost, s));
     if (sdiag) NB_CUDA(cudaMemcpyAsync(diag, ddiag, db, cudaMemcpyDeviceToHost, s));
-    if (spos || svel || sacc || spot || sdiag) NB_CUDA(cudaStreamSynchronize(s));
+    if (sjerk) NB_CUDA(cudaMemcpyAsync(jerk, djerk, n3b, cudaMemcpyDeviceToHost, s));
+    if (spos || svel || sacc || spot || sdiag || sjerk) NB_CUDA(cudaStreamSynchronize(s));
     return check_finite(ctx, (const double *)dacc, (const double *)dpot, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int nbody_step(nbody_ctx *ctx, double *pos, double *vel, const double *mass, double *acc,
+               double *pot, double dt, int32_t nsteps, double *diag, void *stream) {
+    return step_common(ctx, pos, vel, mass, acc, nullptr, pot, dt, nsteps, diag, stream, 0);
+}
+
+int nbody_step_hermite(nbody_ctx *ctx, double *pos, double *vel, const double *mass, double *acc,
+                       double *jerk, double *pot, double dt, int32_t nsteps, double *diag,
+                       void *stream) {
+    return step_common(ctx, pos, vel, mass, acc, jerk, pot, dt, nsteps, diag, stream, 1);
+}
+
+int nbody_forces_jerk(nbody_ctx *ctx, const double *pos, const double *vel, const double *mass,
+                      double *acc, double *jerk, double *pot, void *stream) {
+    int rc = guard(ctx);
+    if (rc) return rc;
+    if (ctx->n == 0) return NBODY_OK;
+    if ((rc = check_ptr(ctx, pos, "pos", true)) || (rc = check_ptr(ctx, vel, "vel", true)) ||
+        (rc = check_ptr(ctx, mass, "mass", true)) || (rc = check_ptr(ctx, acc, "acc", true)) ||
+        (rc = check_ptr(ctx, jerk, "jerk", true)) || (rc = check_ptr(ctx, pot, "pot", false)))
+        return rc;
+    if ((rc = ensure_jerk(ctx))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n3b = 3 * ctx->n * sizeof(double), nb = ctx->n * sizeof(double);
+    void *dpos, *dvel, *dmass, *dacc, *djerk, *dpot;
+    bool spos, svel, smass, sacc, sjerk, spot;
+    if ((rc = resolve(ctx, pos, n3b, ctx->st_pos, true, s, &dpos, &spos)) ||
+        (rc = resolve(ctx, vel, n3b, ctx->st_vel, true, s, &dvel, &svel)) ||
+        (rc = resolve(ctx, mass, nb, ctx->st_mass, true, s, &dmass, &smass)) ||
+        (rc = resolve(ctx, acc, n3b, ctx->st_acc, false, s, &dacc, &sacc)) ||
+        (rc = resolve(ctx, jerk, n3b, ctx->st_jerk, false, s, &djerk, &sjerk)) ||
+        (rc = resolve(ctx, pot, nb, ctx->st_pot, false, s, &dpot, &spot)))
+        return rc;
+    const int slot = next_slot(ctx);
+    if (slot < -1) return ctx->sticky;
+    int k = 0;
+    rc = enqueue_forces_jerk(ctx, (const double *)dpos, (const double *)dvel, (const double *)dmass,
+                             (double *)dacc, (double *)djerk, (double *)dpot, want_reorder(ctx), slot,
+                             false, s, &k);
+    ctx->launches += k;
+    if (rc) return rc;
+    if (slot >= 0) ctx->ev_pending[slot] = true;
+    ctx->evals += 1;
+    if (sacc) NB_CUDA(cudaMemcpyAsync(acc, dacc, n3b, cudaMemcpyDeviceToHost, s));
+    if (sjerk) NB_CUDA(cudaMemcpyAsync(jerk, djerk, n3b, cudaMemcpyDeviceToHost, s));
+    if (spot) NB_CUDA(cudaMemcpyAsync(pot, dpot, nb, cudaMemcpyDeviceToHost, s));
+    if (sacc || sjerk || spot) NB_CUDA(cudaStreamSynchronize(s));
+    return check_finite(ctx, (const double *)dacc, (const double *)dpot, s);
+}
+
+int nbody_get_jerk_tiles(const nbody_ctx *ctx, nbody_tiles *out) {
+    if (!ctx || !out) return NBODY_EINVAL;
+    *out = ctx->mode == NBODY_F32C && ctx->jp.built ? ctx->jp.tiles : nbody_tiles{0, 0, 0, 0, 0};
+    return NBODY_OK;
+}
+
+int nbody_set_jerk_tiles(nbody_ctx *ctx, const nbody_tiles *t) {
+    int rc = guard(ctx);
+    if (rc) return rc;
+    if (!t) return fail(ctx, NBODY_EINVAL, "tiles is NULL");
+    if (ctx->mode != NBODY_F32C) return NBODY_OK;
+    return build_jerk(ctx, *t);
 }
 
 int nbody_energy(nbody_ctx *ctx, const double *pos, const double *vel, const double *mass,

@@ -61,6 +61,25 @@ struct F32CParams {
     double half_dt;
 };
 
+// Parameters of the FP32-compensated acceleration + jerk kernel.
+struct F32CJerkParams {
+    const float *px, *py, *pz, *pm, *pvx, *pvy, *pvz;
+    const float4 *chl;   // position centres (hi, lo) per tile
+    const float4 *vchl;  // velocity centres (hi, lo) per tile
+    const int32_t *perm;
+    const ClusterDev *cl;
+    const Item *items;
+    int32_t n_items;
+    int32_t tc;
+    int *counters;
+    double *partial;     // [slots][7][tc]
+    double *acc;         // [3][n]
+    double *jerk;        // [3][n]
+    double *pot;         // [n] or null
+    int64_t n;
+    double G;
+};
+
 // Parameters of the plain FP64 kernel.
 struct F64Params {
     const double *pos;      // [3][n]
@@ -71,6 +90,8 @@ struct F64Params {
     int64_t n;
     double G;
     double half_dt;
+    const double *velin;  // [3][n]: with jerk != null, the velocities the jerk uses
+    double *jerk;         // [3][n] or null
 };
 
 struct PackParams {
@@ -113,6 +134,27 @@ cudaError_t launch_f64(int grid, const F64Params &prm, cudaStream_t s);
 constexpr int kF64Block = 128;
 
 cudaError_t launch_pack(int n_tiles, const PackParams &prm, cudaStream_t s);
+// Velocity part of the jerk path's packing: FP64 mean velocity per tile as a
+// float pair (vchl) and FP32 offsets from it (pads get velocity offset 0).
+cudaError_t launch_pack_vel(int n_tiles, const double *vel, const int32_t *perm,
+                            const ClusterDev *cl, const int32_t *tile_cluster, int tc, int64_t n,
+                            float *pvx, float *pvy, float *pvz, float4 *vchl, cudaStream_t s);
+
+// Acceleration + jerk kernel (forces_f32c_jerk.cuh), same conventions as launch_f32c.
+cudaError_t launch_f32c_jerk(int block, int p, int tj, int minb, bool eps_zero, int grid,
+                             const F32CJerkParams &prm, cudaStream_t s);
+int f32c_jerk_occupancy(int block, int p, int tj, int minb, bool eps_zero);
+int f32c_jerk_resolve_minb(int block, int p, int tj, int minb, bool eps_zero);
+int f32c_jerk_shapes(int *block, int *p, int *tj, int *minb, int cap);
+
+// Hermite predictor: xp = x + v dt + a dt^2/2 + j dt^3/6, vp = v + a dt + j dt^2/2.
+cudaError_t launch_hermite_predict(int64_t n3, const double *pos, const double *vel,
+                                   const double *acc, const double *jerk, double dt, double *xp,
+                                   double *vp, cudaStream_t s);
+// Hermite corrector: v1 = v + (a0 + a1) dt/2 + (j0 - j1) dt^2/12,
+// x1 = x + (v + v1) dt/2 + (a0 - a1) dt^2/12; then acc <- a1, jerk <- j1.
+cudaError_t launch_hermite_correct(int64_t n3, double *pos, double *vel, double *acc, double *jerk,
+                                   const double *a1, const double *j1, double dt, cudaStream_t s);
 
 cudaError_t launch_kick_drift(int64_t n3, double *pos, double *vel, const double *acc,
                               double half_dt, double dt, cudaStream_t s);

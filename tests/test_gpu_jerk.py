@@ -1,0 +1,181 @@
+"""Acceleration + jerk and Hermite steps through the CUDA path vs the oracle (GPU).
+
+The paper's device kernel computes the acceleration together with its time
+derivative (Sec. 3) and validates the jerk to 0.2 % of a typical magnitude.
+Tolerances here:
+  * NBODY_F64: per-particle relative error of a and jerk <= 1e-12.
+  * NBODY_F32C: acceleration as in the acceleration-only tests (median <= 1e-6,
+    max <= 1e-4); jerk per-particle relative error median <= 1e-5 and every
+    component within 0.2 % of the particle's own jerk magnitude (the paper's
+    bound, read against each particle's own |jerk_i|).
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2509_19294_gb300 as nb
+from paper_2509_19294_gb300 import ic
+from tests import metrics
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+JERK_MEDIAN = 1e-5
+JERK_PAPER = 2e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_19294_gb300 import build
+    build.build()
+    nb.load()
+    torch.cuda.init()
+
+
+def forces_jerk(pos, vel, mass, eps, mode=nb.NBODY_F32C, offsets=None, jerk_tiles=None, **kw):
+    n = mass.shape[0]
+    with nb.nbody_init(n, eps, mode=mode, cluster_offsets=offsets, **kw) as ctx:
+        if jerk_tiles is not None:
+            nb.nbody_set_jerk_tiles(ctx, jerk_tiles)
+        acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        jerk = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        pot = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_forces_jerk(ctx, dev(pos), dev(vel), dev(mass), acc, jerk, pot)
+        return host(acc), host(jerk), host(pot)
+
+
+def check(a, j, p, ra, rj, rp, f64=False):
+    if f64:
+        assert metrics.rel_acc_errors(a, ra).max() <= 1e-12
+        assert metrics.rel_acc_errors(j, rj).max() <= 1e-12
+        assert metrics.rel_pot_errors(p, rp).max() <= 1e-12
+        return
+    s = metrics.summary(a, ra, p, rp)
+    assert s["median"] <= 1e-6 and s["max"] <= 1e-4, s
+    assert s["pot_median"] <= 1e-6 and s["pot_max"] <= 1e-4, s
+    ej = metrics.rel_acc_errors(j, rj)
+    pj = metrics.paper_metric(j, rj)
+    assert np.median(ej) <= JERK_MEDIAN and pj <= JERK_PAPER, (np.median(ej), ej.max(), pj)
+
+
+@pytest.mark.parametrize("mode", [nb.NBODY_F64, nb.NBODY_F32C])
+def test_plummer_forces_and_jerk(oracle, mode):
+    n = 16384 if mode == nb.NBODY_F32C else 2048
+    pos, vel, mass = ic.plummer(n, seed=41)
+    ra, rj, rp = oracle.forces_jerk(pos, vel, mass, 0.005)
+    a, j, p = forces_jerk(pos, vel, mass, 0.005, mode=mode)
+    check(a, j, p, ra, rj, rp, f64=mode == nb.NBODY_F64)
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 257, 1023])
+@pytest.mark.parametrize("eps", [0.0, 0.01])
+def test_ragged_sizes(oracle, n, eps):
+    rng = np.random.default_rng(n + 7)
+    pos = rng.normal(size=(3, n))
+    vel = rng.normal(size=(3, n)) * 0.3
+    mass = rng.uniform(0.5, 1.5, n) / n
+    ra, rj, rp = oracle.forces_jerk(pos, vel, mass, eps)
+    for mode in (nb.NBODY_F64, nb.NBODY_F32C):
+        a, j, p = forces_jerk(pos, vel, mass, eps, mode=mode)
+        if n == 1:
+            assert np.all(a == 0) and np.all(j == 0) and np.all(p == 0)
+            continue
+        if mode == nb.NBODY_F64:
+            check(a, j, p, ra, rj, rp, f64=True)
+        else:
+            assert metrics.rel_acc_errors(a, ra).max() <= 1e-4
+            assert metrics.paper_metric(j, rj) <= JERK_PAPER
+
+
+def test_every_jerk_shape_and_split(oracle):
+    pos, vel, mass = ic.plummer(3001, seed=42)
+    ra, rj, rp = oracle.forces_jerk(pos, vel, mass, 0.01)
+    shapes = [(128, 2, 256, 2), (256, 2, 256, 1), (128, 1, 128, 4), (64, 2, 128, 4), (128, 2, 128, 3)]
+    for b, p_, tj, m in shapes:
+        for split in (1, 3):
+            a, j, p = forces_jerk(pos, vel, mass, 0.01, jerk_tiles=(b, p_, tj, split, m))
+            check(a, j, p, ra, rj, rp)
+
+
+def test_translation_and_galilean_boost(oracle):
+    # FP32 offsets from tile means make the F32C jerk independent of a common
+    # shift of positions and of a common velocity
+    pos, vel, mass = ic.plummer(8192, seed=43)
+    ra, rj, rp = oracle.forces_jerk(pos, vel, mass, 0.005)
+    a, j, p = forces_jerk(pos + np.array([[1e3], [-1e3], [5e2]]),
+                          vel + np.array([[1e2], [50.0], [-80.0]]), mass, 0.005)
+    check(a, j, p, ra, rj, rp)
+
+
+def test_ensemble_jerk(oracle):
+    ens = ic.ensemble(8, seed=44, n_min=256, n_max=3000)
+    a, j, p = forces_jerk(ens.pos, ens.vel, ens.mass, ens.eps, offsets=ens.offsets, reorder_every=1)
+    for c in range(8):
+        b, e = ens.offsets[c], ens.offsets[c + 1]
+        ra, rj, rp = oracle.forces_jerk(ens.pos[:, b:e], ens.vel[:, b:e], ens.mass[b:e], ens.eps[c])
+        check(a[:, b:e], j[:, b:e], p[b:e], ra, rj, rp)
+
+
+def hermite_run(pos, vel, mass, eps, dt, nsteps, mode, chunks=1, flags=0, **kw):
+    n = mass.shape[0]
+    with nb.nbody_init(n, eps, mode=mode, flags=flags, **kw) as ctx:
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        jerk = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        pot = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_forces_jerk(ctx, p, v, m, acc, jerk, pot)
+        ds = []
+        for _ in range(chunks):
+            d = torch.empty((nsteps // chunks, 1, 9), dtype=torch.float64, device="cuda")
+            nb.nbody_step_hermite(ctx, p, v, m, acc, jerk, pot, dt, nsteps // chunks, d)
+            ds.append(host(d))
+        return host(p), host(v), host(acc), host(jerk), host(pot), np.concatenate(ds)
+
+
+def test_hermite_f64_matches_oracle(oracle):
+    pos, vel, mass = ic.plummer(1024, seed=45)
+    gp, gv, ga, gj, _, gd = hermite_run(pos, vel, mass, 0.01, 1e-3, 10, nb.NBODY_F64)
+    rp, rv, ra, rj, _, rd = oracle.hermite(pos, vel, mass, 0.01, 1e-3, 10, diag=True)
+    np.testing.assert_allclose(gp, rp, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(gv, rv, rtol=0, atol=1e-12)
+    assert metrics.rel_acc_errors(ga, ra).max() <= 1e-11
+    assert metrics.rel_acc_errors(gj, rj).max() <= 1e-10
+    np.testing.assert_allclose(gd[:, 0, :], rd[1:], rtol=1e-11, atol=1e-13)
+
+
+def test_hermite_f32c_tracks_oracle(oracle):
+    pos, vel, mass = ic.plummer(4096, seed=46)
+    nsteps, dt = 10, 1e-3
+    gp, gv, ga, gj, _, gd = hermite_run(pos, vel, mass, 0.01, dt, nsteps, nb.NBODY_F32C,
+                                        reorder_every=5)
+    rp, rv, ra, rj, _, rd = oracle.hermite(pos, vel, mass, 0.01, dt, nsteps, diag=True)
+    amax = np.abs(ra).max()
+    # an acceleration error <= 1e-4 max|a| per evaluation bounds v and x as for KDK
+    assert np.abs(gv - rv).max() <= nsteps * dt * 1e-4 * amax
+    assert np.abs(gp - rp).max() <= nsteps ** 2 * dt ** 2 * 1e-4 * amax
+    s = metrics.summary(ga, ra)
+    assert s["median"] <= 1e-6 and s["max"] <= 1e-4, s
+    np.testing.assert_allclose(gd[:, 0, 2], rd[1:, 2], rtol=1e-6)
+
+
+@pytest.mark.parametrize("mode", [nb.NBODY_F32C, nb.NBODY_F64])
+def test_hermite_graph_equals_eager(mode):
+    pos, vel, mass = ic.plummer(2000, seed=47)
+    g = hermite_run(pos, vel, mass, 0.01, 1e-3, 6, mode, chunks=2, reorder_every=3)
+    e = hermite_run(pos, vel, mass, 0.01, 1e-3, 6, mode, chunks=2, reorder_every=3,
+                    flags=nb.NBODY_FLAG_NO_GRAPH)
+    for x, y in zip(g, e):
+        assert np.array_equal(x, y)
+
+
+def test_host_buffers_through_jerk_and_hermite():
+    pos, vel, mass = ic.plummer(1500, seed=48)
+    n = 1500
+    with nb.nbody_init(n, 0.01) as ctx:
+        p, v = pos.copy(), vel.copy()
+        acc, jerk, pot = np.empty((3, n)), np.empty((3, n)), np.empty(n)
+        nb.nbody_forces_jerk(ctx, p, v, mass, acc, jerk, pot)
+        nb.nbody_step_hermite(ctx, p, v, mass, acc, jerk, pot, 1e-3, 3)
+    d = hermite_run(pos, vel, mass, 0.01, 1e-3, 3, nb.NBODY_F32C)
+    for x, y in zip((p, v, acc, jerk, pot), d[:5]):
+        assert np.array_equal(x, y)
