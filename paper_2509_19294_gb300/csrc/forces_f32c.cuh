@@ -22,10 +22,12 @@
 //     3 fma (a) = 13 FP32 operations + 1 MUFU.
 //   * Precision: coordinates are FP32 offsets from each tile's centre, which
 //     is held as an unevaluated float pair hi + lo (48 significant bits).  Per
-//     j-tile the centre difference (hi_I - hi_J) + (lo_I - lo_J) is rounded to
-//     FP32 once (exactly 0 on the diagonal tile) and added to the i offsets, so
-//     close pairs keep their digits whatever the absolute position, and the
-//     tile loop runs no FP64 instruction.  Each thread sums a tile's terms in
+//     j-tile the centre difference c_I - c_J is formed as a float pair by an
+//     error-free TwoSum (exactly 0 on the diagonal tile) and added to each i
+//     offset as two rounded adds, so close pairs keep their digits whatever the
+//     absolute position, the rounding of the shift is per particle (not one
+//     coherent displacement of a whole tile pair), and the tile loop runs no
+//     FP64 instruction.  Each thread sums a tile's terms in
 //     FP32, then folds the tile sum into a Kahan-compensated FP32 accumulator;
 //     sum - compensation is converted to FP64 at the end.
 //   * Split j-ranges (small N or load balance): each split writes its FP64
@@ -49,6 +51,19 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
     return y;
 }
 
+// Centre difference (ih + il) - (jh + jl) as an unevaluated float pair hi + lo,
+// accurate to ~2^-48 relative (Knuth's error-free TwoSum on the hi parts).  The
+// shift is then applied to each i-offset as two rounded adds, so its rounding
+// is per particle rather than one common displacement of the whole tile.
+__device__ __forceinline__ void centre_diff(float ih, float il, float jh, float jl, float &hi,
+                                            float &lo) {
+    const float s = __fsub_rn(ih, jh);
+    const float bb = __fsub_rn(s, ih);
+    const float e = __fadd_rn(__fsub_rn(ih, __fsub_rn(s, bb)), __fsub_rn(-jh, bb));
+    hi = s;
+    lo = __fadd_rn(e, __fsub_rn(il, jl));
+}
+
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     const float y = __fsub_rn(x, c);
     const float t = __fadd_rn(s, y);
@@ -66,7 +81,7 @@ struct F32CKernel {
 
     struct Smem {
         float4 j[2][4][TJ / 4];  // [buffer][x|y|z|m][TJ/4]
-        float shift[2][4];
+        float shift[2][8];       // hi (0..2) and lo (4..6) of the centre difference
         int item;
         int last;
     };
@@ -92,13 +107,13 @@ struct F32CKernel {
         }
     }
 
-    // FP32 offset that moves i-tile coordinates into the j-tile's frame:
-    // (hi_I - hi_J) + (lo_I - lo_J), rounded once more to FP32.
+    // Offset that moves i-tile coordinates into the j-tile's frame, c_I - c_J,
+    // as a float pair (see centre_diff).
     __device__ static __forceinline__ void store_shift(Smem &sm, int b, float4 ih, float4 il,
                                                        float4 jh, float4 jl) {
-        sm.shift[b][0] = __fadd_rn(__fsub_rn(ih.x, jh.x), __fsub_rn(il.x, jl.x));
-        sm.shift[b][1] = __fadd_rn(__fsub_rn(ih.y, jh.y), __fsub_rn(il.y, jl.y));
-        sm.shift[b][2] = __fadd_rn(__fsub_rn(ih.z, jh.z), __fsub_rn(il.z, jl.z));
+        centre_diff(ih.x, il.x, jh.x, jl.x, sm.shift[b][0], sm.shift[b][4]);
+        centre_diff(ih.y, il.y, jh.y, jl.y, sm.shift[b][1], sm.shift[b][5]);
+        centre_diff(ih.z, il.z, jh.z, jl.z, sm.shift[b][2], sm.shift[b][6]);
     }
 
     __device__ static __forceinline__ void body(float2 xj, float2 yj, float2 zj, float2 mj,
@@ -211,11 +226,12 @@ struct F32CKernel {
                 float2 nx[P], ny[P], nz[P];
                 {
                     const float sx = sm.shift[b][0], sy = sm.shift[b][1], sz = sm.shift[b][2];
+                    const float lx = sm.shift[b][4], ly = sm.shift[b][5], lz = sm.shift[b][6];
 #pragma unroll
                     for (int k = 0; k < P; ++k) {
-                        const float qx = -__fadd_rn(ox[k], sx);
-                        const float qy = -__fadd_rn(oy[k], sy);
-                        const float qz = -__fadd_rn(oz[k], sz);
+                        const float qx = -__fadd_rn(__fadd_rn(ox[k], sx), lx);
+                        const float qy = -__fadd_rn(__fadd_rn(oy[k], sy), ly);
+                        const float qz = -__fadd_rn(__fadd_rn(oz[k], sz), lz);
                         nx[k] = make_float2(qx, qx);
                         ny[k] = make_float2(qy, qy);
                         nz[k] = make_float2(qz, qz);

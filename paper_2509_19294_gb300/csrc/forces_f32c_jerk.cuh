@@ -12,7 +12,8 @@
 // the (cluster, i-tile, j-range) queue, p i-particles per thread, j-tiles in
 // double-buffered shared memory, two j-particles per f32x2 instruction, FP32
 // offsets from float-pair tile centres for positions AND velocities, Kahan-
-// compensated per-tile sums, FP64 split reduction and epilogue.  Per pair:
+// compensated per-tile sums, FP64 split reduction and epilogue; centre
+// differences as float pairs added per particle (see forces_f32c.cuh).  Per pair:
 // 3 add (r), 3 add (u), 3 fma (r^2), 3 (r.u), 1 rsqrt, 3 mul (m s, s^2, m s^3),
 // 2 mul (beta = -3 (r.u) s^2), 1 add (phi), 3 fma (a), 6 fma (jerk) =
 // 27 FP32 operations + 1 MUFU.
@@ -38,7 +39,7 @@ struct F32CJerkKernel {
 
     struct Smem {
         float4 j[2][NA][TJ / 4];
-        float shift[2][8];  // position shift (0..2), velocity shift (4..6)
+        float shift[2][12];  // hi, lo of the position shift (0..2, 3..5) and velocity shift (6..8, 9..11)
         int item;
         int last;
     };
@@ -68,19 +69,16 @@ struct F32CJerkKernel {
         }
     }
 
-    __device__ static __forceinline__ float pair_diff(float ih, float il, float jh, float jl) {
-        return __fadd_rn(__fsub_rn(ih, jh), __fsub_rn(il, jl));
-    }
-
     __device__ static __forceinline__ void store_shift(Smem &sm, int b, const float4 (&ic)[4],
                                                        const float4 (&jc)[4]) {
         // ic/jc: position hi, position lo, velocity hi, velocity lo
-        sm.shift[b][0] = pair_diff(ic[0].x, ic[1].x, jc[0].x, jc[1].x);
-        sm.shift[b][1] = pair_diff(ic[0].y, ic[1].y, jc[0].y, jc[1].y);
-        sm.shift[b][2] = pair_diff(ic[0].z, ic[1].z, jc[0].z, jc[1].z);
-        sm.shift[b][4] = pair_diff(ic[2].x, ic[3].x, jc[2].x, jc[3].x);
-        sm.shift[b][5] = pair_diff(ic[2].y, ic[3].y, jc[2].y, jc[3].y);
-        sm.shift[b][6] = pair_diff(ic[2].z, ic[3].z, jc[2].z, jc[3].z);
+        float *sh = sm.shift[b];
+        centre_diff(ic[0].x, ic[1].x, jc[0].x, jc[1].x, sh[0], sh[3]);
+        centre_diff(ic[0].y, ic[1].y, jc[0].y, jc[1].y, sh[1], sh[4]);
+        centre_diff(ic[0].z, ic[1].z, jc[0].z, jc[1].z, sh[2], sh[5]);
+        centre_diff(ic[2].x, ic[3].x, jc[2].x, jc[3].x, sh[6], sh[9]);
+        centre_diff(ic[2].y, ic[3].y, jc[2].y, jc[3].y, sh[7], sh[10]);
+        centre_diff(ic[2].z, ic[3].z, jc[2].z, jc[3].z, sh[8], sh[11]);
     }
 
     __device__ static __forceinline__ void load_centres(const F32CJerkParams &p, int tile,
@@ -202,7 +200,9 @@ struct F32CJerkKernel {
                 for (int k = 0; k < P; ++k)
 #pragma unroll
                     for (int q = 0; q < 6; ++q) {
-                        const float v = -__fadd_rn(own[k][q], sm.shift[b][q < 3 ? q : q + 1]);
+                        const int h = q < 3 ? q : q + 3;  // hi at h, lo at h + 3
+                        const float v =
+                            -__fadd_rn(__fadd_rn(own[k][q], sm.shift[b][h]), sm.shift[b][h + 3]);
                         ni[k][q] = make_float2(v, v);
                     }
                 float2 acc[P][NC];
