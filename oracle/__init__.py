@@ -18,6 +18,8 @@ no fast-math).  This module only builds it and marshals numpy arrays:
   computes together (Sec. 3).
 * ``hermite``      -- the fourth-order Hermite predictor-corrector integrator
   that uses the jerk (shared time step).
+* ``block_hermite`` -- the same scheme with individual power-of-two block time
+  steps chosen by Aarseth's criterion.
 
 Layouts follow the C ABI: positions/velocities/accelerations are ``[3, n]``
 float64 arrays, masses and potentials ``[n]``.
@@ -86,6 +88,9 @@ class Oracle:
         lib.oracle_forces_jerk.restype = None
         lib.oracle_hermite.argtypes = [i64, vp, vp, vp, d, d, d, i64, vp, vp, vp, ctypes.c_int, vp]
         lib.oracle_hermite.restype = None
+        lib.oracle_block_hermite.argtypes = [i64, vp, vp, vp, d, d, d, d, d, d, d, vp, vp, vp, vp,
+                                             ctypes.POINTER(i64)]
+        lib.oracle_block_hermite.restype = i64
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
         self.lib = lib
@@ -185,6 +190,26 @@ def _hermite(self, pos, vel, mass, eps: float, dt: float, nsteps: int, G: float 
     return pos, vel, acc, jerk, pot, dg
 
 
+def _block_hermite(self, pos, vel, mass, eps: float, t_end: float, dt_max: float, dt_min: float,
+                   eta: float, eta_s: float, G: float = 1.0):
+    """Block-step Hermite to t_end.  Returns (pos, vel, acc, jerk, pot, dt, blocks, evals)."""
+    mass = _c(mass)
+    n = mass.shape[0]
+    pos = _c(pos, (3, n)).copy()
+    vel = _c(vel, (3, n)).copy()
+    acc = np.empty((3, n), np.float64)
+    jerk = np.empty((3, n), np.float64)
+    pot = np.empty(n, np.float64)
+    dt = np.empty(n, np.float64)
+    ev = ctypes.c_int64()
+    blocks = self.lib.oracle_block_hermite(n, _p(pos), _p(vel), _p(mass), float(eps), float(G),
+                                           float(t_end), float(dt_max), float(dt_min), float(eta),
+                                           float(eta_s), _p(acc), _p(jerk), _p(pot), _p(dt),
+                                           ctypes.byref(ev))
+    return pos, vel, acc, jerk, pot, dt, int(blocks), int(ev.value)
+
+
+Oracle.block_hermite = _block_hermite
 Oracle.forces_jerk = _forces_jerk
 Oracle.hermite = _hermite
 

@@ -44,6 +44,22 @@
  *     v1 = v + (a + a1) dt/2 + (j - j1) dt^2/12
  *     x1 = x + (v + v1) dt/2 + (a - a1) dt^2/12
  *
+ * Block (individual) time steps around the Hermite scheme -- the usual partner
+ * of a jerk-based integrator in direct N-body codes (Makino & Aarseth 1992; the
+ * paper does not describe its own stepping).  Every particle i carries its own
+ * time t_i and a power-of-two step dt_i <= dt_max.  One block step:
+ *   t_next = min_i (t_i + dt_i); the active set is {i : t_i + dt_i == t_next};
+ *   every particle is predicted to t_next from its own (t_i, x, v, a, jerk);
+ *   the active particles get a1, j1 from all predicted particles and are
+ *   corrected over their own dt_i; their new step follows Aarseth's criterion
+ *     dt_a = sqrt(eta (|a1| |a2| + |j1|^2) / (|j1| |a3| + |a2|^2))
+ *   with a3 = (12 (a0 - a1) + 6 dt (j0 + j1)) / dt^3 and
+ *        a2 = (-6 (a0 - a1) - dt (4 j0 + 2 j1)) / dt^2 + dt a3 (both at t_next),
+ *   quantised: halve dt_i until dt_i <= dt_a (not below dt_min); double it
+ *   when dt_a >= 2 dt_i, 2 dt_i <= dt_max and t_next is a multiple of 2 dt_i.
+ * Initial steps: dt_i = the largest power of two <= min(dt_max, eta_s |a|/|j|),
+ * not below dt_min.
+ *
  * Layout: positions, velocities and accelerations are structure-of-arrays
  * [3][n] (x row, then y row, then z row), masses and potentials are [n].
  */
@@ -259,4 +275,101 @@ void oracle_hermite(int64_t n, double *pos, double *vel, const double *mass, dou
     free(vp);
     free(a1);
     free(j1);
+}
+
+/* Acceleration, jerk and potential on particle i from all j, with every j taken
+ * at the predicted state (xp, vp) and i at (xi, vi) -- the same definition as
+ * oracle_one_jerk. */
+static void oracle_one_jerk_at(int64_t n, const double *xp, const double *vp, const double *mass,
+                               double eps, double G, int64_t i, double out[7]) {
+    oracle_one_jerk(n, xp, vp, mass, eps, G, i, out);
+}
+
+static double norm3(const double *q, int64_t n, int64_t i) {
+    double x = q[i], y = q[n + i], z = q[2 * n + i];
+    return sqrt(x * x + y * y + z * z);
+}
+
+static double pow2_floor(double x) { return exp2(floor(log2(x))); }
+
+/*
+ * Block-step Hermite until every particle reaches t_end (a multiple of dt_max).
+ * pos, vel in/out [3][n]; acc, jerk out [3][n] at t_end; pot out [n] at the
+ * final predicted state of each particle's last step; dt_out [n] final steps;
+ * returns the number of block steps, and the number of force evaluations of
+ * single particles in *n_evals.  dt_max and dt_min are powers of two.
+ */
+int64_t oracle_block_hermite(int64_t n, double *pos, double *vel, const double *mass, double eps,
+                             double G, double t_end, double dt_max, double dt_min, double eta,
+                             double eta_s, double *acc, double *jerk, double *pot, double *dt_out,
+                             int64_t *n_evals) {
+    double *t = malloc(sizeof(double) * n), *dt = malloc(sizeof(double) * n);
+    double *xp = malloc(sizeof(double) * 3 * n), *vp = malloc(sizeof(double) * 3 * n);
+    oracle_forces_jerk(n, pos, vel, mass, eps, G, acc, jerk, pot);
+    for (int64_t i = 0; i < n; ++i) {
+        double an = norm3(acc, n, i), jn = norm3(jerk, n, i);
+        double d = jn > 0.0 ? eta_s * an / jn : dt_max;
+        if (!(d < dt_max)) d = dt_max;
+        d = pow2_floor(d);
+        if (d < dt_min) d = dt_min;
+        t[i] = 0.0;
+        dt[i] = d;
+    }
+    int64_t blocks = 0, evals = 0;
+    for (;;) {
+        double tn = INFINITY;
+        for (int64_t i = 0; i < n; ++i)
+            if (t[i] + dt[i] < tn) tn = t[i] + dt[i];
+        if (n == 0 || tn > t_end) break;
+        for (int64_t i = 0; i < n; ++i) { /* predict every particle to tn */
+            double h = tn - t[i], h2 = h * h, h3 = h2 * h;
+            for (int d = 0; d < 3; ++d) {
+                int64_t q = d * n + i;
+                xp[q] = pos[q] + vel[q] * h + acc[q] * h2 / 2.0 + jerk[q] * h3 / 6.0;
+                vp[q] = vel[q] + acc[q] * h + jerk[q] * h2 / 2.0;
+            }
+        }
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n; ++i) {
+            if (t[i] + dt[i] != tn) continue;
+            double o[7];
+            oracle_one_jerk_at(n, xp, vp, mass, eps, G, i, o);
+            double h = dt[i], h2 = h * h, h3 = h2 * h;
+            double a1[3], j1[3], a2[3], a3[3];
+            for (int d = 0; d < 3; ++d) {
+                int64_t q = d * n + i;
+                a1[d] = o[d];
+                j1[d] = o[3 + d];
+                double v1 = vel[q] + (acc[q] + a1[d]) * h / 2.0 + (jerk[q] - j1[d]) * h2 / 12.0;
+                pos[q] = pos[q] + (vel[q] + v1) * h / 2.0 + (acc[q] - a1[d]) * h2 / 12.0;
+                vel[q] = v1;
+                a3[d] = (12.0 * (acc[q] - a1[d]) + 6.0 * h * (jerk[q] + j1[d])) / h3;
+                a2[d] = (-6.0 * (acc[q] - a1[d]) - h * (4.0 * jerk[q] + 2.0 * j1[d])) / h2 + h * a3[d];
+                acc[q] = a1[d];
+                jerk[q] = j1[d];
+            }
+            pot[i] = o[6];
+            double na = sqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
+            double nj = sqrt(j1[0] * j1[0] + j1[1] * j1[1] + j1[2] * j1[2]);
+            double n2 = sqrt(a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2]);
+            double n3 = sqrt(a3[0] * a3[0] + a3[1] * a3[1] + a3[2] * a3[2]);
+            double den = nj * n3 + n2 * n2;
+            double da = den > 0.0 ? sqrt(eta * (na * n2 + nj * nj) / den) : dt_max;
+            double nd = h;
+            while (nd > da && nd > dt_min) nd /= 2.0;
+            if (nd == h && da >= 2.0 * h && 2.0 * h <= dt_max && fmod(tn, 2.0 * h) == 0.0) nd = 2.0 * h;
+            t[i] = tn;
+            dt[i] = nd;
+        }
+        for (int64_t i = 0; i < n; ++i)
+            if (t[i] == tn) ++evals;
+        ++blocks;
+    }
+    for (int64_t i = 0; i < n; ++i) dt_out[i] = dt[i];
+    *n_evals = evals;
+    free(t);
+    free(dt);
+    free(xp);
+    free(vp);
+    return blocks;
 }

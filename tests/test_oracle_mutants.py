@@ -15,6 +15,7 @@ import tempfile
 import pytest
 
 import oracle as oracle_pkg
+from tests import test_oracle_block_pins as bpins
 from tests import test_oracle_jerk_pins as jpins
 from tests import test_oracle_pins as pins
 
@@ -45,6 +46,10 @@ MUTANTS = {
     "jerk_velocity_order": ("double ux = vx[j] - vx[i], uy = vy[j] - vy[i], uz = vz[j] - vz[i];",
                             "double ux = vx[i] - vx[j], uy = vy[i] - vy[j], uz = vz[i] - vz[j];"),
     "jerk_self_term_kept": ("        if (j == i) continue;\n        double rx", "        double rx"),
+    "block_criterion": ("double da = den > 0.0 ? sqrt(eta * (na * n2 + nj * nj) / den) : dt_max;",
+                        "double da = den > 0.0 ? sqrt(eta * (na * n2 + nj * nj) / den) * 8.0 : dt_max;"),
+    "block_prediction": ("xp[q] = pos[q] + vel[q] * h + acc[q] * h2 / 2.0 + jerk[q] * h3 / 6.0;",
+                         "xp[q] = pos[q] + vel[q] * h + acc[q] * h2 / 2.0;"),
     "hermite_corrector": ("(jerk[q] - j1[q]) * dt2 / 12.0;", "(jerk[q] - j1[q]) * dt2 / 6.0;"),
     "hermite_predictor": ("+ jerk[q] * dt3 / 6.0;", "+ 0.0 * dt3;"),
 }
@@ -77,6 +82,9 @@ def _pin_calls(orc):
         lambda: jpins.test_jerk_is_the_time_derivative_of_the_acceleration(orc, 0.05),
         lambda: jpins.test_jerk_newton_third_law_and_scaling(orc),
         lambda: jpins.test_hermite_is_fourth_order(orc),
+        lambda: bpins.test_equal_steps_reduce_to_shared_hermite(orc),
+        lambda: bpins.test_block_invariants_and_synchronisation(orc),
+        lambda: bpins.test_block_steps_converge_to_accurate_reference(orc),
     ]
     return calls
 
