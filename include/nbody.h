@@ -180,6 +180,39 @@ int nbody_step_hermite(nbody_ctx *ctx, double *pos, double *vel, const double *m
                        double *jerk, double *pot, double dt, int32_t nsteps, double *diag,
                        void *stream);
 
+/*
+ * Individual (block) time steps around the Hermite scheme -- the usual partner
+ * of a jerk-based integrator (Makino & Aarseth 1992; the paper computes the
+ * jerk, Sec. 3, but does not describe its stepping).  Every particle keeps its
+ * own time and a power-of-two step; one block step predicts all particles to
+ * t_next = min(t_i + dt_i), evaluates acceleration and jerk of the active
+ * particles (t_i + dt_i == t_next) against all predicted ones, corrects those
+ * and picks their next step by Aarseth's criterion
+ *     dt = sqrt(eta (|a| |a''| + |a'|^2) / (|a'| |a'''| + |a''|^2)),
+ * halving it until below that value (not below dt_min) or doubling it when
+ * allowed (<= dt_max, t_next a multiple of the doubled step).  The schedule
+ * (min, compaction of the active set, work queue) runs on the device, so each
+ * block step is one replayed CUDA graph.
+ *
+ * nbody_block_start: computes a, jerk, pot at the current state (t = 0) and the
+ *   initial steps, the largest power of two <= min(dt_max, eta_s |a|/|a'|),
+ *   not below dt_min.  dt_max and dt_min are powers of two.
+ * nbody_block_advance: block steps until every particle reaches t_end (a
+ *   multiple of dt_max, so all particles are synchronised there); *blocks and
+ *   *evals (may be NULL) receive the totals since nbody_block_start.  Pass the
+ *   same arrays as to nbody_block_start; acc/jerk/pot hold each particle's last
+ *   corrector values (taken at its last predicted state).
+ * nbody_block_state: copies every particle's time and step to host arrays.
+ * All arrays must be device memory (NBODY_EINVAL otherwise).
+ */
+int nbody_block_start(nbody_ctx *ctx, const double *pos, const double *vel, const double *mass,
+                      double *acc, double *jerk, double *pot, double dt_max, double dt_min,
+                      double eta, double eta_s, void *stream);
+int nbody_block_advance(nbody_ctx *ctx, double *pos, double *vel, const double *mass, double *acc,
+                        double *jerk, double *pot, double t_end, int64_t *blocks, int64_t *evals,
+                        void *stream);
+int nbody_block_state(nbody_ctx *ctx, double *t_host, double *dt_host, void *stream);
+
 /* Tile shape of the acceleration + jerk kernel in use (zeros before its first use or in F64). */
 int nbody_get_jerk_tiles(const nbody_ctx *ctx, nbody_tiles *out);
 

@@ -46,7 +46,8 @@ EXPORTED = ("nbody_init", "nbody_destroy", "nbody_forces", "nbody_step", "nbody_
             "nbody_tune", "nbody_get_tiles", "nbody_tiles_supported", "nbody_profile_read",
             "nbody_kernel_launches", "nbody_strerror", "nbody_last_error_message",
             "nbody_forces_noalloc", "nbody_measure_pipes", "nbody_forces_jerk",
-            "nbody_step_hermite", "nbody_get_jerk_tiles", "nbody_set_jerk_tiles")
+            "nbody_step_hermite", "nbody_get_jerk_tiles", "nbody_set_jerk_tiles",
+            "nbody_block_start", "nbody_block_advance", "nbody_block_state")
 
 
 class NBodyTiles(ctypes.Structure):
@@ -119,6 +120,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.nbody_get_jerk_tiles.restype = ctypes.c_int
         lib.nbody_set_jerk_tiles.argtypes = [vp, ctypes.POINTER(NBodyTiles)]
         lib.nbody_set_jerk_tiles.restype = ctypes.c_int
+        lib.nbody_block_start.argtypes = [vp, vp, vp, vp, vp, vp, vp, d, d, d, d, vp]
+        lib.nbody_block_start.restype = ctypes.c_int
+        lib.nbody_block_advance.argtypes = [vp, vp, vp, vp, vp, vp, vp, d, ctypes.POINTER(i64),
+                                            ctypes.POINTER(i64), vp]
+        lib.nbody_block_advance.restype = ctypes.c_int
+        lib.nbody_block_state.argtypes = [vp, vp, vp, vp]
+        lib.nbody_block_state.restype = ctypes.c_int
         lib.nbody_measure_pipes.argtypes = [ctypes.POINTER(d), ctypes.c_int]
         lib.nbody_measure_pipes.restype = ctypes.c_int
         _lib = lib
@@ -278,6 +286,43 @@ def nbody_step_hermite(ctx: Context, pos, vel, mass, acc, jerk, pot, dt: float, 
                                    _ptr(diag, (int(nsteps), ctx.n_clusters, 9), "diag", keep),
                                    _stream(stream))
     _check(ctx, rc, "nbody_step_hermite")
+
+
+def nbody_block_start(ctx: Context, pos, vel, mass, acc, jerk, pot, dt_max: float, dt_min: float,
+                      eta: float, eta_s: float, stream=None) -> None:
+    """Start individual block time steps (see nbody_block_start in nbody.h)."""
+    n = ctx.n
+    keep = []
+    rc = load().nbody_block_start(ctx.handle, _ptr(pos, (3, n), "pos", keep),
+                                  _ptr(vel, (3, n), "vel", keep), _ptr(mass, (n,), "mass", keep),
+                                  _ptr(acc, (3, n), "acc", keep), _ptr(jerk, (3, n), "jerk", keep),
+                                  _ptr(pot, (n,), "pot", keep), float(dt_max), float(dt_min),
+                                  float(eta), float(eta_s), _stream(stream))
+    _check(ctx, rc, "nbody_block_start")
+
+
+def nbody_block_advance(ctx: Context, pos, vel, mass, acc, jerk, pot, t_end: float, stream=None):
+    """Block steps until t_end; returns (block steps, single-particle evaluations) so far."""
+    n = ctx.n
+    keep = []
+    blocks, evals = ctypes.c_int64(), ctypes.c_int64()
+    rc = load().nbody_block_advance(ctx.handle, _ptr(pos, (3, n), "pos", keep),
+                                    _ptr(vel, (3, n), "vel", keep), _ptr(mass, (n,), "mass", keep),
+                                    _ptr(acc, (3, n), "acc", keep), _ptr(jerk, (3, n), "jerk", keep),
+                                    _ptr(pot, (n,), "pot", keep), float(t_end), ctypes.byref(blocks),
+                                    ctypes.byref(evals), _stream(stream))
+    _check(ctx, rc, "nbody_block_advance")
+    return blocks.value, evals.value
+
+
+def nbody_block_state(ctx: Context, stream=None):
+    """(t[n], dt[n]) of every particle."""
+    t = np.empty(ctx.n, np.float64)
+    dt = np.empty(ctx.n, np.float64)
+    rc = load().nbody_block_state(ctx.handle, ctypes.c_void_p(t.ctypes.data),
+                                  ctypes.c_void_p(dt.ctypes.data), _stream(stream))
+    _check(ctx, rc, "nbody_block_state")
+    return t, dt
 
 
 def nbody_get_jerk_tiles(ctx: Context):

@@ -57,6 +57,21 @@ struct JerkPath {
     double *xp = nullptr, *vp = nullptr, *a1 = nullptr, *j1 = nullptr;
 };
 
+// Individual (block) time steps: per-particle times and steps, the device-side
+// scheduler's scratch and the subset kernel's partial sums.
+struct BlockState {
+    bool started = false;
+    double dt_max = 0.0, dt_min = 0.0, eta = 0.0;
+    int cs = 0, workers = 1, max_split = 1, max_items = 0;
+    double *t = nullptr, *dt = nullptr, *part = nullptr, *partial = nullptr, *p1 = nullptr;
+    uint8_t *flag = nullptr;
+    int *cnt = nullptr, *chunk_off = nullptr, *act_begin = nullptr, *act_n = nullptr;
+    int *ich_off = nullptr, *item_off = nullptr;
+    int32_t *act = nullptr, *inv = nullptr;
+    SubItem *items = nullptr;
+    BlockScalars *sc = nullptr;
+};
+
 }  // namespace
 
 struct nbody_ctx {
@@ -117,6 +132,9 @@ struct nbody_ctx {
 
     // acceleration + jerk path
     JerkPath jp;
+
+    // block time steps
+    BlockState bs;
 
     // graphs
     cudaStream_t cap_stream = nullptr;
@@ -731,6 +749,143 @@ int enqueue_hermite_step(nbody_ctx *ctx, const Arrays &a, double dt, bool reorde
     return NBODY_OK;
 }
 
+// ------------------------------------------------------------------ block steps
+
+void free_block(nbody_ctx *ctx) {
+    BlockState &b = ctx->bs;
+    for (double **q : {&b.t, &b.dt, &b.part, &b.partial, &b.p1}) dev_free(q);
+    dev_free(&b.flag);
+    for (int **q : {&b.cnt, &b.chunk_off, &b.act_begin, &b.act_n, &b.ich_off, &b.item_off}) dev_free(q);
+    dev_free(&b.act);
+    dev_free(&b.inv);
+    dev_free(&b.items);
+    dev_free(&b.sc);
+    b.started = false;
+}
+
+int alloc_block(nbody_ctx *ctx) {
+    BlockState &b = ctx->bs;
+    free_block(ctx);
+    int rc;
+    const size_t n = (size_t)ctx->n, nc = (size_t)std::max(ctx->n_chunks, 1), ncl = (size_t)ctx->ncl;
+    if (ctx->mode == NBODY_F32C) {
+        const nbody_tiles &t = ctx->jp.tiles;
+        b.cs = t.block * t.p;
+        const int occ = subset_occupancy(t.block, t.p, t.tj, t.ctas_per_sm, ctx->eps_zero);
+        if (occ <= 0) return fail(ctx, NBODY_EUNSUPPORTED, "no subset kernel for the jerk tile shape");
+        b.workers = occ * ctx->sms;
+        b.max_split = 64;
+        b.max_items = std::max(2 * b.workers, ctx->jp.n_tiles);
+        if ((rc = dev_alloc(ctx, &b.partial, (size_t)2 * b.workers * 7 * b.cs))) return rc;
+        if ((rc = dev_alloc(ctx, &b.inv, n))) return rc;
+    } else {
+        b.cs = kF64Block;
+        b.workers = 1;
+        b.max_split = 1;
+        b.max_items = std::max(ctx->n_blocks64, 1);
+    }
+    for (double **q : {&b.t, &b.dt, &b.p1})
+        if ((rc = dev_alloc(ctx, q, n))) return rc;
+    if ((rc = dev_alloc(ctx, &b.part, nc))) return rc;
+    if ((rc = dev_alloc(ctx, &b.flag, n))) return rc;
+    for (int **q : {&b.cnt, &b.chunk_off})
+        if ((rc = dev_alloc(ctx, q, nc))) return rc;
+    for (int **q : {&b.act_begin, &b.act_n, &b.ich_off, &b.item_off})
+        if ((rc = dev_alloc(ctx, q, ncl + 1))) return rc;
+    if ((rc = dev_alloc(ctx, &b.act, n))) return rc;
+    if ((rc = dev_alloc(ctx, &b.items, (size_t)b.max_items))) return rc;
+    if ((rc = dev_alloc(ctx, &b.sc, 1))) return rc;
+    NB_CUDA(cudaMemset(b.sc, 0, sizeof(BlockScalars)));
+    return NBODY_OK;
+}
+
+BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
+    BlockState &bs = ctx->bs;
+    JerkPath &j = ctx->jp;
+    BlockLaunch b{};
+    b.n = ctx->n;
+    b.ncl = ctx->ncl;
+    b.n_chunks = ctx->n_chunks;
+    b.cs = bs.cs;
+    b.workers = bs.workers;
+    b.max_split = bs.max_split;
+    b.max_items = bs.max_items;
+    b.chunks = ctx->chunks;
+    b.chunk_first = ctx->chunk_first;
+    b.cl = ctx->mode == NBODY_F32C ? j.dcl : ctx->dcl;
+    b.t = bs.t;
+    b.dt = bs.dt;
+    b.part = bs.part;
+    b.pos = a.pos;
+    b.vel = a.vel;
+    b.acc = a.acc;
+    b.jerk = a.jerk;
+    b.xp = j.xp;
+    b.vp = j.vp;
+    b.flag = bs.flag;
+    b.cnt = bs.cnt;
+    b.chunk_off = bs.chunk_off;
+    b.act_begin = bs.act_begin;
+    b.act_n = bs.act_n;
+    b.ich_off = bs.ich_off;
+    b.item_off = bs.item_off;
+    b.act = bs.act;
+    b.items = bs.items;
+    b.sc = bs.sc;
+    return b;
+}
+
+// One block step (see block.cu): schedule, predict, pack the predicted j-set,
+// forces + jerks of the active subset, correct and re-step the active ones.
+int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, bool capturing,
+                       cudaStream_t s, int *kernels) {
+    if (ctx->n == 0) return NBODY_OK;
+    BlockState &bs = ctx->bs;
+    JerkPath &j = ctx->jp;
+    const BlockLaunch b = block_launch(ctx, a);
+    NB_CUDA(launch_block_prepare(b, s, kernels));
+    int rc;
+    if (ctx->mode == NBODY_F32C) {
+        if (reorder) {
+            NB_CUDA(launch_reorder(j.xp, ctx->n, ctx->chunks, ctx->n_chunks, ctx->chunk_first, ctx->ncl,
+                                   j.dcl, ctx->bpart, ctx->bbox, ctx->keys, ctx->vals, ctx->sort_n,
+                                   ctx->max_cluster, j.perm, s, kernels));
+        }
+        PackParams pp{j.xp, a.mass, j.perm, j.dcl, j.tile_cluster, j.tc, ctx->n,
+                      j.px, j.py, j.pz, j.pm, j.chl};
+        NB_CUDA(launch_pack(j.n_tiles, pp, s));
+        NB_CUDA(launch_pack_vel(j.n_tiles, j.vp, j.perm, j.dcl, j.tile_cluster, j.tc, ctx->n, j.pvx,
+                                j.pvy, j.pvz, j.vchl, s));
+        NB_CUDA(launch_inverse_perm(j.n_pad, j.perm, bs.inv, s));
+        *kernels += 3;
+        NB_CUDA(launch_block_queue(b, bs.inv, s, kernels));
+        NB_CUDA(cudaMemsetAsync(j.counters, 0, ((size_t)j.n_tiles + 1) * sizeof(int), s));
+        F32CSubsetParams q{};
+        q.base = jerk_params(ctx, j.a1, j.j1, bs.p1);
+        q.act_slot = bs.act;
+        q.items = bs.items;
+        q.n_items = &bs.sc->n_items;
+        q.partial = bs.partial;
+        q.tcj = j.tc;
+        if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
+        NB_CUDA(launch_subset_f32c(j.tiles.block, j.tiles.p, j.tiles.tj, j.tiles.ctas_per_sm,
+                                   ctx->eps_zero, bs.workers, q, s));
+        ++*kernels;
+        if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
+    } else {
+        NB_CUDA(launch_block_queue(b, nullptr, s, kernels));
+        if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
+        NB_CUDA(launch_subset_f64(bs.max_items, j.xp, j.vp, a.mass, ctx->dcl, bs.items,
+                                  &bs.sc->n_items, bs.act, ctx->n, ctx->G, j.a1, j.j1, bs.p1, s));
+        ++*kernels;
+        if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
+    }
+    NB_CUDA(launch_block_correct(ctx->n, bs.flag, bs.sc, bs.t, bs.dt, a.pos, a.vel, a.acc, a.jerk,
+                                 a.pot, j.a1, j.j1, bs.p1, bs.dt_max, bs.dt_min, bs.eta, s));
+    ++*kernels;
+    return NBODY_OK;
+}
+
 // ------------------------------------------------------------------ autotuner
 
 std::string tune_key(const nbody_ctx *ctx) {
@@ -787,60 +942,88 @@ __global__ void tune_fill_kernel(float *px, float *py, float *pz, float *pm, int
     }
 }
 
+// Time one tile shape: build its geometry (j-ranges scaled by jfrac), fill the
+// packed arrays with a synthetic cube, best of `reps` timed launches (after one
+// warm-up).  Returns the time in ms, or a negative status.
+double time_shape(nbody_ctx *ctx, nbody_tiles t, double jfrac, int reps, double *acc, cudaEvent_t e0,
+                  cudaEvent_t e1, cudaStream_t s, int *rc) {
+    if ((*rc = build_f32c(ctx, t, jfrac))) return -1.0;
+    tune_fill_kernel<<<256, 256, 0, s>>>(ctx->px, ctx->py, ctx->pz, ctx->pm, ctx->n_pad);
+    if (cudaMemsetAsync(ctx->chl, 0, (size_t)ctx->n_tiles * 2 * sizeof(float4), s) != cudaSuccess) {
+        *rc = cuda_fail(ctx, cudaGetLastError(), "tuner memset");
+        return -1.0;
+    }
+    float best = 1e30f;
+    for (int rep = 0; rep <= reps; ++rep) {
+        F32CParams fp{};
+        fp.px = ctx->px; fp.py = ctx->py; fp.pz = ctx->pz; fp.pm = ctx->pm;
+        fp.chl = ctx->chl; fp.perm = ctx->perm; fp.cl = ctx->dcl;
+        fp.items = ctx->items; fp.n_items = ctx->n_items; fp.tc = ctx->tc;
+        fp.counters = ctx->counters; fp.partial = ctx->partial;
+        fp.acc = acc; fp.pot = acc + 3 * ctx->n; fp.vel = nullptr; fp.n = ctx->n; fp.G = 1.0;
+        cudaError_t e = cudaMemsetAsync(ctx->counters, 0, ((size_t)ctx->n_tiles + 1) * sizeof(int), s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess)
+            e = launch_f32c(ctx->tiles.block, ctx->tiles.p, ctx->tiles.tj, ctx->tiles.ctas_per_sm,
+                            ctx->eps_zero, ctx->grid, fp, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            *rc = cuda_fail(ctx, e, "tuner launch");
+            return -1.0;
+        }
+        ctx->launches += 1;
+        if (rep > 0) best = std::min(best, ms);
+    }
+    return best;
+}
+
+// Two rounds: every compiled shape (and three split counts) on a short proxy
+// (j-ranges truncated to ~1e11 pairs), then the three fastest again on a proxy
+// four times longer; the fastest of those is kept and cached.
 int run_tuner(nbody_ctx *ctx, cudaStream_t s) {
     if (ctx->mode != NBODY_F32C || ctx->n == 0) return NBODY_OK;
     int blocks[64], ps[64], tjs[64], mbs[64];
     const int ns = std::min(64, f32c_shapes(blocks, ps, tjs, mbs, 64));
     double total_pairs = 0.0;
     for (int k = 0; k < ctx->ncl; ++k) total_pairs += (double)cluster_n(ctx, k) * cluster_n(ctx, k);
-    // bound each timed launch to ~1e11 pairs (~40 ms) by truncating the j-ranges
     const double jfrac = std::min(1.0, 1.0e11 / std::max(total_pairs, 1.0));
-    double acc_scratch_bytes = (double)ctx->n * 4 * sizeof(double);
     double *acc = nullptr;
-    NB_CUDA(cudaMalloc(&acc, (size_t)acc_scratch_bytes));
+    NB_CUDA(cudaMalloc(&acc, (size_t)ctx->n * 4 * sizeof(double)));
     cudaEvent_t e0, e1;
     NB_CUDA(cudaEventCreate(&e0));
     NB_CUDA(cudaEventCreate(&e1));
-    nbody_tiles best{0, 0, 0, 0, 0};
-    double best_ms = 1e30;
+    std::vector<std::pair<double, nbody_tiles>> timed;
     int rc = NBODY_OK;
     for (int c = 0; c < ns && rc == NBODY_OK; ++c) {
         nbody_tiles t{blocks[c], ps[c], tjs[c], 0, mbs[c]};
         if ((int64_t)t.block * t.p > 2 * std::max<int64_t>(ctx->max_cluster, 128)) continue;
+        const int occ = f32c_occupancy(t.block, t.p, t.tj, t.ctas_per_sm, ctx->eps_zero);
+        const int base = choose_split(ctx, t.block * t.p, t.tj, occ * ctx->sms);
         for (int sv = 0; sv < 3 && rc == NBODY_OK; ++sv) {
             nbody_tiles tt = t;
-            if (sv > 0) {
-                const int occ = f32c_occupancy(t.block, t.p, t.tj, t.ctas_per_sm, ctx->eps_zero);
-                const int base = choose_split(ctx, t.block * t.p, t.tj, occ * ctx->sms);
-                tt.split = sv == 1 ? base * 2 : std::max(1, base / 2);
-                if (tt.split == base) continue;
-            }
-            if ((rc = build_f32c(ctx, tt, jfrac))) break;
-            tune_fill_kernel<<<256, 256, 0, s>>>(ctx->px, ctx->py, ctx->pz, ctx->pm, ctx->n_pad);
-            NB_CUDA(cudaMemsetAsync(ctx->chl, 0, (size_t)ctx->n_tiles * 2 * sizeof(float4), s));
-            Arrays a{nullptr, nullptr, acc, acc + 3 * ctx->n, nullptr, nullptr};
-            float ms_best = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {
-                F32CParams fp{};
-                fp.px = ctx->px; fp.py = ctx->py; fp.pz = ctx->pz; fp.pm = ctx->pm;
-                fp.chl = ctx->chl; fp.perm = ctx->perm; fp.cl = ctx->dcl;
-                fp.items = ctx->items; fp.n_items = ctx->n_items; fp.tc = ctx->tc;
-                fp.counters = ctx->counters; fp.partial = ctx->partial;
-                fp.acc = a.acc; fp.pot = a.pot; fp.vel = nullptr; fp.n = ctx->n; fp.G = 1.0;
-                NB_CUDA(cudaMemsetAsync(ctx->counters, 0, ((size_t)ctx->n_tiles + 1) * sizeof(int), s));
-                NB_CUDA(cudaEventRecord(e0, s));
-                NB_CUDA(launch_f32c(tt.block, tt.p, tt.tj, tt.ctas_per_sm, ctx->eps_zero, ctx->grid,
-                                    fp, s));
-                NB_CUDA(cudaEventRecord(e1, s));
-                NB_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.0f;
-                NB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (rep > 0) ms_best = std::min(ms_best, ms);
-                ctx->launches += 1;
-            }
-            if (ms_best < best_ms) {
-                best_ms = ms_best;
-                best = ctx->tiles;
+            tt.split = sv == 0 ? base : sv == 1 ? base * 2 : std::max(1, base / 2);
+            if (sv > 0 && tt.split == base) continue;
+            const double ms = time_shape(ctx, tt, jfrac, 2, acc, e0, e1, s, &rc);
+            if (rc == NBODY_OK) timed.push_back({ms, ctx->tiles});
+        }
+    }
+    nbody_tiles best{0, 0, 0, 0, 0};
+    double best_ms = 1e30;
+    if (rc == NBODY_OK && !timed.empty()) {
+        std::stable_sort(timed.begin(), timed.end(),
+                         [](const std::pair<double, nbody_tiles> &x, const std::pair<double, nbody_tiles> &y) {
+                             return x.first < y.first;
+                         });
+        const double jfrac2 = std::min(1.0, 4.0 * jfrac);
+        for (size_t k = 0; k < std::min<size_t>(3, timed.size()) && rc == NBODY_OK; ++k) {
+            const double ms = jfrac2 > jfrac ? time_shape(ctx, timed[k].second, jfrac2, 2, acc, e0, e1, s, &rc)
+                                             : timed[k].first;
+            if (rc == NBODY_OK && ms < best_ms) {
+                best_ms = ms;
+                best = timed[k].second;
             }
         }
     }
@@ -891,6 +1074,7 @@ void nbody_destroy(nbody_ctx *ctx) {
     drop_graphs(ctx);
     free_f32c(ctx);
     free_jerk(ctx);
+    free_block(ctx);
     dev_free(&ctx->blocks64);
     dev_free(&ctx->chunks);
     dev_free(&ctx->chunk_first);
@@ -1077,9 +1261,10 @@ int step_common(nbody_ctx *ctx, double *pos, double *vel, const double *mass, do
     if ((rc = check_ptr(ctx, pos, "pos", true)) || (rc = check_ptr(ctx, vel, "vel", true)) ||
         (rc = check_ptr(ctx, mass, "mass", true)) || (rc = check_ptr(ctx, acc, "acc", true)) ||
         (rc = check_ptr(ctx, pot, "pot", false)) || (rc = check_ptr(ctx, diag, "diag", false)) ||
-        (rc = check_ptr(ctx, jerk, "jerk", kind == 1)))
+        (rc = check_ptr(ctx, jerk, "jerk", kind >= 1)))
         return rc;
-    if (kind == 1 && (rc = ensure_jerk(ctx))) return rc;
+    if (kind >= 1 && (rc = ensure_jerk(ctx))) return rc;
+    if (kind == 2 && !ctx->bs.started) return fail(ctx, NBODY_EINVAL, "nbody_block_start was not called");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n3b = 3 * ctx->n * sizeof(double), nb = ctx->n * sizeof(double);
     const size_t db = (size_t)nsteps * ctx->ncl * 9 * sizeof(double);
@@ -1105,8 +1290,9 @@ int step_common(nbody_ctx *ctx, double *pos, double *vel, const double *mass, do
         if (slot < -1) return ctx->sticky;
         if (!use_graph) {
             int k = 0;
-            rc = kind == 1 ? enqueue_hermite_step(ctx, a, dt, reorder, slot, false, s, &k)
-                           : enqueue_step(ctx, a, dt, reorder, slot, false, s, &k);
+            rc = kind == 2   ? enqueue_block_step(ctx, a, reorder, slot, false, s, &k)
+                 : kind == 1 ? enqueue_hermite_step(ctx, a, dt, reorder, slot, false, s, &k)
+                             : enqueue_step(ctx, a, dt, reorder, slot, false, s, &k);
             ctx->launches += k;
             if (rc) return rc;
         } else {
@@ -1122,8 +1308,9 @@ int step_common(nbody_ctx *ctx, double *pos, double *vel, const double *mass, do
                               (int)reorder, slot, nullptr, 0};
                 NB_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
                 int k = 0;
-                rc = kind == 1 ? enqueue_hermite_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k)
-                               : enqueue_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k);
+                rc = kind == 2   ? enqueue_block_step(ctx, a, reorder, slot, true, ctx->cap_stream, &k)
+                     : kind == 1 ? enqueue_hermite_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k)
+                                 : enqueue_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k);
                 cudaGraph_t graph = nullptr;
                 cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
                 if (rc) {
@@ -1205,6 +1392,77 @@ int nbody_forces_jerk(nbody_ctx *ctx, const double *pos, const double *vel, cons
     if (spot) NB_CUDA(cudaMemcpyAsync(pot, dpot, nb, cudaMemcpyDeviceToHost, s));
     if (sacc || sjerk || spot) NB_CUDA(cudaStreamSynchronize(s));
     return check_finite(ctx, (const double *)dacc, (const double *)dpot, s);
+}
+
+static bool pow2(double x) { return x > 0.0 && std::isfinite(x) && std::exp2(std::round(std::log2(x))) == x; }
+
+int nbody_block_start(nbody_ctx *ctx, const double *pos, const double *vel, const double *mass,
+                      double *acc, double *jerk, double *pot, double dt_max, double dt_min,
+                      double eta, double eta_s, void *stream) {
+    int rc = guard(ctx);
+    if (rc) return rc;
+    if (!pow2(dt_max) || !pow2(dt_min) || dt_min > dt_max || !(eta > 0.0) || !(eta_s > 0.0) ||
+        !std::isfinite(eta) || !std::isfinite(eta_s))
+        return fail(ctx, NBODY_EINVAL, "block steps: dt_max, dt_min must be powers of two, eta > 0");
+    if (ctx->n == 0) return NBODY_OK;
+    for (const void *q : {(const void *)pos, (const void *)vel, (const void *)mass, (const void *)acc,
+                          (const void *)jerk})
+        if (!q || !is_device_ptr(q)) return fail(ctx, NBODY_EINVAL, "block steps need device arrays");
+    if (pot && !is_device_ptr(pot)) return fail(ctx, NBODY_EINVAL, "block steps need device arrays");
+    if ((rc = ensure_jerk(ctx))) return rc;
+    if ((rc = alloc_block(ctx))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = nbody_forces_jerk(ctx, pos, vel, mass, acc, jerk, pot, stream))) return rc;
+    BlockState &b = ctx->bs;
+    b.dt_max = dt_max;
+    b.dt_min = dt_min;
+    b.eta = eta;
+    NB_CUDA(launch_block_init(ctx->n, acc, jerk, dt_max, dt_min, eta_s, b.t, b.dt, s));
+    ctx->launches += 1;
+    NB_CUDA(cudaMemsetAsync(b.sc, 0, sizeof(BlockScalars), s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    b.started = true;
+    return NBODY_OK;
+}
+
+int nbody_block_advance(nbody_ctx *ctx, double *pos, double *vel, const double *mass, double *acc,
+                        double *jerk, double *pot, double t_end, int64_t *blocks, int64_t *evals,
+                        void *stream) {
+    int rc = guard(ctx);
+    if (rc) return rc;
+    if (ctx->n == 0) return NBODY_OK;
+    BlockState &b = ctx->bs;
+    if (!b.started) return fail(ctx, NBODY_EINVAL, "nbody_block_start was not called");
+    if (!std::isfinite(t_end) || t_end < 0.0 || std::fmod(t_end, b.dt_max) != 0.0)
+        return fail(ctx, NBODY_EINVAL, "t_end must be a non-negative multiple of dt_max");
+    for (const void *q : {(const void *)pos, (const void *)vel, (const void *)mass, (const void *)acc,
+                          (const void *)jerk})
+        if (!q || !is_device_ptr(q)) return fail(ctx, NBODY_EINVAL, "block steps need device arrays");
+    if (pot && !is_device_ptr(pot)) return fail(ctx, NBODY_EINVAL, "block steps need device arrays");
+    cudaStream_t s = (cudaStream_t)stream;
+    NB_CUDA(cudaMemcpyAsync(&b.sc->t_end, &t_end, sizeof(double), cudaMemcpyHostToDevice, s));
+    BlockScalars h{};
+    for (;;) {
+        if ((rc = step_common(ctx, pos, vel, mass, acc, jerk, pot, 0.0, 16, nullptr, stream, 2))) return rc;
+        NB_CUDA(cudaMemcpyAsync(&h, b.sc, sizeof h, cudaMemcpyDeviceToHost, s));
+        NB_CUDA(cudaStreamSynchronize(s));
+        if (!(h.t_next <= t_end)) break;
+    }
+    if (blocks) *blocks = h.blocks;
+    if (evals) *evals = h.evals;
+    return NBODY_OK;
+}
+
+int nbody_block_state(nbody_ctx *ctx, double *t_host, double *dt_host, void *stream) {
+    int rc = guard(ctx);
+    if (rc) return rc;
+    if (ctx->n == 0) return NBODY_OK;
+    if (!ctx->bs.started) return fail(ctx, NBODY_EINVAL, "nbody_block_start was not called");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (t_host) NB_CUDA(cudaMemcpyAsync(t_host, ctx->bs.t, ctx->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (dt_host) NB_CUDA(cudaMemcpyAsync(dt_host, ctx->bs.dt, ctx->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    return NBODY_OK;
 }
 
 int nbody_get_jerk_tiles(const nbody_ctx *ctx, nbody_tiles *out) {

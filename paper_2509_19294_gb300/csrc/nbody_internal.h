@@ -114,6 +114,69 @@ struct Chunk {
     int64_t begin, end;  // caller rows [begin, end)
 };
 
+// Block time steps (block.cu).  One work item: an i-chunk of the active list
+// (positions a0 .. a0 + na - 1, all in one cluster) against one j-range split.
+struct SubItem {
+    int32_t a0, na, cluster, chunk;
+    int32_t jt0, jt1, split, nsplit;
+    int32_t pbase, pad;
+};
+
+// Device-side scalars of the block-step scheduler.
+struct BlockScalars {
+    double t_next;   // time of the current block step
+    double t_end;    // stop time (set by the host before each batch)
+    int n_active, n_chunks, split, n_items;
+    long long blocks, evals;  // block steps taken, single-particle evaluations
+};
+
+// Subset acceleration + jerk kernel: base carries the j-set (the jerk path's
+// packed predicted particles), perm (slot -> row) and the outputs (rows).
+struct F32CSubsetParams {
+    F32CJerkParams base;
+    const int32_t *act_slot;  // active list: j-set slot of each active particle
+    const SubItem *items;
+    const int *n_items;       // device count
+    double *partial;          // [slots][7][block * p]
+    int tcj;                  // j-set centre-tile size
+};
+
+struct BlockLaunch {
+    int64_t n;
+    int ncl, n_chunks, cs, workers, max_split, max_items;
+    const Chunk *chunks;
+    const int32_t *chunk_first;
+    const ClusterDev *cl;
+    double *t, *dt, *part;
+    double *pos, *vel, *acc, *jerk, *xp, *vp;
+    uint8_t *flag;
+    int *cnt, *chunk_off, *act_begin, *act_n, *ich_off, *item_off;
+    int32_t *act;
+    SubItem *items;
+    BlockScalars *sc;
+};
+
+cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, double dt_max,
+                              double dt_min, double eta_s, double *t, double *dt, cudaStream_t s);
+// t_next, prediction + flags, counts and the plan (offsets, split, queue size).
+cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kernels);
+// Ordered compaction of the active rows (as j-set slots through inv, or rows
+// when inv is null) and the work queue.
+cudaError_t launch_block_queue(const BlockLaunch &b, const int32_t *inv, cudaStream_t s, int *kernels);
+cudaError_t launch_inverse_perm(int64_t n_pad, const int32_t *perm, int32_t *inv, cudaStream_t s);
+int subset_occupancy(int block, int p, int tj, int minb, bool eps_zero);
+cudaError_t launch_subset_f32c(int block, int p, int tj, int minb, bool eps_zero, int grid,
+                               const F32CSubsetParams &prm, cudaStream_t s);
+cudaError_t launch_subset_f64(int max_items, const double *xp, const double *vp, const double *mass,
+                              const ClusterDev *cl, const SubItem *items, const int *n_items,
+                              const int32_t *act, int64_t n, double G, double *acc, double *jerk,
+                              double *pot, cudaStream_t s);
+cudaError_t launch_block_correct(int64_t n, const uint8_t *flag, const BlockScalars *sc, double *t,
+                                 double *dt, double *pos, double *vel, double *acc, double *jerk,
+                                 double *pot, const double *a1, const double *j1, const double *p1,
+                                 double dt_max, double dt_min, double eta, cudaStream_t s);
+
+
 // ---- kernel launchers (all enqueue on `s`, return cudaGetLastError()) ----
 
 // The F32C force kernel for tile shape (block, p, tj) compiled for minb resident

@@ -1,0 +1,165 @@
+"""Individual (block) time steps on the GPU against the oracle's block scheme (GPU).
+
+The schedule is integer-like (power-of-two steps, an active set), decided from
+FP64 quantities on both sides.  With NBODY_F64 forces the GPU takes the same
+decisions as the oracle, so the steps, the number of block steps and of
+evaluations match exactly and the trajectories to rounding.  With NBODY_F32C
+forces a step decision can flip where the criterion sits on a power-of-two
+boundary, so those runs are compared statistically and within the accuracy of
+the integration.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2509_19294_gb300 as nb
+from paper_2509_19294_gb300 import ic
+from tests import metrics
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+DT_MAX, DT_MIN = 2.0 ** -6, 2.0 ** -20
+T_END = 2.0 ** -4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_19294_gb300 import build
+    build.build()
+    nb.load()
+    torch.cuda.init()
+
+
+def block_run(pos, vel, mass, eps, mode, eta=0.02, eta_s=0.01, t_end=T_END, offsets=None, flags=0,
+              **kw):
+    n = mass.shape[0]
+    with nb.nbody_init(n, eps, mode=mode, cluster_offsets=offsets, flags=flags, **kw) as ctx:
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        a = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        j = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        ph = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_block_start(ctx, p, v, m, a, j, ph, DT_MAX, DT_MIN, eta, eta_s)
+        blocks, evals = nb.nbody_block_advance(ctx, p, v, m, a, j, ph, t_end)
+        t, dt = nb.nbody_block_state(ctx)
+        return host(p), host(v), host(a), host(j), dt, t, blocks, evals
+
+
+def cluster_system(n=600, seed=51):
+    pos, vel, mass = ic.plummer(n, seed=seed)
+    return pos, vel, mass
+
+
+def test_f64_block_steps_match_oracle_exactly(oracle):
+    pos, vel, mass = cluster_system()
+    gp, gv, ga, gj, gdt, gt, gb, ge = block_run(pos, vel, mass, 0.01, nb.NBODY_F64)
+    rp, rv, ra, rj, _, rdt, rb, re = oracle.block_hermite(pos, vel, mass, 0.01, T_END, DT_MAX, DT_MIN,
+                                                         0.02, 0.01)
+    assert len(np.unique(rdt)) > 1            # the particles really take different steps
+    assert np.array_equal(gdt, rdt) and gb == rb and ge == re
+    assert np.all(gt == T_END)
+    np.testing.assert_allclose(gp, rp, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(gv, rv, rtol=0, atol=1e-10)
+    assert metrics.rel_acc_errors(ga, ra).max() <= 1e-10
+
+
+@pytest.mark.parametrize("mode", [nb.NBODY_F64, nb.NBODY_F32C])
+def test_equal_steps_reduce_to_shared_hermite(mode):
+    pos, vel, mass = cluster_system(500, 52)
+    n = 500
+    gp, gv, ga, gj, gdt, _, gb, ge = block_run(pos, vel, mass, 0.01, mode, eta=1e30, eta_s=1e30)
+    assert np.all(gdt == DT_MAX) and gb == 4 and ge == 4 * n
+    with nb.nbody_init(n, 0.01, mode=mode) as ctx:
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        a = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        j = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        ph = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_forces_jerk(ctx, p, v, m, a, j, ph)
+        nb.nbody_step_hermite(ctx, p, v, m, a, j, ph, DT_MAX, 4)
+        sp, sv = host(p), host(v)
+    if mode == nb.NBODY_F64:
+        assert np.array_equal(gp, sp) and np.array_equal(gv, sv)
+    else:
+        # same scheme, FP32C forces on the subset path vs the full path
+        np.testing.assert_allclose(gp, sp, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(gv, sv, rtol=0, atol=1e-9)
+
+
+def test_f32c_block_steps_track_oracle(oracle):
+    pos, vel, mass = cluster_system(2000, 53)
+    gp, gv, ga, gj, gdt, gt, gb, ge = block_run(pos, vel, mass, 0.005, nb.NBODY_F32C)
+    rp, rv, ra, rj, _, rdt, rb, re = oracle.block_hermite(pos, vel, mass, 0.005, T_END, DT_MAX, DT_MIN,
+                                                         0.02, 0.01)
+    assert np.all(gt == T_END)
+    assert np.mean(gdt == rdt) >= 0.99
+    assert abs(ge - re) <= 0.01 * re
+    dx = np.abs(gp - rp).max(axis=0)
+    assert np.median(dx) <= 1e-10 and dx.max() <= 1e-7, (np.median(dx), dx.max())
+    s = metrics.summary(ga, ra)
+    assert s["median"] <= 1e-6, s
+
+
+@pytest.mark.parametrize("mode", [nb.NBODY_F64, nb.NBODY_F32C])
+def test_ensemble_block_steps_equal_independent_clusters(oracle, mode):
+    ens = ic.ensemble(5, seed=54, n_min=256, n_max=900)
+    gp, gv, ga, gj, gdt, gt, gb, ge = block_run(ens.pos, ens.vel, ens.mass, ens.eps, mode,
+                                                offsets=ens.offsets)
+    total = 0
+    for c in range(5):
+        b, e = ens.offsets[c], ens.offsets[c + 1]
+        rp, rv, ra, rj, _, rdt, rb, re = oracle.block_hermite(
+            ens.pos[:, b:e], ens.vel[:, b:e], ens.mass[b:e], ens.eps[c], T_END, DT_MAX, DT_MIN, 0.02,
+            0.01)
+        total += re
+        if mode == nb.NBODY_F64:
+            assert np.array_equal(gdt[b:e], rdt)
+            np.testing.assert_allclose(gp[:, b:e], rp, rtol=0, atol=1e-12)
+        else:
+            assert np.mean(gdt[b:e] == rdt) >= 0.98
+            assert np.abs(gp[:, b:e] - rp).max() <= 1e-7
+    if mode == nb.NBODY_F64:
+        assert ge == total
+
+
+@pytest.mark.parametrize("mode", [nb.NBODY_F64, nb.NBODY_F32C])
+def test_block_graph_equals_eager(mode):
+    pos, vel, mass = cluster_system(700, 55)
+    g = block_run(pos, vel, mass, 0.01, mode, reorder_every=5)
+    e = block_run(pos, vel, mass, 0.01, mode, reorder_every=5, flags=nb.NBODY_FLAG_NO_GRAPH)
+    for x, y in zip(g, e):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_block_steps_save_evaluations():
+    pos, vel, mass = cluster_system(3000, 56)
+    *_, gb, ge = block_run(pos, vel, mass, 0.002, nb.NBODY_F32C)
+    # a shared step at the smallest block step would cost n * blocks evaluations
+    assert ge < 0.5 * 3000 * gb
+
+
+def test_block_api_errors():
+    n = 64
+    pos, vel, mass = cluster_system(n, 57)
+    with nb.nbody_init(n, 0.01) as ctx:
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        a = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        j = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        with pytest.raises(nb.NBodyError):
+            nb.nbody_block_advance(ctx, p, v, m, a, j, None, T_END)
+    with nb.nbody_init(n, 0.01) as ctx:
+        with pytest.raises(nb.NBodyError):
+            nb.nbody_block_start(ctx, pos, vel, mass, np.empty((3, n)), np.empty((3, n)), None,
+                                 DT_MAX, DT_MIN, 0.02, 0.01)
+    with nb.nbody_init(n, 0.01) as ctx:
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        a = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        j = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        with pytest.raises(nb.NBodyError):
+            nb.nbody_block_start(ctx, p, v, m, a, j, None, 0.03, DT_MIN, 0.02, 0.01)
+    with nb.nbody_init(n, 0.01) as ctx:   # errors are sticky: a fresh context
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        a = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        j = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        nb.nbody_block_start(ctx, p, v, m, a, j, None, DT_MAX, DT_MIN, 0.02, 0.01)
+        with pytest.raises(nb.NBodyError):
+            nb.nbody_block_advance(ctx, p, v, m, a, j, None, DT_MAX * 1.5)
