@@ -383,6 +383,40 @@ def run_ours(args):
             "note": "context only: the paper's times are whole-application runs of its own code "
                     "and initial conditions on other hardware (Sec. 4)"}
 
+    # individual (block) time steps on the paper's particle count
+    block = None
+    if rank == 0 and not args.no_paper_scale:
+        from paper_2509_19294_gb300 import ic
+        bp_, bv_, bm_ = ic.plummer(PAPER_N, seed=7)
+        with nb.nbody_init(PAPER_N, 1e-3, mode=nb.NBODY_F32C, reorder_every=4,
+                           flags=nb.NBODY_FLAG_PROFILE) as cb:
+            p_, v_, m_ = (torch.from_numpy(x.copy()).cuda() for x in (bp_, bv_, bm_))
+            a_ = torch.empty((3, PAPER_N), dtype=torch.float64, device="cuda")
+            j_ = torch.empty((3, PAPER_N), dtype=torch.float64, device="cuda")
+            po_ = torch.empty(PAPER_N, dtype=torch.float64, device="cuda")
+            nb.nbody_block_start(cb, p_, v_, m_, a_, j_, po_, 2.0 ** -7, 2.0 ** -22, 0.02, 0.01)
+            nb.nbody_block_advance(cb, p_, v_, m_, a_, j_, po_, 2.0 ** -7)   # warm-up, graphs
+            torch.cuda.synchronize()
+            b0, e0_ = nb.nbody_block_advance(cb, p_, v_, m_, a_, j_, po_, 2.0 ** -7)
+            nb.nbody_profile_read(cb, reset=True)
+            t0 = time.perf_counter()
+            b1, e1_ = nb.nbody_block_advance(cb, p_, v_, m_, a_, j_, po_, 2.0 ** -4)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            kms, kn = nb.nbody_profile_read(cb, reset=True)
+            _, dts = nb.nbody_block_state(cb)
+        evals = e1_ - e0_
+        blocks = b1 - b0
+        block = {"workload": "Plummer sphere N=102400 (seed 7), eps=1e-3, Hermite with individual "
+                             "power-of-two steps (dt_max 2^-7, Aarseth eta 0.02) from t=2^-7 to 2^-4",
+                 "block_steps": int(blocks), "particle_evaluations": int(evals),
+                 "mean_active": evals / max(blocks, 1), "seconds": sec,
+                 "interactions_per_s": evals * float(PAPER_N) / sec,
+                 "subset_kernel_ms_total": kms,
+                 "steps_histogram": {f"2^{int(round(np.log2(v)))}": int(c)
+                                     for v, c in zip(*np.unique(dts, return_counts=True))},
+                 "shared_step_equivalent_evaluations": int(blocks) * PAPER_N}
+
     # end to end through the same C ABI call with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -464,6 +498,10 @@ def run_ours(args):
         paper_scale["jerk_roofline"] = {"achieved": jach, "peak": jpeak, "unit": "Ginteractions/s",
                                         "frac": jach / jpeak,
                                         "basis": f"{JERK_OPS_PER_PAIR} FP32 ops per pair"}
+    if block is not None:
+        jpeak = FP32_LANES_PER_SM * sms * sm_max * 1e6 / JERK_OPS_PER_PAIR / 1e9
+        bk = block["particle_evaluations"] * float(PAPER_N) / (block["subset_kernel_ms_total"] / 1e3) / 1e9
+        block["subset_kernel_roofline_frac"] = bk / jpeak
     if ensemble is not None:
         ek = ensemble["pairs_per_step"] / (ensemble["force_kernel_ms"] / 1e3) / 1e9
         ensemble["roofline_frac"] = ek / peak
@@ -487,6 +525,7 @@ def run_ours(args):
         "fp64_gpu": fp64,
         "ensemble": ensemble,
         "paper_scale": paper_scale,
+        "block_steps": block,
         "energy": energy,
         "accuracy": accuracy,
         "clocks": clocks,

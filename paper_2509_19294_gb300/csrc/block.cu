@@ -14,6 +14,7 @@
 // An active particle is evaluated with its own j-set offset and its own tile
 // centre: per j-tile each thread forms the exact centre difference for each of
 // its particles, so the self pair is exactly zero, as in the full kernels.
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -24,6 +25,21 @@
 namespace nbody {
 
 namespace {
+
+// FP64 epilogue of one active particle: scale by G, remove the self term of
+// phi (its own j-tile contributed m_i rsqrt(eps^2) exactly), scatter to its row.
+__device__ __forceinline__ void subset_finalize(const F32CJerkParams &p, const ClusterDev &cl,
+                                                int slot, const double (&r)[7]) {
+    const int64_t u = p.perm[slot];
+    double ph = r[6];
+    if (cl.eps2f > 0.0f) ph -= (double)__fmul_rn(p.pm[slot], rsqrt_mufu(cl.eps2f));
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        p.acc[d * p.n + u] = p.G * r[d];
+        p.jerk[d * p.n + u] = p.G * r[3 + d];
+    }
+    if (p.pot) p.pot[u] = -p.G * ph;
+}
 
 template <int BLOCK, int P, int TJ, bool EPS_ZERO>
 struct SubsetKernel {
@@ -37,7 +53,6 @@ struct SubsetKernel {
         float4 j[2][NA][TJ / 4];
         float4 jc[2][4];  // j-tile centre: position hi, lo, velocity hi, lo
         int item;
-        int last;
     };
 
     __device__ static __forceinline__ void store_tile(Smem &sm, int b, const float4 (&r)[NLD]) {
@@ -157,56 +172,74 @@ struct SubsetKernel {
                     if (valid[k]) finalize(p, cl, slot[k], res[k]);
                 continue;
             }
+            // split j-ranges: FP64 partials, summed in a fixed order by
+            // subset_reduce_kernel (in parallel over particles and components)
             const int tcs = BLOCK * P;
             double *mine = q.partial + (size_t)(it.pbase + it.split) * NC * tcs;
 #pragma unroll
             for (int k = 0; k < P; ++k) {
                 const int l = threadIdx.x + k * BLOCK;
 #pragma unroll
-                for (int c = 0; c < NC; ++c) __stcg(mine + c * tcs + l, res[k][c]);
-            }
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                const int prev = atomicAdd(p.counters + 1 + it.chunk, 1);
-                sm.last = (prev == it.nsplit - 1);
-            }
-            __syncthreads();
-            if (!sm.last) continue;
-            __threadfence();
-#pragma unroll
-            for (int k = 0; k < P; ++k) {
-                const int l = threadIdx.x + k * BLOCK;
-                double tot[NC];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) tot[c] = 0.0;
-                for (int s = 0; s < it.nsplit; ++s) {
-                    const double *ps = q.partial + (size_t)(it.pbase + s) * NC * tcs;
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) tot[c] += __ldcg(ps + c * tcs + l);
-                }
-                if (valid[k]) finalize(p, cl, slot[k], tot);
+                for (int c = 0; c < NC; ++c) mine[c * tcs + l] = res[k][c];
             }
         }
     }
 
     __device__ static __forceinline__ void finalize(const F32CJerkParams &p, const ClusterDev &cl,
                                                     int slot, const double (&r)[NC]) {
-        const int64_t u = p.perm[slot];
-        double ph = r[6];
-        if (cl.eps2f > 0.0f) ph -= (double)__fmul_rn(p.pm[slot], rsqrt_mufu(cl.eps2f));
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            p.acc[d * p.n + u] = p.G * r[d];
-            p.jerk[d * p.n + u] = p.G * r[3 + d];
-        }
-        if (p.pot) p.pot[u] = -p.G * ph;
+        subset_finalize(p, cl, slot, r);
     }
 };
 
 template <int BLOCK, int P, int TJ, int MINB, bool EPS_ZERO>
 __global__ void __launch_bounds__(BLOCK, MINB) subset_jerk_kernel(const F32CSubsetParams q) {
     SubsetKernel<BLOCK, P, TJ, EPS_ZERO>::run(q);
+}
+
+// Sum the split partials of every chunk and finalise.  Work unit = 32
+// particles of one chunk; its 8 warps each sum one contiguous eighth of the
+// splits (loads unrolled, so their latencies overlap), then warp 0 adds the
+// eight group sums in group order.  The order of every addition is fixed by
+// (nsplit, particle), so the result does not depend on scheduling.
+constexpr int kReduceWarps = 8;
+
+__global__ void __launch_bounds__(32 * kReduceWarps)
+subset_reduce_kernel(const F32CSubsetParams q, const SubItem *__restrict__ info,
+                     const BlockScalars *__restrict__ sc, int cs) {
+    __shared__ double part[kReduceWarps][7][32];
+    const int subs = (cs + 31) / 32;
+    const int units = sc->n_chunks * subs;
+    const int lane = threadIdx.x % 32, g = threadIdx.x / 32;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const SubItem it = info[u / subs];
+        const int l = (u % subs) * 32 + lane;
+        if (it.nsplit <= 1 || (u % subs) * 32 >= it.na) continue;  // uniform over the CTA
+        const int s0 = (int)((int64_t)g * it.nsplit / kReduceWarps);
+        const int s1 = (int)((int64_t)(g + 1) * it.nsplit / kReduceWarps);
+        double tot[7] = {0, 0, 0, 0, 0, 0, 0};
+        if (l < it.na) {
+#pragma unroll 4
+            for (int s = s0; s < s1; ++s) {
+                const double *ps = q.partial + (size_t)(it.pbase + s) * 7 * cs + l;
+#pragma unroll
+                for (int c = 0; c < 7; ++c) tot[c] += ps[c * cs];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 7; ++c) part[g][c][lane] = tot[c];
+        __syncthreads();
+        if (g == 0 && l < it.na) {
+            double r[7];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                r[c] = part[0][c][lane];
+#pragma unroll
+                for (int h = 1; h < kReduceWarps; ++h) r[c] += part[h][c][lane];
+            }
+            subset_finalize(q.base, q.base.cl[it.cluster], q.act_slot[it.a0 + l], r);
+        }
+        __syncthreads();
+    }
 }
 
 struct SubsetShape {
@@ -219,9 +252,8 @@ struct SubsetShape {
     SubsetShape{B, P, T, M, false, (const void *)subset_jerk_kernel<B, P, T, M, false>},    \
         SubsetShape{B, P, T, M, true, (const void *)subset_jerk_kernel<B, P, T, M, true>}
 
-const SubsetShape kSubsetShapes[] = {SUBSET(128, 2, 256, 2), SUBSET(256, 2, 256, 1),
-                                     SUBSET(128, 1, 128, 4), SUBSET(64, 2, 128, 4),
-                                     SUBSET(128, 2, 128, 3)};
+const SubsetShape kSubsetShapes[] = {SUBSET(64, 2, 256, 4), SUBSET(128, 2, 256, 2),
+                                     SUBSET(64, 2, 128, 4), SUBSET(128, 1, 128, 4)};
 
 const SubsetShape *find_subset(int block, int p, int tj, int minb, bool eps_zero) {
     for (const SubsetShape &s : kSubsetShapes)
@@ -482,7 +514,7 @@ __global__ void block_items_kernel(int ncl, const ClusterDev *__restrict__ cl, i
                                    const int *__restrict__ act_begin, const int *__restrict__ act_n,
                                    const int *__restrict__ ich_off, const int *__restrict__ item_off,
                                    const BlockScalars *__restrict__ sc, int max_items,
-                                   SubItem *__restrict__ items) {
+                                   SubItem *__restrict__ items, SubItem *__restrict__ info) {
     const int n_items = sc->n_items;
     const int split = sc->split;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_items && k < max_items;
@@ -510,6 +542,7 @@ __global__ void block_items_kernel(int ncl, const ClusterDev *__restrict__ cl, i
         it.pbase = sc_c > 1 ? it.chunk * split : 0;
         it.pad = 0;
         items[k] = it;
+        if (s == 0) info[it.chunk] = it;
     }
 }
 
@@ -572,6 +605,30 @@ int grid_of(int64_t work, int threads) {
 
 }  // namespace
 
+int subset_shapes(int *block, int *p, int *tj, int *minb, int cap) {
+    int n = 0;
+    for (const SubsetShape &s : kSubsetShapes) {
+        if (s.eps_zero) continue;
+        if (n < cap) {
+            block[n] = s.block;
+            p[n] = s.p;
+            tj[n] = s.tj;
+            minb[n] = s.minb;
+        }
+        ++n;
+    }
+    return n;
+}
+
+cudaError_t launch_subset_reduce(int max_chunks, int max_ctas, const F32CSubsetParams &prm,
+                                 const SubItem *info, const BlockScalars *sc, int cs, cudaStream_t s) {
+    const int64_t units = (int64_t)max_chunks * ((cs + 31) / 32);
+    if (units <= 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>(units, max_ctas);
+    subset_reduce_kernel<<<grid, 32 * kReduceWarps, 0, s>>>(prm, info, sc, cs);
+    return cudaGetLastError();
+}
+
 int subset_occupancy(int block, int p, int tj, int minb, bool eps_zero) {
     const SubsetShape *s = find_subset(block, p, tj, minb, eps_zero);
     if (!s) return 0;
@@ -613,7 +670,8 @@ cudaError_t launch_block_queue(const BlockLaunch &b, const int32_t *inv, cudaStr
     block_scatter_kernel<<<b.n_chunks, 256, 0, s>>>(b.flag, b.chunks, b.chunk_off, inv, b.act);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     block_items_kernel<<<grid_of(b.max_items, 256), 256, 0, s>>>(
-        b.ncl, b.cl, b.cs, b.act_begin, b.act_n, b.ich_off, b.item_off, b.sc, b.max_items, b.items);
+        b.ncl, b.cl, b.cs, b.act_begin, b.act_n, b.ich_off, b.item_off, b.sc, b.max_items, b.items,
+        b.info);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *kernels += 2;
     return cudaSuccess;

@@ -35,7 +35,6 @@ struct F32CJerkKernel {
     static constexpr int NLD = (NV + BLOCK - 1) / BLOCK;
     static constexpr int NC = 7;                 // ax, ay, az, jx, jy, jz, phi
     static_assert(TJ % 8 == 0, "tj must be a multiple of 8");
-    static_assert(TC % TJ == 0, "a j-tile must not straddle two centre tiles");
 
     struct Smem {
         float4 j[2][NA][TJ / 4];
@@ -145,6 +144,7 @@ struct F32CJerkKernel {
     }
 
     __device__ static void run(const F32CJerkParams p) {
+        static_assert(TC % TJ == 0, "a j-tile must not straddle two centre tiles");
         __shared__ Smem sm;
         for (;;) {
             if (threadIdx.x == 0) sm.item = atomicAdd(p.counters, 1);

@@ -62,13 +62,14 @@ struct JerkPath {
 struct BlockState {
     bool started = false;
     double dt_max = 0.0, dt_min = 0.0, eta = 0.0;
-    int cs = 0, workers = 1, max_split = 1, max_items = 0;
+    int cs = 0, workers = 1, max_split = 1, max_items = 0, max_chunks = 0;
+    nbody_tiles sub{0, 0, 0, 0, 0};  // subset kernel shape (F32C)
     double *t = nullptr, *dt = nullptr, *part = nullptr, *partial = nullptr, *p1 = nullptr;
     uint8_t *flag = nullptr;
     int *cnt = nullptr, *chunk_off = nullptr, *act_begin = nullptr, *act_n = nullptr;
     int *ich_off = nullptr, *item_off = nullptr;
     int32_t *act = nullptr, *inv = nullptr;
-    SubItem *items = nullptr;
+    SubItem *items = nullptr, *info = nullptr;
     BlockScalars *sc = nullptr;
 };
 
@@ -759,6 +760,7 @@ void free_block(nbody_ctx *ctx) {
     dev_free(&b.act);
     dev_free(&b.inv);
     dev_free(&b.items);
+    dev_free(&b.info);
     dev_free(&b.sc);
     b.started = false;
 }
@@ -769,20 +771,31 @@ int alloc_block(nbody_ctx *ctx) {
     int rc;
     const size_t n = (size_t)ctx->n, nc = (size_t)std::max(ctx->n_chunks, 1), ncl = (size_t)ctx->ncl;
     if (ctx->mode == NBODY_F32C) {
-        const nbody_tiles &t = ctx->jp.tiles;
-        b.cs = t.block * t.p;
-        const int occ = subset_occupancy(t.block, t.p, t.tj, t.ctas_per_sm, ctx->eps_zero);
-        if (occ <= 0) return fail(ctx, NBODY_EUNSUPPORTED, "no subset kernel for the jerk tile shape");
+        // the subset kernel must stream the jerk geometry's j-tiles (same tj);
+        // among those shapes take the smallest i-chunk (less idle lanes when few
+        // particles are active)
+        int bl[16], pp[16], tj[16], mb[16];
+        const int ns = std::min(16, subset_shapes(bl, pp, tj, mb, 16));
+        b.sub = nbody_tiles{0, 0, 0, 0, 0};
+        for (int k = 0; k < ns; ++k)
+            if (tj[k] == ctx->jp.tiles.tj && (b.sub.block == 0 || bl[k] * pp[k] < b.sub.block * b.sub.p))
+                b.sub = nbody_tiles{bl[k], pp[k], tj[k], 0, mb[k]};
+        if (b.sub.block == 0) return fail(ctx, NBODY_EUNSUPPORTED, "no subset kernel for the jerk tiles");
+        b.cs = b.sub.block * b.sub.p;
+        const int occ = subset_occupancy(b.sub.block, b.sub.p, b.sub.tj, b.sub.ctas_per_sm, ctx->eps_zero);
+        if (occ <= 0) return fail(ctx, NBODY_EUNSUPPORTED, "subset kernel not loadable");
         b.workers = occ * ctx->sms;
-        b.max_split = 64;
-        b.max_items = std::max(2 * b.workers, ctx->jp.n_tiles);
+        b.max_split = 128;
+        b.max_chunks = (int)(ctx->n / b.cs) + ctx->ncl + 1;
+        b.max_items = std::max(2 * b.workers, b.max_chunks);
         if ((rc = dev_alloc(ctx, &b.partial, (size_t)2 * b.workers * 7 * b.cs))) return rc;
         if ((rc = dev_alloc(ctx, &b.inv, n))) return rc;
     } else {
         b.cs = kF64Block;
         b.workers = 1;
         b.max_split = 1;
-        b.max_items = std::max(ctx->n_blocks64, 1);
+        b.max_chunks = std::max(ctx->n_blocks64, 1);
+        b.max_items = b.max_chunks;
     }
     for (double **q : {&b.t, &b.dt, &b.p1})
         if ((rc = dev_alloc(ctx, q, n))) return rc;
@@ -794,6 +807,7 @@ int alloc_block(nbody_ctx *ctx) {
         if ((rc = dev_alloc(ctx, q, ncl + 1))) return rc;
     if ((rc = dev_alloc(ctx, &b.act, n))) return rc;
     if ((rc = dev_alloc(ctx, &b.items, (size_t)b.max_items))) return rc;
+    if ((rc = dev_alloc(ctx, &b.info, (size_t)b.max_chunks))) return rc;
     if ((rc = dev_alloc(ctx, &b.sc, 1))) return rc;
     NB_CUDA(cudaMemset(b.sc, 0, sizeof(BlockScalars)));
     return NBODY_OK;
@@ -831,6 +845,7 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
     b.item_off = bs.item_off;
     b.act = bs.act;
     b.items = bs.items;
+    b.info = bs.info;
     b.sc = bs.sc;
     return b;
 }
@@ -859,7 +874,7 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
         NB_CUDA(launch_inverse_perm(j.n_pad, j.perm, bs.inv, s));
         *kernels += 3;
         NB_CUDA(launch_block_queue(b, bs.inv, s, kernels));
-        NB_CUDA(cudaMemsetAsync(j.counters, 0, ((size_t)j.n_tiles + 1) * sizeof(int), s));
+        NB_CUDA(cudaMemsetAsync(j.counters, 0, sizeof(int), s));  // queue head
         F32CSubsetParams q{};
         q.base = jerk_params(ctx, j.a1, j.j1, bs.p1);
         q.act_slot = bs.act;
@@ -868,9 +883,10 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
         q.partial = bs.partial;
         q.tcj = j.tc;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
-        NB_CUDA(launch_subset_f32c(j.tiles.block, j.tiles.p, j.tiles.tj, j.tiles.ctas_per_sm,
+        NB_CUDA(launch_subset_f32c(bs.sub.block, bs.sub.p, bs.sub.tj, bs.sub.ctas_per_sm,
                                    ctx->eps_zero, bs.workers, q, s));
-        ++*kernels;
+        NB_CUDA(launch_subset_reduce(bs.max_chunks, 4 * ctx->sms, q, bs.info, bs.sc, bs.cs, s));
+        *kernels += 2;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
     } else {
         NB_CUDA(launch_block_queue(b, nullptr, s, kernels));

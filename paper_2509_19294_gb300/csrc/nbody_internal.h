@@ -153,6 +153,7 @@ struct BlockLaunch {
     int *cnt, *chunk_off, *act_begin, *act_n, *ich_off, *item_off;
     int32_t *act;
     SubItem *items;
+    SubItem *info;  // per i-chunk: range, cluster, split count, partial base
     BlockScalars *sc;
 };
 
@@ -165,6 +166,10 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
 cudaError_t launch_block_queue(const BlockLaunch &b, const int32_t *inv, cudaStream_t s, int *kernels);
 cudaError_t launch_inverse_perm(int64_t n_pad, const int32_t *perm, int32_t *inv, cudaStream_t s);
 int subset_occupancy(int block, int p, int tj, int minb, bool eps_zero);
+int subset_shapes(int *block, int *p, int *tj, int *minb, int cap);
+// Deterministic parallel sum of the subset kernel's split partials + epilogue.
+cudaError_t launch_subset_reduce(int max_chunks, int max_ctas, const F32CSubsetParams &prm,
+                                 const SubItem *info, const BlockScalars *sc, int cs, cudaStream_t s);
 cudaError_t launch_subset_f32c(int block, int p, int tj, int minb, bool eps_zero, int grid,
                                const F32CSubsetParams &prm, cudaStream_t s);
 cudaError_t launch_subset_f64(int max_items, const double *xp, const double *vp, const double *mass,
