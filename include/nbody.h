@@ -109,7 +109,8 @@ typedef struct nbody_config {
     const double *eps;               /* host, n_clusters softening lengths, each finite, >= 0 */
     double G;                        /* gravitational constant, finite */
     int32_t reorder_every;           /* F32C: re-sort particles along a Morton curve every k
-                                        force evaluations (0 = keep the caller's order) */
+                                        force evaluations (0 = keep the caller's order); in
+                                        block steps every k * dt_max of simulated time */
     int32_t flags;                   /* NBODY_FLAG_* */
     nbody_tiles tiles;               /* F32C tile shape; zeros = default or autotuned */
 } nbody_config;

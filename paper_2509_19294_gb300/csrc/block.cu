@@ -19,6 +19,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "block_reduce.cuh"
 #include "forces_f32c_jerk.cuh"
 #include "nbody_internal.h"
 
@@ -41,25 +42,49 @@ __device__ __forceinline__ void subset_finalize(const F32CJerkParams &p, const C
     if (p.pot) p.pot[u] = -p.G * ph;
 }
 
-template <int BLOCK, int P, int TJ, bool EPS_ZERO>
+// Subset kernel: persistent CTAs over the device-built queue of (i-chunk of the
+// active list, j-range) items.  A CTA holds BLOCK * P active particles (P per
+// thread) in G thread groups of BLOCK; all groups hold the same particles and
+// each takes one G-th of every shared-memory j-tile, so a small active set
+// still keeps G times more warps busy.  The groups' Kahan sums are added in
+// group order (FP64, shared memory); a j-range split is written as an FP64
+// partial that subset_reduce_kernel sums in split order.
+template <int BLOCK, int P, int TJ, int G, bool EPS_ZERO>
 struct SubsetKernel {
     using JK = F32CJerkKernel<BLOCK, P, TJ, EPS_ZERO>;
+    static constexpr int NT = BLOCK * G;       // threads per CTA
+    static constexpr int CS = BLOCK * P;       // active particles per chunk
     static constexpr int NA = JK::NA;
     static constexpr int NC = JK::NC;
     static constexpr int NV = JK::NV;
-    static constexpr int NLD = JK::NLD;
+    static constexpr int NLD = (NV + NT - 1) / NT;
+    static constexpr int COLS = TJ / 4 / G;    // float4 columns of a j-tile per group
+    static_assert((TJ / 4) % G == 0, "a group takes whole float4 columns");
 
     struct Smem {
         float4 j[2][NA][TJ / 4];
         float4 jc[2][4];  // j-tile centre: position hi, lo, velocity hi, lo
+        double red[G > 1 ? G : 1][NC][CS];
         int item;
     };
+
+    __device__ static __forceinline__ void load_tile(const F32CJerkParams &p, int gs, float4 (&r)[NLD]) {
+#pragma unroll
+        for (int q = 0; q < NLD; ++q) {
+            const int v = threadIdx.x + q * NT;
+            if (NV % NT == 0 || v < NV) {
+                const int a = v / (TJ / 4);
+                const int off = (v % (TJ / 4)) * 4;
+                r[q] = __ldg(reinterpret_cast<const float4 *>(JK::array(p, a) + gs + off));
+            }
+        }
+    }
 
     __device__ static __forceinline__ void store_tile(Smem &sm, int b, const float4 (&r)[NLD]) {
 #pragma unroll
         for (int q = 0; q < NLD; ++q) {
-            const int v = threadIdx.x + q * BLOCK;
-            if (NV % BLOCK == 0 || v < NV) sm.j[b][v / (TJ / 4)][v % (TJ / 4)] = r[q];
+            const int v = threadIdx.x + q * NT;
+            if (NV % NT == 0 || v < NV) sm.j[b][v / (TJ / 4)][v % (TJ / 4)] = r[q];
         }
     }
 
@@ -67,6 +92,7 @@ struct SubsetKernel {
         __shared__ Smem sm;
         const F32CJerkParams &p = q.base;
         const int n_items = *q.n_items;
+        const int li = threadIdx.x % BLOCK, g = threadIdx.x / BLOCK;
         for (;;) {
             if (threadIdx.x == 0) sm.item = atomicAdd(p.counters, 1);
             __syncthreads();
@@ -79,7 +105,7 @@ struct SubsetKernel {
             bool valid[P];
 #pragma unroll
             for (int k = 0; k < P; ++k) {
-                const int pos = threadIdx.x + k * BLOCK;
+                const int pos = li + k * BLOCK;
                 valid[k] = pos < it.na;
                 slot[k] = q.act_slot[it.a0 + (valid[k] ? pos : 0)];
             }
@@ -94,7 +120,7 @@ struct SubsetKernel {
             float4 jc[4];
             {
                 const int gs = cl.slot_begin + it.jt0 * TJ;
-                JK::load_tile(p, gs, reg);
+                load_tile(p, gs, reg);
                 store_tile(sm, 0, reg);
                 if (threadIdx.x == 0) {
                     JK::load_centres(p, gs / q.tcj, jc);
@@ -107,7 +133,7 @@ struct SubsetKernel {
                 const int b = t & 1;
                 const bool more = t + 1 < ntj;
                 const int gsn = cl.slot_begin + (it.jt0 + t + 1) * TJ;
-                if (more) JK::load_tile(p, gsn, reg);
+                if (more) load_tile(p, gsn, reg);
                 if (more && threadIdx.x == 0) JK::load_centres(p, gsn / q.tcj, jc);
                 float2 ni[P][6];
 #pragma unroll
@@ -136,7 +162,7 @@ struct SubsetKernel {
 #pragma unroll
                     for (int c = 0; c < NC; ++c) acc[k][c] = make_float2(0.0f, 0.0f);
 #pragma unroll 1
-                for (int v = 0; v < TJ / 4; ++v) {
+                for (int v = g * COLS; v < (g + 1) * COLS; ++v) {
                     float4 Q[NA];
 #pragma unroll
                     for (int a = 0; a < NA; ++a) Q[a] = sm.j[b][a][v];
@@ -166,34 +192,195 @@ struct SubsetKernel {
             for (int k = 0; k < P; ++k)
 #pragma unroll
                 for (int c = 0; c < NC; ++c) res[k][c] = (double)ksum[k][c] - (double)kcmp[k][c];
+            if (G > 1) {
+#pragma unroll
+                for (int k = 0; k < P; ++k)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) sm.red[g][c][li + k * BLOCK] = res[k][c];
+                __syncthreads();
+                if (g != 0) continue;  // group 0 adds the groups in order and stores
+#pragma unroll
+                for (int k = 0; k < P; ++k)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        double r = sm.red[0][c][li + k * BLOCK];
+#pragma unroll
+                        for (int h = 1; h < G; ++h) r += sm.red[h][c][li + k * BLOCK];
+                        res[k][c] = r;
+                    }
+            }
             if (it.nsplit <= 1) {
 #pragma unroll
                 for (int k = 0; k < P; ++k)
-                    if (valid[k]) finalize(p, cl, slot[k], res[k]);
+                    if (valid[k]) subset_finalize(p, cl, slot[k], res[k]);
                 continue;
             }
-            // split j-ranges: FP64 partials, summed in a fixed order by
-            // subset_reduce_kernel (in parallel over particles and components)
-            const int tcs = BLOCK * P;
-            double *mine = q.partial + (size_t)(it.pbase + it.split) * NC * tcs;
+            double *mine = q.partial + (size_t)(it.pbase + it.split) * NC * CS;
 #pragma unroll
             for (int k = 0; k < P; ++k) {
-                const int l = threadIdx.x + k * BLOCK;
+                const int l = li + k * BLOCK;
 #pragma unroll
-                for (int c = 0; c < NC; ++c) mine[c * tcs + l] = res[k][c];
+                for (int c = 0; c < NC; ++c) mine[c * CS + l] = res[k][c];
             }
         }
     }
-
-    __device__ static __forceinline__ void finalize(const F32CJerkParams &p, const ClusterDev &cl,
-                                                    int slot, const double (&r)[NC]) {
-        subset_finalize(p, cl, slot, r);
-    }
 };
 
-template <int BLOCK, int P, int TJ, int MINB, bool EPS_ZERO>
-__global__ void __launch_bounds__(BLOCK, MINB) subset_jerk_kernel(const F32CSubsetParams q) {
-    SubsetKernel<BLOCK, P, TJ, EPS_ZERO>::run(q);
+template <int BLOCK, int P, int TJ, int G, int MINB, bool EPS_ZERO>
+__global__ void __launch_bounds__(BLOCK * G, MINB) subset_jerk_kernel(const F32CSubsetParams q) {
+    SubsetKernel<BLOCK, P, TJ, G, EPS_ZERO>::run(q);
+}
+
+// Few-particle path (at most kFewMax active particles, F32C): every thread
+// takes j-particles of the active clusters (grid-stride over their real
+// particles) and evaluates them against the active particles of the same
+// cluster, kFewBatch at a time; pair terms as in the subset kernel (FP32
+// offsets from float-pair centres, exact centre differences, MUFU rsqrt).
+// Per thread and per warp FP32 sums, then FP64: the warps in order, the CTAs in
+// a fixed order by the last CTA (ticket), which also applies the epilogue.
+constexpr int kFewThreads = 256;
+constexpr int kFewBatch = 8;
+
+__global__ void __launch_bounds__(kFewThreads)
+    subset_few_kernel(const F32CJerkParams p, const int32_t *__restrict__ act, BlockScalars *sc,
+                      double *__restrict__ part) {
+    __shared__ float own[kFewMax][6];
+    __shared__ float4 oc[kFewMax][4];
+    __shared__ int ocl[kFewMax];
+    __shared__ float wsum[kFewThreads / 32][kFewBatch][7];
+    __shared__ double csum[kFewMax][7];
+    __shared__ double fsum[kFewThreads / 32][kFewMax * 7];
+    __shared__ int fjb[kFewMax + 1], fcl[kFewMax];
+    __shared__ bool last;
+    if (!sc->few) return;  // uniform: the plan chose the subset kernel
+    const int na = sc->n_active;
+    const int nf = sc->few_ncl;
+    for (int e = threadIdx.x; e <= nf; e += blockDim.x) {
+        fjb[e] = sc->few_jbase[e];
+        if (e < nf) fcl[e] = sc->few_cl[e];
+    }
+    for (int a = threadIdx.x; a < na; a += blockDim.x) {
+        const int slot = act[a];
+        own[a][0] = p.px[slot];
+        own[a][1] = p.py[slot];
+        own[a][2] = p.pz[slot];
+        own[a][3] = p.pvx[slot];
+        own[a][4] = p.pvy[slot];
+        own[a][5] = p.pvz[slot];
+        const int tile = slot / p.tc;
+        oc[a][0] = p.chl[2 * tile];
+        oc[a][1] = p.chl[2 * tile + 1];
+        oc[a][2] = p.vchl[2 * tile];
+        oc[a][3] = p.vchl[2 * tile + 1];
+        int e = 0;
+        while (e + 1 < nf && sc->few_abeg[e + 1] <= a) ++e;
+        ocl[a] = sc->few_cl[e];
+    }
+    __syncthreads();
+    const int jtot = fjb[nf];
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    for (int b0 = 0; b0 < na; b0 += kFewBatch) {
+        float acc[kFewBatch][7];
+#pragma unroll
+        for (int k = 0; k < kFewBatch; ++k)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) acc[k][c] = 0.0f;
+        for (int g = blockIdx.x * kFewThreads + threadIdx.x; g < jtot; g += gridDim.x * kFewThreads) {
+            int e = 0;
+            while (e + 1 < nf && fjb[e + 1] <= g) ++e;
+            const int c = fcl[e];
+            const ClusterDev d = p.cl[c];
+            const int js = d.slot_begin + (g - fjb[e]);
+            const float J[7] = {p.px[js], p.py[js], p.pz[js], p.pm[js], p.pvx[js], p.pvy[js], p.pvz[js]};
+            const int jt = js / p.tc;
+            const float4 jc0 = p.chl[2 * jt], jc1 = p.chl[2 * jt + 1];
+            const float4 jv0 = p.vchl[2 * jt], jv1 = p.vchl[2 * jt + 1];
+            const float jh[6] = {jc0.x, jc0.y, jc0.z, jv0.x, jv0.y, jv0.z};
+            const float jl[6] = {jc1.x, jc1.y, jc1.z, jv1.x, jv1.y, jv1.z};
+#pragma unroll
+            for (int k = 0; k < kFewBatch; ++k) {
+                const int a = b0 + k;
+                if (a >= na || ocl[a] != c) continue;
+                const float ih[6] = {oc[a][0].x, oc[a][0].y, oc[a][0].z, oc[a][2].x, oc[a][2].y, oc[a][2].z};
+                const float il[6] = {oc[a][1].x, oc[a][1].y, oc[a][1].z, oc[a][3].x, oc[a][3].y, oc[a][3].z};
+                float r[6];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    float hi, lo;
+                    centre_diff(ih[q], il[q], jh[q], jl[q], hi, lo);
+                    r[q] = __fsub_rn(J[q < 3 ? q : q + 1], __fadd_rn(__fadd_rn(own[a][q], hi), lo));
+                }
+                float r2 = __fmaf_rn(r[0], r[0], d.eps2f);
+                r2 = __fmaf_rn(r[1], r[1], r2);
+                r2 = __fmaf_rn(r[2], r[2], r2);
+                float rv = __fmul_rn(r[0], r[3]);
+                rv = __fmaf_rn(r[1], r[4], rv);
+                rv = __fmaf_rn(r[2], r[5], rv);
+                const float s = r2 > 0.0f ? rsqrt_mufu(r2) : 0.0f;
+                const float ms = __fmul_rn(J[3], s), s2 = __fmul_rn(s, s);
+                const float w3 = __fmul_rn(ms, s2);
+                const float beta = __fmul_rn(rv, __fmul_rn(s2, -3.0f));
+                acc[k][6] = __fadd_rn(acc[k][6], ms);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    acc[k][q] = __fmaf_rn(w3, r[q], acc[k][q]);
+                    acc[k][3 + q] = __fmaf_rn(w3, __fmaf_rn(beta, r[q], r[3 + q]), acc[k][3 + q]);
+                }
+            }
+        }
+        // warp trees in FP32 (no less accurate than the subset kernel's FP32
+        // tile sums), then FP64: the warps in order
+#pragma unroll
+        for (int k = 0; k < kFewBatch; ++k)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                float v = acc[k][c];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+                if (lane == 0) wsum[warp][k][c] = v;
+            }
+        __syncthreads();
+        if (threadIdx.x < kFewBatch * 7) {
+            const int k = threadIdx.x / 7, c = threadIdx.x % 7;
+            double v = wsum[0][k][c];
+            for (int w = 1; w < kFewThreads / 32; ++w) v += wsum[w][k][c];
+            if (b0 + k < na) csum[b0 + k][c] = v;
+        }
+        __syncthreads();
+    }
+    double *mine = part + (size_t)blockIdx.x * kFewMax * 7;
+    for (int t = threadIdx.x; t < na * 7; t += blockDim.x) mine[t] = csum[t / 7][t % 7];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&sc->ticket_few, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // CTA partials in order: warp w adds CTAs [w G/8, (w+1) G/8), then the
+    // warps' sums in warp order
+    {
+        const int nw = kFewThreads / 32;
+        const int b0 = (int)(warp * gridDim.x / nw), b1 = (int)((warp + 1) * gridDim.x / nw);
+        for (int t = lane; t < na * 7; t += 32) {
+            double v = 0.0;
+            for (int b = b0; b < b1; ++b) v += __ldcg(part + (size_t)b * kFewMax * 7 + t);
+            fsum[warp][t] = v;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < na * 7; t += blockDim.x) {
+        double v = fsum[0][t];
+        for (int w = 1; w < kFewThreads / 32; ++w) v += fsum[w][t];
+        csum[t / 7][t % 7] = v;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < na; a += blockDim.x) {
+        double r[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) r[c] = csum[a][c];
+        subset_finalize(p, p.cl[ocl[a]], act[a], r);
+    }
+    if (threadIdx.x == 0) sc->ticket_few = 0;
 }
 
 // Sum the split partials of every chunk and finalise.  Work unit = 32
@@ -243,21 +430,26 @@ subset_reduce_kernel(const F32CSubsetParams q, const SubItem *__restrict__ info,
 }
 
 struct SubsetShape {
-    int block, p, tj, minb;
+    int block, p, tj, groups, minb;
     bool eps_zero;
     const void *kernel;
 };
 
-#define SUBSET(B, P, T, M)                                                                  \
-    SubsetShape{B, P, T, M, false, (const void *)subset_jerk_kernel<B, P, T, M, false>},    \
-        SubsetShape{B, P, T, M, true, (const void *)subset_jerk_kernel<B, P, T, M, true>}
+#define SUBSET(B, P, T, G, M)                                                                    \
+    SubsetShape{B, P, T, G, M, false, (const void *)subset_jerk_kernel<B, P, T, G, M, false>},   \
+        SubsetShape{B, P, T, G, M, true, (const void *)subset_jerk_kernel<B, P, T, G, M, true>}
 
-const SubsetShape kSubsetShapes[] = {SUBSET(64, 2, 256, 4), SUBSET(128, 2, 256, 2),
-                                     SUBSET(64, 2, 128, 4), SUBSET(128, 1, 128, 4)};
+// In order of preference for each tj (the first one matching the jerk tiles is
+// the default; measured at N = 102400 with individual steps).
+const SubsetShape kSubsetShapes[] = {SUBSET(64, 1, 256, 4, 2),  SUBSET(64, 1, 128, 4, 2),
+                                     SUBSET(64, 2, 256, 4, 1),  SUBSET(128, 2, 256, 2, 1),
+                                     SUBSET(128, 1, 256, 2, 2), SUBSET(32, 2, 256, 8, 1),
+                                     SUBSET(64, 2, 256, 1, 4),  SUBSET(64, 2, 128, 4, 1)};
 
-const SubsetShape *find_subset(int block, int p, int tj, int minb, bool eps_zero) {
+const SubsetShape *find_subset(int block, int p, int tj, int groups, int minb, bool eps_zero) {
     for (const SubsetShape &s : kSubsetShapes)
-        if (s.block == block && s.p == p && s.tj == tj && s.minb == minb && s.eps_zero == eps_zero)
+        if (s.block == block && s.p == p && s.tj == tj && s.groups == groups && s.minb == minb &&
+            s.eps_zero == eps_zero)
             return &s;
     return nullptr;
 }
@@ -338,10 +530,13 @@ __global__ void block_init_kernel(int64_t n, const double *acc, const double *je
     }
 }
 
-// Stage 1 of t_next: per chunk, min of t_i + dt_i (exact).
+// t_next = min_i (t_i + dt_i) (exact): per chunk minima, then the last CTA to
+// finish (ticket) takes the min over them.  No CTA waits for another.
 __global__ void block_min_kernel(const double *__restrict__ t, const double *__restrict__ dt,
-                                 const Chunk *__restrict__ chunks, double *__restrict__ part) {
+                                 const Chunk *__restrict__ chunks, double *__restrict__ part,
+                                 int n_chunks, BlockScalars *sc) {
     __shared__ double red[8];
+    __shared__ bool last;
     const Chunk ch = chunks[blockIdx.x];
     double m = INFINITY;
     for (int64_t i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) m = fmin(m, t[i] + dt[i]);
@@ -351,24 +546,40 @@ __global__ void block_min_kernel(const double *__restrict__ t, const double *__r
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x / 32); ++w) m = fmin(m, red[w]);
         part[blockIdx.x] = m;
+        __threadfence();
+        last = atomicAdd(&sc->ticket_min, 1) == (int)gridDim.x - 1;
     }
-}
-
-// Stage 2 of t_next (one CTA): min over the chunk minima.
-__global__ void block_tnext_kernel(const double *__restrict__ part, int n_chunks, BlockScalars *sc) {
-    __shared__ double red[8];
-    double m = INFINITY;
-    for (int k = threadIdx.x; k < n_chunks; k += blockDim.x) m = fmin(m, part[k]);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    m = INFINITY;
+    for (int k = threadIdx.x; k < n_chunks; k += blockDim.x) m = fmin(m, __ldcg(part + k));
     for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
     if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x / 32); ++w) m = fmin(m, red[w]);
         sc->t_next = m;
+        sc->ticket_min = 0;
     }
 }
 
-// Predict every particle to t_next and flag the active ones.
+// Hermite predictor of particle (row) u to time tn: x[0..2] position, x[3..5] velocity.
+__device__ __forceinline__ void predict_row(int64_t n, int64_t u, double tn, const double *__restrict__ t,
+                                            const double *__restrict__ pos, const double *__restrict__ vel,
+                                            const double *__restrict__ acc,
+                                            const double *__restrict__ jerk, double (&x)[6]) {
+    const double h = tn - t[u], h2 = h * h, h3 = h2 * h;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int64_t q = d * n + u;
+        x[d] = pos[q] + vel[q] * h + acc[q] * h2 / 2.0 + jerk[q] * h3 / 6.0;
+        x[3 + d] = vel[q] + acc[q] * h + jerk[q] * h2 / 2.0;
+    }
+}
+
+// Predict every particle to t_next and flag the active ones (FP64 path).
 __global__ void block_predict_kernel(int64_t n, const BlockScalars *__restrict__ sc,
                                      const double *__restrict__ t,
                                      const double *__restrict__ dt, const double *__restrict__ pos,
@@ -379,17 +590,18 @@ __global__ void block_predict_kernel(int64_t n, const BlockScalars *__restrict__
     const bool live = tn <= sc->t_end;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double h = tn - t[i], h2 = h * h, h3 = h2 * h;
+        double x[6];
+        predict_row(n, i, tn, t, pos, vel, acc, jerk, x);
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const int64_t qd = d * n + i;
-            xp[qd] = pos[qd] + vel[qd] * h + acc[qd] * h2 / 2.0 + jerk[qd] * h3 / 6.0;
-            vp[qd] = vel[qd] + acc[qd] * h + jerk[qd] * h2 / 2.0;
+            xp[d * n + i] = x[d];
+            vp[d * n + i] = x[3 + d];
         }
         flag[i] = live && (t[i] + dt[i] == tn);
     }
 }
 
-// Compaction stage 1: active count per chunk.
+// Compaction stage 1 (FP64 path): active count per chunk.
 __global__ void block_count_kernel(const uint8_t *__restrict__ flag, const Chunk *__restrict__ chunks,
                                    int *__restrict__ cnt) {
     __shared__ int red[8];
@@ -405,15 +617,17 @@ __global__ void block_count_kernel(const uint8_t *__restrict__ flag, const Chunk
     }
 }
 
-// Block-wide exclusive scan of int values (one CTA of kScan threads).
+// Block-wide exclusive scan of int values by a CTA of NT threads (L2 reads, so
+// the last CTA of a kernel sees what the others wrote).
+template <int NT>
 __device__ void block_exclusive_scan(const int *in, int *out, int n, int *total) {
-    __shared__ int warp_sums[kScan / 32];
+    __shared__ int warp_sums[NT / 32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int base = 0; base < n; base += kScan) {
+    for (int base = 0; base < n; base += NT) {
         const int i = base + threadIdx.x;
-        const int v = i < n ? in[i] : 0;
+        const int v = i < n ? __ldcg(in + i) : 0;
         int x = v;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -422,94 +636,299 @@ __device__ void block_exclusive_scan(const int *in, int *out, int n, int *total)
         if (threadIdx.x % 32 == 31) warp_sums[threadIdx.x / 32] = x;
         __syncthreads();
         if (threadIdx.x < 32) {
-            int w = warp_sums[threadIdx.x];
+            int w = threadIdx.x < NT / 32 ? warp_sums[threadIdx.x] : 0;
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, w, o);
                 if (threadIdx.x >= o) w += y;
             }
-            warp_sums[threadIdx.x] = w;
+            if (threadIdx.x < NT / 32) warp_sums[threadIdx.x] = w;
         }
         __syncthreads();
         const int warp_off = threadIdx.x >= 32 ? warp_sums[threadIdx.x / 32 - 1] : 0;
         if (i < n) out[i] = carry + warp_off + x - v;
         __syncthreads();
-        if (threadIdx.x == 0) carry += warp_sums[kScan / 32 - 1];
+        if (threadIdx.x == 0) carry += warp_sums[NT / 32 - 1];
         __syncthreads();
     }
     if (threadIdx.x == 0) *total = carry;
 }
 
-// Compaction stage 2 (one CTA): chunk offsets, per-cluster active ranges and
-// i-chunk counts, the split count and the work-queue size.
+// The step's plan (one thread, after the scan of the per-unit active counts;
+// cluster c owns units [unit_first[c], unit_first[c + 1])): per-cluster active
+// ranges and i-chunk counts, the split count, the work-queue size, and the
+// queue head reset for the subset kernel.
+__device__ void plan_step(const int *__restrict__ unit_off, int total, int n_units,
+                          const int32_t *__restrict__ unit_first, int ncl,
+                          const ClusterDev *__restrict__ cl, int cs, int workers, int max_split,
+                          int *__restrict__ act_begin, int *__restrict__ act_n, int *__restrict__ ich_off,
+                          int *__restrict__ item_off, BlockScalars *sc, int *queue_head, int few_max) {
+    const bool few = total > 0 && total <= few_max;
+    int chunks = 0, nf = 0, jb = 0;
+    for (int c = 0; c < ncl; ++c) {
+        const int b = unit_first[c], e = unit_first[c + 1];
+        const int a0 = b < n_units ? unit_off[b] : total;
+        const int a1 = e < n_units ? unit_off[e] : total;
+        act_begin[c] = a0;
+        act_n[c] = a1 - a0;
+        ich_off[c] = chunks;
+        if (!few) chunks += (a1 - a0 + cs - 1) / cs;
+        if (few && a1 > a0) {  // at most total (<= kFewMax) clusters
+            sc->few_cl[nf] = c;
+            sc->few_abeg[nf] = a0;
+            sc->few_jbase[nf] = jb;
+            jb += cl[c].n;
+            ++nf;
+        }
+    }
+    ich_off[ncl] = chunks;
+    sc->few = few;
+    sc->few_ncl = nf;
+    sc->few_jbase[nf] = jb;
+    int split = chunks > 0 ? (2 * workers) / chunks : 1;
+    if (split > max_split) split = max_split;
+    if (split < 1) split = 1;
+    int items = 0;
+    for (int c = 0; c < ncl; ++c) {
+        item_off[c] = items;
+        const int sc_c = split < cl[c].n_jt ? split : (cl[c].n_jt > 0 ? cl[c].n_jt : 1);
+        items += (ich_off[c + 1] - ich_off[c]) * sc_c;
+    }
+    item_off[ncl] = items;
+    sc->n_active = total;
+    sc->n_chunks = chunks;
+    sc->split = split;
+    sc->n_items = items;
+    if (total > 0) {
+        sc->blocks += 1;
+        sc->evals += total;
+    }
+    if (queue_head) *queue_head = 0;
+}
+
+// Compaction stage 2 (FP64 path, one CTA): chunk offsets and the plan.
 __global__ void __launch_bounds__(kScan)
     block_plan_kernel(const int *__restrict__ cnt, int n_chunks, const int32_t *__restrict__ chunk_first,
                       int ncl, const ClusterDev *__restrict__ cl, int cs, int workers, int max_split,
                       int *__restrict__ chunk_off, int *__restrict__ act_begin, int *__restrict__ act_n,
                       int *__restrict__ ich_off, int *__restrict__ item_off, BlockScalars *sc) {
     __shared__ int total;
-    block_exclusive_scan(cnt, chunk_off, n_chunks, &total);
+    block_exclusive_scan<kScan>(cnt, chunk_off, n_chunks, &total);
+    __syncthreads();
+    if (threadIdx.x == 0)
+        plan_step(chunk_off, total, n_chunks, chunk_first, ncl, cl, cs, workers, max_split, act_begin,
+                  act_n, ich_off, item_off, sc, nullptr, 0);
+}
+
+// F32C: one CTA per centre tile of the j-set.  Predicts the tile's particles to
+// t_next (FP64, as block_predict_kernel), packs them as pack_kernel does
+// (FP64 mean position and velocity as float pairs, FP32 offsets, FP32 masses,
+// pads far away with mass 0), flags the active slots and counts them.  The
+// last CTA to finish (ticket) scans the tile counts and plans the step.
+struct BlockPackParams {
+    const int32_t *perm;
+    const ClusterDev *cl;
+    const int32_t *tile_cluster;
+    int tc, n_tiles;
+    int64_t n;
+    const double *mass, *t, *dt, *pos, *vel, *acc, *jerk;
+    float *px, *py, *pz, *pm, *pvx, *pvy, *pvz;
+    float4 *chl, *vchl;
+    uint8_t *flag;  // per slot
+    int *tile_cnt, *tile_off;
+    const int32_t *tile_first;
+    int ncl, cs, workers, max_split;
+    int *act_begin, *act_n, *ich_off, *item_off;
+    BlockScalars *sc;
+    int *queue_head;
+    int few_max;
+};
+
+// Hermite predictor in Horner form for the packed j-set (F32C); its rounding
+// differs from predict_row's only at the FP64 level, far below the FP32 offsets.
+__device__ __forceinline__ void predict_horner(int64_t n, int64_t u, double tn,
+                                               const double *__restrict__ t,
+                                               const double *__restrict__ pos,
+                                               const double *__restrict__ vel,
+                                               const double *__restrict__ acc,
+                                               const double *__restrict__ jerk, double (&x)[6]) {
+    const double h = tn - t[u];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int64_t q = d * n + u;
+        const double a = acc[q], j = jerk[q], v = vel[q];
+        x[d] = pos[q] + h * (v + h * (0.5 * a + h * (j * (1.0 / 6.0))));
+        x[3 + d] = v + h * (a + h * (0.5 * j));
+    }
+}
+
+constexpr int kPackMaxPer = 4;  // slots per thread in block_pack_kernel (tc <= 4 NT)
+
+// FP64 is scarce on this part (about 1/64 of the FP32 rate), so the tile
+// centre comes from an FP32 tree: the mean of the FP32-rounded predicted
+// positions (velocities), stored as a float (lo = 0).  Any centre near the tile
+// serves -- offsets are FP64 differences from it, rounded once to FP32 -- and
+// the mean keeps them small.
+template <int NT>
+__global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q) {
+    __shared__ float redf[NT / 32][8];
+    __shared__ double cen[6];
+    __shared__ bool last;
+    __shared__ int total;
+    const int tile = blockIdx.x;
+    const double tn = q.sc->t_next;
+    const bool live = tn <= q.sc->t_end;
+    const ClusterDev cl = q.cl[q.tile_cluster[tile]];
+    const int base = tile * q.tc;
+    const int per = q.tc / NT;
+    float sf[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // position, velocity sums (6), count, active count
+    double x[kPackMaxPer][6];
+    bool act[kPackMaxPer];
+#pragma unroll
+    for (int r = 0; r < kPackMaxPer; ++r) {
+        act[r] = false;
+        const int slot = base + threadIdx.x + NT * r;
+        if (r < per && slot - cl.slot_begin < cl.n) {
+            const int64_t u = q.perm[slot];
+            predict_horner(q.n, u, tn, q.t, q.pos, q.vel, q.acc, q.jerk, x[r]);
+#pragma unroll
+            for (int d = 0; d < 6; ++d) sf[d] += (float)x[r][d];
+            sf[6] += 1.0f;
+            act[r] = live && (q.t[u] + q.dt[u] == tn);
+            sf[7] += act[r] ? 1.0f : 0.0f;
+        }
+    }
+    // CTA sum in FP32, fixed order (counts are exact: at most tc)
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sf[k] += __shfl_xor_sync(0xffffffffu, sf[k], o);
+    if (threadIdx.x % 32 == 0)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) redf[threadIdx.x / 32][k] = sf[k];
     __syncthreads();
     if (threadIdx.x == 0) {
-        int chunks = 0;
-        for (int c = 0; c < ncl; ++c) {
-            const int b = chunk_first[c], e = chunk_first[c + 1];
-            const int a0 = b < n_chunks ? chunk_off[b] : total;
-            const int a1 = e < n_chunks ? chunk_off[e] : total;
-            act_begin[c] = a0;
-            act_n[c] = a1 - a0;
-            ich_off[c] = chunks;
-            chunks += (a1 - a0 + cs - 1) / cs;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float v = redf[0][k];
+            for (int w = 1; w < NT / 32; ++w) v += redf[w][k];
+            sf[k] = v;
         }
-        ich_off[ncl] = chunks;
-        int split = chunks > 0 ? (2 * workers) / chunks : 1;
-        if (split > max_split) split = max_split;
-        if (split < 1) split = 1;
-        int items = 0;
-        for (int c = 0; c < ncl; ++c) {
-            item_off[c] = items;
-            const int sc_c = split < cl[c].n_jt ? split : (cl[c].n_jt > 0 ? cl[c].n_jt : 1);
-            items += (ich_off[c + 1] - ich_off[c]) * sc_c;
+        const float inv = sf[6] > 0.0f ? 1.0f / sf[6] : 0.0f;
+        float h[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            h[d] = sf[d] * inv;
+            cen[d] = (double)h[d];
         }
-        item_off[ncl] = items;
-        sc->n_active = total;
-        sc->n_chunks = chunks;
-        sc->split = split;
-        sc->n_items = items;
-        if (total > 0) {
-            sc->blocks += 1;
-            sc->evals += total;
+        q.chl[2 * tile + 0] = make_float4(h[0], h[1], h[2], 0.0f);
+        q.chl[2 * tile + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        q.vchl[2 * tile + 0] = make_float4(h[3], h[4], h[5], 0.0f);
+        q.vchl[2 * tile + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        q.tile_cnt[tile] = (int)sf[7];
+    }
+    __syncthreads();
+    double c[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) c[d] = cen[d];
+#pragma unroll
+    for (int r = 0; r < kPackMaxPer; ++r) {
+        const int slot = base + threadIdx.x + NT * r;
+        if (r >= per) break;
+        if (slot - cl.slot_begin < cl.n) {
+            q.px[slot] = (float)(x[r][0] - c[0]);
+            q.py[slot] = (float)(x[r][1] - c[1]);
+            q.pz[slot] = (float)(x[r][2] - c[2]);
+            q.pm[slot] = (float)q.mass[q.perm[slot]];
+            q.pvx[slot] = (float)(x[r][3] - c[3]);
+            q.pvy[slot] = (float)(x[r][4] - c[4]);
+            q.pvz[slot] = (float)(x[r][5] - c[5]);
+            q.flag[slot] = act[r];
+        } else {
+            q.px[slot] = kPadOffset;
+            q.py[slot] = kPadOffset;
+            q.pz[slot] = kPadOffset;
+            q.pm[slot] = 0.0f;
+            q.pvx[slot] = q.pvy[slot] = q.pvz[slot] = 0.0f;
+            q.flag[slot] = 0;
         }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&q.sc->ticket_pack, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    block_exclusive_scan<NT>(q.tile_cnt, q.tile_off, q.n_tiles, &total);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        plan_step(q.tile_off, total, q.n_tiles, q.tile_first, q.ncl, q.cl, q.cs, q.workers, q.max_split,
+                  q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max);
+        q.sc->ticket_pack = 0;
     }
 }
 
-// Compaction stage 3: ordered scatter of the active rows (as j-set slots for
-// F32C, as rows for F64) to act[] in row order within each cluster.
-__global__ void block_scatter_kernel(const uint8_t *__restrict__ flag, const Chunk *__restrict__ chunks,
-                                     const int *__restrict__ chunk_off, const int32_t *__restrict__ inv,
-                                     int32_t *__restrict__ act) {
-    __shared__ int warp_cnt[8];
-    __shared__ int base_s;
-    const Chunk ch = chunks[blockIdx.x];
-    if (threadIdx.x == 0) base_s = chunk_off[blockIdx.x];
-    __syncthreads();
-    for (int64_t b = ch.begin; b < ch.end; b += blockDim.x) {
+// Work item k -> (cluster, i-chunk of the active list, j-range split).
+__device__ __forceinline__ SubItem make_item(int k, int ncl, const ClusterDev *__restrict__ cl, int cs,
+                                             int split, const int *__restrict__ act_begin,
+                                             const int *__restrict__ act_n,
+                                             const int *__restrict__ ich_off,
+                                             const int *__restrict__ item_off) {
+    int lo = 0, hi = ncl;  // cluster c with item_off[c] <= k < item_off[c + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (item_off[mid] <= k) lo = mid;
+        else hi = mid;
+    }
+    const int c = lo;
+    const ClusterDev d = cl[c];
+    const int sc_c = split < d.n_jt ? split : (d.n_jt > 0 ? d.n_jt : 1);
+    const int local = k - item_off[c];
+    const int ch = local / sc_c, s = local % sc_c;
+    SubItem it;
+    it.a0 = act_begin[c] + ch * cs;
+    it.na = min(cs, act_n[c] - ch * cs);
+    it.cluster = c;
+    it.chunk = ich_off[c] + ch;
+    it.jt0 = (int)((int64_t)s * d.n_jt / sc_c);
+    it.jt1 = (int)((int64_t)(s + 1) * d.n_jt / sc_c);
+    it.split = s;
+    it.nsplit = sc_c;
+    it.pbase = sc_c > 1 ? it.chunk * split : 0;
+    it.pad = 0;
+    return it;
+}
+
+// Ordered compaction of one run of flags [begin, end): the k-th set flag in
+// order writes its index to act[off + k] (warp ballots, warps in order).
+template <int NT>
+__device__ __forceinline__ void compact_run(const uint8_t *__restrict__ flag, int64_t begin, int64_t end,
+                                            int off, int32_t *__restrict__ act) {
+    __shared__ int warp_cnt[NT / 32];
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    for (int64_t b = begin; b < end; b += NT) {
         const int64_t i = b + threadIdx.x;
-        const int f = i < ch.end ? flag[i] : 0;
+        const int f = i < end ? flag[i] : 0;
         const unsigned mask = __ballot_sync(0xffffffffu, f);
-        const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
         if (lane == 0) warp_cnt[w] = __popc(mask);
         __syncthreads();
-        int off = base_s;
-        for (int k = 0; k < w; ++k) off += warp_cnt[k];
-        if (f) act[off + __popc(mask & ((1u << lane) - 1u))] = inv ? inv[i] : (int32_t)i;
-        __syncthreads();
-        if (threadIdx.x == 0)
-            for (int k = 0; k < (int)(blockDim.x / 32); ++k) base_s += warp_cnt[k];
+        int o = off;
+        for (int k = 0; k < w; ++k) o += warp_cnt[k];
+        if (f) act[o + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
+        for (int k = 0; k < NT / 32; ++k) off += warp_cnt[k];
         __syncthreads();
     }
 }
 
-// Work queue: item k -> (cluster, i-chunk of the active list, j-range split).
+// Compaction stage 3 (FP64 path): ordered scatter of the active rows to act[]
+// in row order within each cluster.
+__global__ void block_scatter_kernel(const uint8_t *__restrict__ flag, const Chunk *__restrict__ chunks,
+                                     const int *__restrict__ chunk_off, int32_t *__restrict__ act) {
+    const Chunk ch = chunks[blockIdx.x];
+    const int off = __ldcg(chunk_off + blockIdx.x);
+    compact_run<256>(flag, ch.begin, ch.end, off, act);
+}
+
+// Work queue (FP64 path).
 __global__ void block_items_kernel(int ncl, const ClusterDev *__restrict__ cl, int cs,
                                    const int *__restrict__ act_begin, const int *__restrict__ act_n,
                                    const int *__restrict__ ich_off, const int *__restrict__ item_off,
@@ -519,54 +938,60 @@ __global__ void block_items_kernel(int ncl, const ClusterDev *__restrict__ cl, i
     const int split = sc->split;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_items && k < max_items;
          k += gridDim.x * blockDim.x) {
-        int lo = 0, hi = ncl;  // cluster c with item_off[c] <= k < item_off[c + 1]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) / 2;
-            if (item_off[mid] <= k) lo = mid;
-            else hi = mid;
-        }
-        const int c = lo;
-        const ClusterDev d = cl[c];
-        const int sc_c = split < d.n_jt ? split : (d.n_jt > 0 ? d.n_jt : 1);
-        const int local = k - item_off[c];
-        const int ch = local / sc_c, s = local % sc_c;
-        SubItem it;
-        it.a0 = act_begin[c] + ch * cs;
-        it.na = min(cs, act_n[c] - ch * cs);
-        it.cluster = c;
-        it.chunk = ich_off[c] + ch;
-        it.jt0 = (int)((int64_t)s * d.n_jt / sc_c);
-        it.jt1 = (int)((int64_t)(s + 1) * d.n_jt / sc_c);
-        it.split = s;
-        it.nsplit = sc_c;
-        it.pbase = sc_c > 1 ? it.chunk * split : 0;
-        it.pad = 0;
+        const SubItem it = make_item(k, ncl, cl, cs, split, act_begin, act_n, ich_off, item_off);
         items[k] = it;
-        if (s == 0) info[it.chunk] = it;
+        if (it.split == 0) info[it.chunk] = it;
     }
 }
 
-// Inverse of the j-set permutation: inv[row] = slot.
-__global__ void inverse_perm_kernel(int64_t n_pad, const int32_t *__restrict__ perm, int32_t *inv) {
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t u = perm[s];
-        if (u >= 0) inv[u] = (int32_t)s;
+// F32C queue: one CTA per centre tile compacts the tile's active slots to
+// act[] (slot order within each cluster), and all threads build the items.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+    block_queue_kernel(const uint8_t *__restrict__ flag, int tc, const int *__restrict__ tile_cnt,
+                       const int *__restrict__ tile_off, int32_t *__restrict__ act, int ncl,
+                       const ClusterDev *__restrict__ cl, int cs, const int *__restrict__ act_begin,
+                       const int *__restrict__ act_n, const int *__restrict__ ich_off,
+                       const int *__restrict__ item_off, const BlockScalars *__restrict__ sc,
+                       int max_items, SubItem *__restrict__ items, SubItem *__restrict__ info) {
+    const int tile = blockIdx.x;
+    if (tile_cnt[tile] > 0)  // uniform over the CTA
+        compact_run<NT>(flag, (int64_t)tile * tc, (int64_t)(tile + 1) * tc, __ldcg(tile_off + tile), act);
+    const int n_items = sc->n_items;
+    const int split = sc->split;
+    for (int k = blockIdx.x * NT + threadIdx.x; k < n_items && k < max_items; k += gridDim.x * NT) {
+        const SubItem it = make_item(k, ncl, cl, cs, split, act_begin, act_n, ich_off, item_off);
+        items[k] = it;
+        if (it.split == 0) info[it.chunk] = it;
     }
+}
+
+// 1/h, exact for a power of two h (built from its exponent; FP64 division is
+// slow on this part), else the division.
+__device__ __forceinline__ double recip_pow2(double h) {
+    const long long b = __double_as_longlong(h);
+    if ((b & 0x000FFFFFFFFFFFFFLL) == 0 && b > 0 && b < 0x7FE0000000000000LL)
+        return __longlong_as_double(0x7FE0000000000000LL - b);
+    return 1.0 / h;
 }
 
 // Correct the active particles over their own steps and choose the next step.
-__global__ void block_correct_kernel(int64_t n, const uint8_t *__restrict__ flag,
+// Work runs over the active list; row = perm[act[k]] (F32C, act holds j-set
+// slots) or act[k] (FP64).  Steps are powers of two, so dividing by h, h^2, h^3
+// is the exact multiplication by their reciprocals.
+__global__ void block_correct_kernel(int64_t n, const int32_t *__restrict__ act,
+                                     const int32_t *__restrict__ perm,
                                      const BlockScalars *__restrict__ sc, double *t, double *dt,
                                      double *pos, double *vel, double *acc, double *jerk,
                                      double *pot, const double *__restrict__ a1,
                                      const double *__restrict__ j1, const double *__restrict__ p1,
                                      double dt_max, double dt_min, double eta) {
     const double tn = sc->t_next;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if (!flag[i]) continue;
+    const int n_active = sc->n_active;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_active; k += gridDim.x * blockDim.x) {
+        const int64_t i = perm ? perm[act[k]] : act[k];
         const double h = dt[i], h2 = h * h, h3 = h2 * h;
+        const double ih = recip_pow2(h), ih2 = ih * ih, ih3 = ih2 * ih;
         double A1[3], J1[3], A2[3], A3[3];
         for (int d = 0; d < 3; ++d) {
             const int64_t q = d * n + i;
@@ -576,8 +1001,8 @@ __global__ void block_correct_kernel(int64_t n, const uint8_t *__restrict__ flag
             const double v1 = v0 + (a0 + A1[d]) * h / 2.0 + (j0 - J1[d]) * h2 / 12.0;
             pos[q] = pos[q] + (v0 + v1) * h / 2.0 + (a0 - A1[d]) * h2 / 12.0;
             vel[q] = v1;
-            A3[d] = (12.0 * (a0 - A1[d]) + 6.0 * h * (j0 + J1[d])) / h3;
-            A2[d] = (-6.0 * (a0 - A1[d]) - h * (4.0 * j0 + 2.0 * J1[d])) / h2 + h * A3[d];
+            A3[d] = (12.0 * (a0 - A1[d]) + 6.0 * h * (j0 + J1[d])) * ih3;
+            A2[d] = (-6.0 * (a0 - A1[d]) - h * (4.0 * j0 + 2.0 * J1[d])) * ih2 + h * A3[d];
             acc[q] = A1[d];
             jerk[q] = J1[d];
         }
@@ -605,7 +1030,7 @@ int grid_of(int64_t work, int threads) {
 
 }  // namespace
 
-int subset_shapes(int *block, int *p, int *tj, int *minb, int cap) {
+int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap) {
     int n = 0;
     for (const SubsetShape &s : kSubsetShapes) {
         if (s.eps_zero) continue;
@@ -613,6 +1038,7 @@ int subset_shapes(int *block, int *p, int *tj, int *minb, int cap) {
             block[n] = s.block;
             p[n] = s.p;
             tj[n] = s.tj;
+            groups[n] = s.groups;
             minb[n] = s.minb;
         }
         ++n;
@@ -629,11 +1055,12 @@ cudaError_t launch_subset_reduce(int max_chunks, int max_ctas, const F32CSubsetP
     return cudaGetLastError();
 }
 
-int subset_occupancy(int block, int p, int tj, int minb, bool eps_zero) {
-    const SubsetShape *s = find_subset(block, p, tj, minb, eps_zero);
+int subset_occupancy(int block, int p, int tj, int groups, int minb, bool eps_zero) {
+    const SubsetShape *s = find_subset(block, p, tj, groups, minb, eps_zero);
     if (!s) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, s->kernel, block, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, s->kernel, block * groups, 0) != cudaSuccess)
+        return 0;
     return n;
 }
 
@@ -653,43 +1080,67 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         if (e != cudaSuccess) return e; \
         ++*kernels;                     \
     } while (0)
-    NB_BL((block_min_kernel<<<b.n_chunks, 256, 0, s>>>(b.t, b.dt, b.chunks, b.part)));
-    NB_BL((block_tnext_kernel<<<1, 256, 0, s>>>(b.part, b.n_chunks, b.sc)));
-    NB_BL((block_predict_kernel<<<grid_of(b.n, 256), 256, 0, s>>>(
-        b.n, b.sc, b.t, b.dt, b.pos, b.vel, b.acc, b.jerk, b.xp, b.vp, b.flag)));
-    NB_BL((block_count_kernel<<<b.n_chunks, 256, 0, s>>>(b.flag, b.chunks, b.cnt)));
-    NB_BL((block_plan_kernel<<<1, kScan, 0, s>>>(b.cnt, b.n_chunks, b.chunk_first, b.ncl, b.cl, b.cs,
-                                                  b.workers, b.max_split, b.chunk_off, b.act_begin,
-                                                  b.act_n, b.ich_off, b.item_off, b.sc)));
-#undef NB_BL
+    NB_BL((block_min_kernel<<<b.n_chunks, 256, 0, s>>>(b.t, b.dt, b.chunks, b.part, b.n_chunks, b.sc)));
+    if (b.px) {
+        if (b.tc <= 0 || b.tc % 128 != 0 || b.tc > kPackMaxPer * (b.tc % 256 == 0 ? 256 : 128))
+            return cudaErrorInvalidValue;
+        BlockPackParams q{};
+        q.perm = b.perm; q.cl = b.cl; q.tile_cluster = b.tile_cluster; q.tc = b.tc;
+        q.n_tiles = b.n_tiles; q.n = b.n; q.mass = b.mass; q.t = b.t; q.dt = b.dt;
+        q.pos = b.pos; q.vel = b.vel; q.acc = b.acc; q.jerk = b.jerk;
+        q.px = b.px; q.py = b.py; q.pz = b.pz; q.pm = b.pm;
+        q.pvx = b.pvx; q.pvy = b.pvy; q.pvz = b.pvz; q.chl = b.chl; q.vchl = b.vchl;
+        q.flag = b.flag; q.tile_cnt = b.cnt; q.tile_off = b.chunk_off; q.tile_first = b.tile_first;
+        q.ncl = b.ncl; q.cs = b.cs; q.workers = b.workers; q.max_split = b.max_split;
+        q.act_begin = b.act_begin; q.act_n = b.act_n; q.ich_off = b.ich_off; q.item_off = b.item_off;
+        q.sc = b.sc; q.queue_head = b.queue_head; q.few_max = b.few_max;
+        if (b.tc % 256 == 0) NB_BL((block_pack_kernel<256><<<b.n_tiles, 256, 0, s>>>(q)));
+        else NB_BL((block_pack_kernel<128><<<b.n_tiles, 128, 0, s>>>(q)));
+    } else {
+        NB_BL((block_predict_kernel<<<grid_of(b.n, 256), 256, 0, s>>>(
+            b.n, b.sc, b.t, b.dt, b.pos, b.vel, b.acc, b.jerk, b.xp, b.vp, b.flag)));
+        NB_BL((block_count_kernel<<<b.n_chunks, 256, 0, s>>>(b.flag, b.chunks, b.cnt)));
+        NB_BL((block_plan_kernel<<<1, kScan, 0, s>>>(b.cnt, b.n_chunks, b.chunk_first, b.ncl, b.cl, b.cs,
+                                                      b.workers, b.max_split, b.chunk_off, b.act_begin,
+                                                      b.act_n, b.ich_off, b.item_off, b.sc)));
+    }
     return cudaSuccess;
 }
 
-cudaError_t launch_block_queue(const BlockLaunch &b, const int32_t *inv, cudaStream_t s, int *kernels) {
+cudaError_t launch_block_queue(const BlockLaunch &b, cudaStream_t s, int *kernels) {
     cudaError_t e;
-    block_scatter_kernel<<<b.n_chunks, 256, 0, s>>>(b.flag, b.chunks, b.chunk_off, inv, b.act);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    block_items_kernel<<<grid_of(b.max_items, 256), 256, 0, s>>>(
-        b.ncl, b.cl, b.cs, b.act_begin, b.act_n, b.ich_off, b.item_off, b.sc, b.max_items, b.items,
-        b.info);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    *kernels += 2;
+    if (b.px) {
+        if (b.tc % 256 == 0)
+            NB_BL((block_queue_kernel<256><<<b.n_tiles, 256, 0, s>>>(
+                b.flag, b.tc, b.cnt, b.chunk_off, b.act, b.ncl, b.cl, b.cs, b.act_begin, b.act_n, b.ich_off,
+                b.item_off, b.sc, b.max_items, b.items, b.info)));
+        else
+            NB_BL((block_queue_kernel<128><<<b.n_tiles, 128, 0, s>>>(
+                b.flag, b.tc, b.cnt, b.chunk_off, b.act, b.ncl, b.cl, b.cs, b.act_begin, b.act_n, b.ich_off,
+                b.item_off, b.sc, b.max_items, b.items, b.info)));
+    } else {
+        NB_BL((block_scatter_kernel<<<b.n_chunks, 256, 0, s>>>(b.flag, b.chunks, b.chunk_off, b.act)));
+        NB_BL((block_items_kernel<<<grid_of(b.max_items, 256), 256, 0, s>>>(
+            b.ncl, b.cl, b.cs, b.act_begin, b.act_n, b.ich_off, b.item_off, b.sc, b.max_items, b.items,
+            b.info)));
+    }
     return cudaSuccess;
 }
+#undef NB_BL
 
-cudaError_t launch_inverse_perm(int64_t n_pad, const int32_t *perm, int32_t *inv, cudaStream_t s) {
-    if (n_pad <= 0) return cudaSuccess;
-    inverse_perm_kernel<<<grid_of(n_pad, 256), 256, 0, s>>>(n_pad, perm, inv);
+cudaError_t launch_subset_few(const F32CJerkParams &prm, const int32_t *act, BlockScalars *sc,
+                              double *part, cudaStream_t s) {
+    subset_few_kernel<<<kFewCtas, kFewThreads, 0, s>>>(prm, act, sc, part);
     return cudaGetLastError();
 }
 
-cudaError_t launch_subset_f32c(int block, int p, int tj, int minb, bool eps_zero, int grid,
-                               const F32CSubsetParams &prm, cudaStream_t st) {
-    const SubsetShape *sh = find_subset(block, p, tj, minb, eps_zero);
+cudaError_t launch_subset_f32c(int block, int p, int tj, int groups, int minb, bool eps_zero,
+                               int grid, const F32CSubsetParams &prm, cudaStream_t st) {
+    const SubsetShape *sh = find_subset(block, p, tj, groups, minb, eps_zero);
     if (!sh) return cudaErrorNotSupported;
     if (grid <= 0) return cudaSuccess;
     void *args[] = {(void *)&prm};
-    return cudaLaunchKernel(sh->kernel, dim3(grid), dim3(block), args, 0, st);
+    return cudaLaunchKernel(sh->kernel, dim3(grid), dim3(block * groups), args, 0, st);
 }
 
 cudaError_t launch_subset_f64(int max_items, const double *xp, const double *vp, const double *mass,
@@ -702,13 +1153,13 @@ cudaError_t launch_subset_f64(int max_items, const double *xp, const double *vp,
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_correct(int64_t n, const uint8_t *flag, const BlockScalars *sc, double *t,
-                                 double *dt, double *pos, double *vel, double *acc, double *jerk,
-                                 double *pot, const double *a1, const double *j1, const double *p1,
-                                 double dt_max, double dt_min, double eta, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    block_correct_kernel<<<grid_of(n, 256), 256, 0, s>>>(n, flag, sc, t, dt, pos, vel, acc, jerk, pot,
-                                                         a1, j1, p1, dt_max, dt_min, eta);
+cudaError_t launch_block_correct(const BlockLaunch &b, const double *a1, const double *j1,
+                                 const double *p1, double *pot, double dt_max, double dt_min, double eta,
+                                 cudaStream_t s) {
+    if (b.n <= 0) return cudaSuccess;
+    block_correct_kernel<<<grid_of(b.n, 256), 256, 0, s>>>(b.n, b.act, b.px ? b.perm : nullptr, b.sc, b.t,
+                                                           b.dt, b.pos, b.vel, b.acc, b.jerk, pot, a1, j1,
+                                                           p1, dt_max, dt_min, eta);
     return cudaGetLastError();
 }
 

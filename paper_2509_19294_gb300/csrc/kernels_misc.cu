@@ -3,138 +3,81 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "block_reduce.cuh"
 #include "nbody_internal.h"
 
 namespace nbody {
 
 namespace {
 
-constexpr int kPackWarps = 8;
-
-// Deterministic block sum of NV doubles (fixed shuffle tree, then warps in order).
-template <int NT, int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double (*scratch)[NV]) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) scratch[warp][k] = v[k];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < NT / 32; ++w) s += scratch[w][k];
-            scratch[0][k] = s;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = scratch[0][k];
-}
-
-// One warp per centre tile: centre = FP64 mean of the tile's real particles
-// (fixed-order shuffle tree, so bitwise reproducible), FP32 offsets from it,
-// FP32 masses; pad slots get mass 0 and a far offset.  The centre is stored as
-// a float pair hi + lo for the force kernel.  No block barriers: a CTA of
-// kPackWarps warps packs kPackWarps independent tiles.
-__global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(const PackParams p, int n_tiles) {
-    const int lane = threadIdx.x % 32;
-    const int t = blockIdx.x * kPackWarps + threadIdx.x / 32;
-    if (t >= n_tiles) return;  // warp-uniform
+// One CTA per centre tile: centre = FP64 mean of the tile's real particles
+// (fixed reduction tree, so bitwise reproducible), FP32 offsets from it, FP32
+// masses; pad slots get mass 0 and a far offset.  The centre is stored as a
+// float pair hi + lo for the force kernels.  With VEL the tile's velocities are
+// packed the same way (mean velocity as a float pair, offsets; pads 0).
+template <int NT, bool VEL>
+__global__ void __launch_bounds__(NT) pack_kernel(const PackParams p) {
+    constexpr int NV = VEL ? 7 : 4;
+    __shared__ double red[NT / 32][NV];
+    const int t = blockIdx.x;
     const ClusterDev cl = p.cl[p.tile_cluster[t]];
     const int base = t * p.tc;
-    const int per = p.tc / 32;
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 4
+    const int per = p.tc / NT;
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s[k] = 0.0;
     for (int r = 0; r < per; ++r) {
-        const int slot = base + lane + 32 * r;
+        const int slot = base + threadIdx.x + NT * r;
         if (slot - cl.slot_begin < cl.n) {
             const int64_t u = p.perm[slot];
-            s[0] += p.pos[u];
-            s[1] += p.pos[p.n + u];
-            s[2] += p.pos[2 * p.n + u];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) s[d] += p.pos[d * p.n + u];
             s[3] += 1.0;
+            if (VEL)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) s[4 + d] += p.vel[d * p.n + u];
         }
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    block_sum<NT, NV>(s, red);
     const double cnt = s[3] > 0.0 ? s[3] : 1.0;
-    const double cx = s[0] / cnt, cy = s[1] / cnt, cz = s[2] / cnt;
-#pragma unroll 4
+    double c[6];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        c[d] = s[d] / cnt;
+        c[3 + d] = VEL ? s[4 + d] / cnt : 0.0;
+    }
     for (int r = 0; r < per; ++r) {
-        const int slot = base + lane + 32 * r;
+        const int slot = base + threadIdx.x + NT * r;
         if (slot - cl.slot_begin < cl.n) {
             const int64_t u = p.perm[slot];
-            p.px[slot] = (float)(p.pos[u] - cx);
-            p.py[slot] = (float)(p.pos[p.n + u] - cy);
-            p.pz[slot] = (float)(p.pos[2 * p.n + u] - cz);
+            p.px[slot] = (float)(p.pos[u] - c[0]);
+            p.py[slot] = (float)(p.pos[p.n + u] - c[1]);
+            p.pz[slot] = (float)(p.pos[2 * p.n + u] - c[2]);
             p.pm[slot] = (float)p.mass[u];
+            if (VEL) {
+                p.pvx[slot] = (float)(p.vel[u] - c[3]);
+                p.pvy[slot] = (float)(p.vel[p.n + u] - c[4]);
+                p.pvz[slot] = (float)(p.vel[2 * p.n + u] - c[5]);
+            }
         } else {
             p.px[slot] = kPadOffset;
             p.py[slot] = kPadOffset;
             p.pz[slot] = kPadOffset;
             p.pm[slot] = 0.0f;
+            if (VEL) p.pvx[slot] = p.pvy[slot] = p.pvz[slot] = 0.0f;
         }
     }
-    if (lane == 0) {
-        const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
-        p.chl[2 * t + 0] = make_float4(hx, hy, hz, 0.0f);
-        p.chl[2 * t + 1] = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), 0.0f);
-    }
-}
-
-// Velocity half of the jerk path's packing (one warp per tile, as pack_kernel).
-__global__ void __launch_bounds__(kPackWarps * 32)
-    pack_vel_kernel(const double *__restrict__ vel, const int32_t *__restrict__ perm,
-                    const ClusterDev *__restrict__ cls, const int32_t *__restrict__ tile_cluster,
-                    int tc, int64_t n, int n_tiles, float *pvx, float *pvy, float *pvz,
-                    float4 *vchl) {
-    const int lane = threadIdx.x % 32;
-    const int t = blockIdx.x * kPackWarps + threadIdx.x / 32;
-    if (t >= n_tiles) return;
-    const ClusterDev cl = cls[tile_cluster[t]];
-    const int base = t * tc;
-    const int per = tc / 32;
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 4
-    for (int r = 0; r < per; ++r) {
-        const int slot = base + lane + 32 * r;
-        if (slot - cl.slot_begin < cl.n) {
-            const int64_t u = perm[slot];
-            s[0] += vel[u];
-            s[1] += vel[n + u];
-            s[2] += vel[2 * n + u];
-            s[3] += 1.0;
-        }
-    }
+    if (threadIdx.x == 0) {
+        float h[6];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
-    const double cnt = s[3] > 0.0 ? s[3] : 1.0;
-    const double cx = s[0] / cnt, cy = s[1] / cnt, cz = s[2] / cnt;
-#pragma unroll 4
-    for (int r = 0; r < per; ++r) {
-        const int slot = base + lane + 32 * r;
-        if (slot - cl.slot_begin < cl.n) {
-            const int64_t u = perm[slot];
-            pvx[slot] = (float)(vel[u] - cx);
-            pvy[slot] = (float)(vel[n + u] - cy);
-            pvz[slot] = (float)(vel[2 * n + u] - cz);
-        } else {
-            pvx[slot] = pvy[slot] = pvz[slot] = 0.0f;
+        for (int d = 0; d < 6; ++d) h[d] = (float)c[d];
+        p.chl[2 * t + 0] = make_float4(h[0], h[1], h[2], 0.0f);
+        p.chl[2 * t + 1] = make_float4((float)(c[0] - h[0]), (float)(c[1] - h[1]), (float)(c[2] - h[2]), 0.0f);
+        if (VEL) {
+            p.vchl[2 * t + 0] = make_float4(h[3], h[4], h[5], 0.0f);
+            p.vchl[2 * t + 1] =
+                make_float4((float)(c[3] - h[3]), (float)(c[4] - h[4]), (float)(c[5] - h[5]), 0.0f);
         }
-    }
-    if (lane == 0) {
-        const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
-        vchl[2 * t + 0] = make_float4(hx, hy, hz, 0.0f);
-        vchl[2 * t + 1] = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), 0.0f);
     }
 }
 
@@ -252,18 +195,15 @@ int grid_for(int64_t work, int threads) {
 
 cudaError_t launch_pack(int n_tiles, const PackParams &prm, cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
-    if (prm.tc % 32 != 0) return cudaErrorInvalidValue;
-    pack_kernel<<<(n_tiles + kPackWarps - 1) / kPackWarps, kPackWarps * 32, 0, s>>>(prm, n_tiles);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pack_vel(int n_tiles, const double *vel, const int32_t *perm,
-                            const ClusterDev *cl, const int32_t *tile_cluster, int tc, int64_t n,
-                            float *pvx, float *pvy, float *pvz, float4 *vchl, cudaStream_t s) {
-    if (n_tiles <= 0) return cudaSuccess;
-    if (tc % 32 != 0) return cudaErrorInvalidValue;
-    pack_vel_kernel<<<(n_tiles + kPackWarps - 1) / kPackWarps, kPackWarps * 32, 0, s>>>(
-        vel, perm, cl, tile_cluster, tc, n, n_tiles, pvx, pvy, pvz, vchl);
+    if (prm.tc <= 0 || prm.tc % 128 != 0) return cudaErrorInvalidValue;
+    const bool vel = prm.vel != nullptr;
+    if (prm.tc % 256 == 0) {
+        if (vel) pack_kernel<256, true><<<n_tiles, 256, 0, s>>>(prm);
+        else pack_kernel<256, false><<<n_tiles, 256, 0, s>>>(prm);
+    } else {
+        if (vel) pack_kernel<128, true><<<n_tiles, 128, 0, s>>>(prm);
+        else pack_kernel<128, false><<<n_tiles, 128, 0, s>>>(prm);
+    }
     return cudaGetLastError();
 }
 

@@ -47,6 +47,7 @@ struct JerkPath {
     int64_t n_pad = 0;
     ClusterDev *dcl = nullptr;
     int32_t *tile_cluster = nullptr;
+    int32_t *tile_first = nullptr;  // [ncl + 1] first centre tile of each cluster
     Item *items = nullptr;
     int *counters = nullptr;
     double *partial = nullptr;
@@ -63,12 +64,17 @@ struct BlockState {
     bool started = false;
     double dt_max = 0.0, dt_min = 0.0, eta = 0.0;
     int cs = 0, workers = 1, max_split = 1, max_items = 0, max_chunks = 0;
+    // Morton re-sorting follows simulated time here: once per reorder_every
+    // multiples of dt_max, at the start of the next 16-step batch
+    int64_t reorder_epoch = 0;
+    bool reorder_pending = false;
     nbody_tiles sub{0, 0, 0, 0, 0};  // subset kernel shape (F32C)
     double *t = nullptr, *dt = nullptr, *part = nullptr, *partial = nullptr, *p1 = nullptr;
+    double *few_part = nullptr;  // few-particle path: kFewCtas * kFewMax * 7
     uint8_t *flag = nullptr;
     int *cnt = nullptr, *chunk_off = nullptr, *act_begin = nullptr, *act_n = nullptr;
     int *ich_off = nullptr, *item_off = nullptr;
-    int32_t *act = nullptr, *inv = nullptr;
+    int32_t *act = nullptr;
     SubItem *items = nullptr, *info = nullptr;
     BlockScalars *sc = nullptr;
 };
@@ -100,6 +106,7 @@ struct nbody_ctx {
     int64_t n_pad = 0;
     int n_tiles = 0;
     int32_t *tile_cluster = nullptr;
+    int32_t *tile_first = nullptr;  // [ncl + 1] first centre tile of each cluster
     Item *items = nullptr;
     int n_items = 0;
     int *counters = nullptr;
@@ -611,6 +618,7 @@ void free_jerk(nbody_ctx *ctx) {
     JerkPath &j = ctx->jp;
     dev_free(&j.dcl);
     dev_free(&j.tile_cluster);
+    dev_free(&j.tile_first);
     dev_free(&j.items);
     dev_free(&j.counters);
     dev_free(&j.partial);
@@ -629,8 +637,13 @@ nbody_tiles default_jerk_tiles(const nbody_ctx *c) {
 }
 
 // Build the jerk path's geometry for tile shape t (F32C) and the Hermite scratch.
+void free_block(nbody_ctx *ctx);
+
+// (Re)builds the jerk path's j-set geometry; block-step state sized for the old
+// geometry is dropped (nbody_block_start must be called again).
 int build_jerk(nbody_ctx *ctx, nbody_tiles t, double jfrac = 1.0) {
     drop_graphs(ctx);
+    free_block(ctx);
     free_jerk(ctx);
     JerkPath &j = ctx->jp;
     int rc;
@@ -655,6 +668,9 @@ int build_jerk(nbody_ctx *ctx, nbody_tiles t, double jfrac = 1.0) {
         j.grid = std::min(j.n_items, workers);
         if ((rc = upload(ctx, &j.dcl, pl.cl))) return rc;
         if ((rc = upload(ctx, &j.tile_cluster, pl.tile_cluster))) return rc;
+        std::vector<int32_t> tfirst(pl.cl.size() + 1, (int32_t)pl.n_tiles);
+        for (size_t c = 0; c < pl.cl.size(); ++c) tfirst[c] = pl.cl[c].slot_begin / tc;
+        if ((rc = upload(ctx, &j.tile_first, tfirst))) return rc;
         if ((rc = upload(ctx, &j.items, pl.items))) return rc;
         if ((rc = dev_alloc(ctx, &j.counters, (size_t)j.n_tiles + 1))) return rc;
         if ((rc = dev_alloc(ctx, &j.partial, (size_t)pl.partial_slots * 7 * tc))) return rc;
@@ -704,11 +720,9 @@ int enqueue_forces_jerk(nbody_ctx *ctx, const double *pos, const double *vel, co
                                    ctx->max_cluster, j.perm, s, kernels));
         }
         PackParams pp{pos, mass, j.perm, j.dcl, j.tile_cluster, j.tc, ctx->n,
-                      j.px, j.py, j.pz, j.pm, j.chl};
+                      j.px, j.py, j.pz, j.pm, j.chl, vel, j.pvx, j.pvy, j.pvz, j.vchl};
         NB_CUDA(launch_pack(j.n_tiles, pp, s));
-        NB_CUDA(launch_pack_vel(j.n_tiles, vel, j.perm, j.dcl, j.tile_cluster, j.tc, ctx->n, j.pvx,
-                                j.pvy, j.pvz, j.vchl, s));
-        *kernels += 2;
+        *kernels += 1;
         NB_CUDA(cudaMemsetAsync(j.counters, 0, ((size_t)j.n_tiles + 1) * sizeof(int), s));
         const F32CJerkParams fp = jerk_params(ctx, acc, jerk, pot);
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
@@ -754,11 +768,10 @@ int enqueue_hermite_step(nbody_ctx *ctx, const Arrays &a, double dt, bool reorde
 
 void free_block(nbody_ctx *ctx) {
     BlockState &b = ctx->bs;
-    for (double **q : {&b.t, &b.dt, &b.part, &b.partial, &b.p1}) dev_free(q);
+    for (double **q : {&b.t, &b.dt, &b.part, &b.partial, &b.p1, &b.few_part}) dev_free(q);
     dev_free(&b.flag);
     for (int **q : {&b.cnt, &b.chunk_off, &b.act_begin, &b.act_n, &b.ich_off, &b.item_off}) dev_free(q);
     dev_free(&b.act);
-    dev_free(&b.inv);
     dev_free(&b.items);
     dev_free(&b.info);
     dev_free(&b.sc);
@@ -772,24 +785,31 @@ int alloc_block(nbody_ctx *ctx) {
     const size_t n = (size_t)ctx->n, nc = (size_t)std::max(ctx->n_chunks, 1), ncl = (size_t)ctx->ncl;
     if (ctx->mode == NBODY_F32C) {
         // the subset kernel must stream the jerk geometry's j-tiles (same tj);
-        // among those shapes take the smallest i-chunk (less idle lanes when few
-        // particles are active)
-        int bl[16], pp[16], tj[16], mb[16];
-        const int ns = std::min(16, subset_shapes(bl, pp, tj, mb, 16));
-        b.sub = nbody_tiles{0, 0, 0, 0, 0};
-        for (int k = 0; k < ns; ++k)
-            if (tj[k] == ctx->jp.tiles.tj && (b.sub.block == 0 || bl[k] * pp[k] < b.sub.block * b.sub.p))
-                b.sub = nbody_tiles{bl[k], pp[k], tj[k], 0, mb[k]};
+        // the shape table is in order of preference
+        int bl[16], pp[16], tj[16], gr[16], mb[16];
+        const int ns = std::min(16, subset_shapes(bl, pp, tj, gr, mb, 16));
+        b.sub = nbody_tiles{0, 0, 0, 0, 0};  // split holds the group count
+        for (int k = 0; k < ns && b.sub.block == 0; ++k)
+            if (tj[k] == ctx->jp.tiles.tj) b.sub = nbody_tiles{bl[k], pp[k], tj[k], gr[k], mb[k]};
+        // NBODY_SUBSET_SHAPE="block,p,groups" picks another compiled shape
+        if (const char *env = getenv("NBODY_SUBSET_SHAPE")) {
+            int eb = 0, ep = 0, eg = 0;
+            if (sscanf(env, "%d,%d,%d", &eb, &ep, &eg) == 3)
+                for (int k = 0; k < ns; ++k)
+                    if (tj[k] == ctx->jp.tiles.tj && bl[k] == eb && pp[k] == ep && gr[k] == eg)
+                        b.sub = nbody_tiles{bl[k], pp[k], tj[k], gr[k], mb[k]};
+        }
         if (b.sub.block == 0) return fail(ctx, NBODY_EUNSUPPORTED, "no subset kernel for the jerk tiles");
         b.cs = b.sub.block * b.sub.p;
-        const int occ = subset_occupancy(b.sub.block, b.sub.p, b.sub.tj, b.sub.ctas_per_sm, ctx->eps_zero);
+        const int occ = subset_occupancy(b.sub.block, b.sub.p, b.sub.tj, b.sub.split, b.sub.ctas_per_sm,
+                                         ctx->eps_zero);
         if (occ <= 0) return fail(ctx, NBODY_EUNSUPPORTED, "subset kernel not loadable");
         b.workers = occ * ctx->sms;
         b.max_split = 128;
         b.max_chunks = (int)(ctx->n / b.cs) + ctx->ncl + 1;
         b.max_items = std::max(2 * b.workers, b.max_chunks);
         if ((rc = dev_alloc(ctx, &b.partial, (size_t)2 * b.workers * 7 * b.cs))) return rc;
-        if ((rc = dev_alloc(ctx, &b.inv, n))) return rc;
+        if ((rc = dev_alloc(ctx, &b.few_part, (size_t)kFewCtas * kFewMax * 7))) return rc;
     } else {
         b.cs = kF64Block;
         b.workers = 1;
@@ -797,12 +817,16 @@ int alloc_block(nbody_ctx *ctx) {
         b.max_chunks = std::max(ctx->n_blocks64, 1);
         b.max_items = b.max_chunks;
     }
+    // flags per row (FP64) or per j-set slot (F32C); counts per row chunk or per tile
+    const bool f32c = ctx->mode == NBODY_F32C;
+    const size_t nflag = f32c ? (size_t)ctx->jp.n_pad : n;
+    const size_t nunit = f32c ? (size_t)std::max(ctx->jp.n_tiles, 1) : nc;
     for (double **q : {&b.t, &b.dt, &b.p1})
         if ((rc = dev_alloc(ctx, q, n))) return rc;
     if ((rc = dev_alloc(ctx, &b.part, nc))) return rc;
-    if ((rc = dev_alloc(ctx, &b.flag, n))) return rc;
+    if ((rc = dev_alloc(ctx, &b.flag, nflag))) return rc;
     for (int **q : {&b.cnt, &b.chunk_off})
-        if ((rc = dev_alloc(ctx, q, nc))) return rc;
+        if ((rc = dev_alloc(ctx, q, nunit))) return rc;
     for (int **q : {&b.act_begin, &b.act_n, &b.ich_off, &b.item_off})
         if ((rc = dev_alloc(ctx, q, ncl + 1))) return rc;
     if ((rc = dev_alloc(ctx, &b.act, n))) return rc;
@@ -847,6 +871,19 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
     b.items = bs.items;
     b.info = bs.info;
     b.sc = bs.sc;
+    b.mass = a.mass;
+    if (ctx->mode == NBODY_F32C) {
+        b.perm = j.perm;
+        b.tile_cluster = j.tile_cluster;
+        b.tile_first = j.tile_first;
+        b.tc = j.tc;
+        b.n_tiles = j.n_tiles;
+        b.px = j.px; b.py = j.py; b.pz = j.pz; b.pm = j.pm;
+        b.pvx = j.pvx; b.pvy = j.pvy; b.pvz = j.pvz;
+        b.chl = j.chl; b.vchl = j.vchl;
+        b.queue_head = j.counters;
+        b.few_max = kFewMax;
+    }
     return b;
 }
 
@@ -858,23 +895,14 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
     BlockState &bs = ctx->bs;
     JerkPath &j = ctx->jp;
     const BlockLaunch b = block_launch(ctx, a);
-    NB_CUDA(launch_block_prepare(b, s, kernels));
     int rc;
+    if (ctx->mode == NBODY_F32C && reorder)
+        NB_CUDA(launch_reorder(a.pos, ctx->n, ctx->chunks, ctx->n_chunks, ctx->chunk_first, ctx->ncl, j.dcl,
+                               ctx->bpart, ctx->bbox, ctx->keys, ctx->vals, ctx->sort_n, ctx->max_cluster,
+                               j.perm, s, kernels));
+    NB_CUDA(launch_block_prepare(b, s, kernels));
+    NB_CUDA(launch_block_queue(b, s, kernels));
     if (ctx->mode == NBODY_F32C) {
-        if (reorder) {
-            NB_CUDA(launch_reorder(j.xp, ctx->n, ctx->chunks, ctx->n_chunks, ctx->chunk_first, ctx->ncl,
-                                   j.dcl, ctx->bpart, ctx->bbox, ctx->keys, ctx->vals, ctx->sort_n,
-                                   ctx->max_cluster, j.perm, s, kernels));
-        }
-        PackParams pp{j.xp, a.mass, j.perm, j.dcl, j.tile_cluster, j.tc, ctx->n,
-                      j.px, j.py, j.pz, j.pm, j.chl};
-        NB_CUDA(launch_pack(j.n_tiles, pp, s));
-        NB_CUDA(launch_pack_vel(j.n_tiles, j.vp, j.perm, j.dcl, j.tile_cluster, j.tc, ctx->n, j.pvx,
-                                j.pvy, j.pvz, j.vchl, s));
-        NB_CUDA(launch_inverse_perm(j.n_pad, j.perm, bs.inv, s));
-        *kernels += 3;
-        NB_CUDA(launch_block_queue(b, bs.inv, s, kernels));
-        NB_CUDA(cudaMemsetAsync(j.counters, 0, sizeof(int), s));  // queue head
         F32CSubsetParams q{};
         q.base = jerk_params(ctx, j.a1, j.j1, bs.p1);
         q.act_slot = bs.act;
@@ -883,21 +911,20 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
         q.partial = bs.partial;
         q.tcj = j.tc;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
-        NB_CUDA(launch_subset_f32c(bs.sub.block, bs.sub.p, bs.sub.tj, bs.sub.ctas_per_sm,
-                                   ctx->eps_zero, bs.workers, q, s));
+        NB_CUDA(launch_subset_few(q.base, bs.act, bs.sc, bs.few_part, s));
+        NB_CUDA(launch_subset_f32c(bs.sub.block, bs.sub.p, bs.sub.tj, bs.sub.split,
+                                   bs.sub.ctas_per_sm, ctx->eps_zero, bs.workers, q, s));
         NB_CUDA(launch_subset_reduce(bs.max_chunks, 4 * ctx->sms, q, bs.info, bs.sc, bs.cs, s));
-        *kernels += 2;
+        *kernels += 3;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
     } else {
-        NB_CUDA(launch_block_queue(b, nullptr, s, kernels));
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
         NB_CUDA(launch_subset_f64(bs.max_items, j.xp, j.vp, a.mass, ctx->dcl, bs.items,
                                   &bs.sc->n_items, bs.act, ctx->n, ctx->G, j.a1, j.j1, bs.p1, s));
         ++*kernels;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
     }
-    NB_CUDA(launch_block_correct(ctx->n, bs.flag, bs.sc, bs.t, bs.dt, a.pos, a.vel, a.acc, a.jerk,
-                                 a.pot, j.a1, j.j1, bs.p1, bs.dt_max, bs.dt_min, bs.eta, s));
+    NB_CUDA(launch_block_correct(b, j.a1, j.j1, bs.p1, a.pot, bs.dt_max, bs.dt_min, bs.eta, s));
     ++*kernels;
     return NBODY_OK;
 }
@@ -1301,7 +1328,11 @@ int step_common(nbody_ctx *ctx, double *pos, double *vel, const double *mass, do
     uint64_t dt_bits;
     memcpy(&dt_bits, &dt, sizeof dt);
     for (int32_t step = 0; step < nsteps; ++step) {
-        const bool reorder = want_reorder(ctx);
+        bool reorder = want_reorder(ctx);
+        if (kind == 2) {
+            reorder = ctx->bs.reorder_pending;
+            ctx->bs.reorder_pending = false;
+        }
         const int slot = next_slot(ctx);
         if (slot < -1) return ctx->sticky;
         if (!use_graph) {
@@ -1437,6 +1468,8 @@ int nbody_block_start(nbody_ctx *ctx, const double *pos, const double *vel, cons
     ctx->launches += 1;
     NB_CUDA(cudaMemsetAsync(b.sc, 0, sizeof(BlockScalars), s));
     NB_CUDA(cudaStreamSynchronize(s));
+    b.reorder_epoch = 0;
+    b.reorder_pending = false;
     b.started = true;
     return NBODY_OK;
 }
@@ -1463,6 +1496,13 @@ int nbody_block_advance(nbody_ctx *ctx, double *pos, double *vel, const double *
         NB_CUDA(cudaMemcpyAsync(&h, b.sc, sizeof h, cudaMemcpyDeviceToHost, s));
         NB_CUDA(cudaStreamSynchronize(s));
         if (!(h.t_next <= t_end)) break;
+        if (ctx->mode == NBODY_F32C && ctx->reorder_every > 0) {
+            const int64_t epoch = (int64_t)std::floor(h.t_next / (ctx->reorder_every * b.dt_max));
+            if (epoch > b.reorder_epoch) {
+                b.reorder_epoch = epoch;
+                b.reorder_pending = true;
+            }
+        }
     }
     if (blocks) *blocks = h.blocks;
     if (evals) *evals = h.evals;

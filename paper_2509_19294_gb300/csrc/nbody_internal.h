@@ -104,6 +104,11 @@ struct PackParams {
     int64_t n;
     float *px, *py, *pz, *pm;
     float4 *chl;
+    // optional velocity half (jerk path): mean velocity per tile as a float
+    // pair (vchl) and FP32 offsets from it; pads get velocity offset 0
+    const double *vel = nullptr;  // [3][n]
+    float *pvx = nullptr, *pvy = nullptr, *pvz = nullptr;
+    float4 *vchl = nullptr;
 };
 
 // A run of at most kChunk consecutive rows inside one cluster (energy, bbox, keys).
@@ -123,11 +128,21 @@ struct SubItem {
 };
 
 // Device-side scalars of the block-step scheduler.
+// Block steps with at most kFewMax active particles take the few-particle
+// kernel (j-parallel) instead of the i-chunk subset kernel.
+constexpr int kFewMax = 32;
+constexpr int kFewCtas = 64;
+
 struct BlockScalars {
     double t_next;   // time of the current block step
     double t_end;    // stop time (set by the host before each batch)
     int n_active, n_chunks, split, n_items;
     long long blocks, evals;  // block steps taken, single-particle evaluations
+    int ticket_min, ticket_pack, ticket_few;  // last-CTA tickets (each reset by its last CTA)
+    // few-particle path (F32C, n_active <= kFewMax): the clusters holding active
+    // particles, their first active index and the prefix of their sizes
+    int few, few_ncl;
+    int few_cl[kFewMax], few_abeg[kFewMax], few_jbase[kFewMax + 1];
 };
 
 // Subset acceleration + jerk kernel: base carries the j-set (the jerk path's
@@ -149,37 +164,50 @@ struct BlockLaunch {
     const ClusterDev *cl;
     double *t, *dt, *part;
     double *pos, *vel, *acc, *jerk, *xp, *vp;
-    uint8_t *flag;
+    const double *mass;
+    uint8_t *flag;  // per row (FP64) or per j-set slot (F32C)
+    // per row chunk (FP64) or per centre tile (F32C): active counts, offsets
     int *cnt, *chunk_off, *act_begin, *act_n, *ich_off, *item_off;
     int32_t *act;
     SubItem *items;
     SubItem *info;  // per i-chunk: range, cluster, split count, partial base
     BlockScalars *sc;
+    // F32C j-set geometry (px == nullptr on the FP64 path)
+    const int32_t *perm, *tile_cluster, *tile_first;
+    int tc, n_tiles;
+    float *px, *py, *pz, *pm, *pvx, *pvy, *pvz;
+    float4 *chl, *vchl;
+    int *queue_head;
+    int few_max;  // 0 disables the few-particle path
 };
 
 cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, double dt_max,
                               double dt_min, double eta_s, double *t, double *dt, cudaStream_t s);
-// t_next, prediction + flags, counts and the plan (offsets, split, queue size).
+// t_next, prediction (+ the packed j-set for F32C), flags, counts and the plan
+// (offsets, split, queue size, queue head reset).
 cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kernels);
-// Ordered compaction of the active rows (as j-set slots through inv, or rows
-// when inv is null) and the work queue.
-cudaError_t launch_block_queue(const BlockLaunch &b, const int32_t *inv, cudaStream_t s, int *kernels);
-cudaError_t launch_inverse_perm(int64_t n_pad, const int32_t *perm, int32_t *inv, cudaStream_t s);
-int subset_occupancy(int block, int p, int tj, int minb, bool eps_zero);
-int subset_shapes(int *block, int *p, int *tj, int *minb, int cap);
+// Ordered compaction of the active particles (rows, or j-set slots for F32C)
+// and the work queue.
+cudaError_t launch_block_queue(const BlockLaunch &b, cudaStream_t s, int *kernels);
+int subset_occupancy(int block, int p, int tj, int groups, int minb, bool eps_zero);
+int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap);
 // Deterministic parallel sum of the subset kernel's split partials + epilogue.
 cudaError_t launch_subset_reduce(int max_chunks, int max_ctas, const F32CSubsetParams &prm,
                                  const SubItem *info, const BlockScalars *sc, int cs, cudaStream_t s);
-cudaError_t launch_subset_f32c(int block, int p, int tj, int minb, bool eps_zero, int grid,
-                               const F32CSubsetParams &prm, cudaStream_t s);
+// Few-particle path: all j of the active clusters in parallel, FP64 partials per
+// CTA (part: kFewCtas * kFewMax * 7 doubles) summed in order by the last CTA.
+cudaError_t launch_subset_few(const F32CJerkParams &prm, const int32_t *act, BlockScalars *sc,
+                              double *part, cudaStream_t s);
+// block * groups threads per CTA (see SubsetKernel in block.cu).
+cudaError_t launch_subset_f32c(int block, int p, int tj, int groups, int minb, bool eps_zero,
+                               int grid, const F32CSubsetParams &prm, cudaStream_t s);
 cudaError_t launch_subset_f64(int max_items, const double *xp, const double *vp, const double *mass,
                               const ClusterDev *cl, const SubItem *items, const int *n_items,
                               const int32_t *act, int64_t n, double G, double *acc, double *jerk,
                               double *pot, cudaStream_t s);
-cudaError_t launch_block_correct(int64_t n, const uint8_t *flag, const BlockScalars *sc, double *t,
-                                 double *dt, double *pos, double *vel, double *acc, double *jerk,
-                                 double *pot, const double *a1, const double *j1, const double *p1,
-                                 double dt_max, double dt_min, double eta, cudaStream_t s);
+cudaError_t launch_block_correct(const BlockLaunch &b, const double *a1, const double *j1,
+                                 const double *p1, double *pot, double dt_max, double dt_min, double eta,
+                                 cudaStream_t s);
 
 
 // ---- kernel launchers (all enqueue on `s`, return cudaGetLastError()) ----
@@ -201,12 +229,8 @@ int f32c_shapes(int *block, int *p, int *tj, int *minb, int cap);
 cudaError_t launch_f64(int grid, const F64Params &prm, cudaStream_t s);
 constexpr int kF64Block = 128;
 
+// One CTA per centre tile; tc must be a positive multiple of 128.
 cudaError_t launch_pack(int n_tiles, const PackParams &prm, cudaStream_t s);
-// Velocity part of the jerk path's packing: FP64 mean velocity per tile as a
-// float pair (vchl) and FP32 offsets from it (pads get velocity offset 0).
-cudaError_t launch_pack_vel(int n_tiles, const double *vel, const int32_t *perm,
-                            const ClusterDev *cl, const int32_t *tile_cluster, int tc, int64_t n,
-                            float *pvx, float *pvy, float *pvz, float4 *vchl, cudaStream_t s);
 
 // Acceleration + jerk kernel (forces_f32c_jerk.cuh), same conventions as launch_f32c.
 cudaError_t launch_f32c_jerk(int block, int p, int tj, int minb, bool eps_zero, int grid,
