@@ -392,7 +392,8 @@ constexpr int kReduceWarps = 8;
 
 __global__ void __launch_bounds__(32 * kReduceWarps)
 subset_reduce_kernel(const F32CSubsetParams q, const SubItem *__restrict__ info,
-                     const BlockScalars *__restrict__ sc, int cs) {
+                     const BlockScalars *__restrict__ sc) {
+    const int cs = sc->cs;
     __shared__ double part[kReduceWarps][7][32];
     const int subs = (cs + 31) / 32;
     const int units = sc->n_chunks * subs;
@@ -439,12 +440,10 @@ struct SubsetShape {
     SubsetShape{B, P, T, G, M, false, (const void *)subset_jerk_kernel<B, P, T, G, M, false>},   \
         SubsetShape{B, P, T, G, M, true, (const void *)subset_jerk_kernel<B, P, T, G, M, true>}
 
-// In order of preference for each tj (the first one matching the jerk tiles is
-// the default; measured at N = 102400 with individual steps).
-const SubsetShape kSubsetShapes[] = {SUBSET(64, 1, 256, 4, 2),  SUBSET(64, 1, 128, 4, 2),
-                                     SUBSET(64, 2, 256, 4, 1),  SUBSET(128, 2, 256, 2, 1),
-                                     SUBSET(128, 1, 256, 2, 2), SUBSET(32, 2, 256, 8, 1),
-                                     SUBSET(64, 2, 256, 1, 4),  SUBSET(64, 2, 128, 4, 1)};
+// Small active sets: several thread groups per CTA split each j-tile (more
+// warps on few i-chunks); large ones: one group, P = 2 (more reuse per load).
+const SubsetShape kSubsetShapes[] = {SUBSET(64, 1, 256, 4, 2), SUBSET(64, 1, 128, 4, 2),
+                                     SUBSET(64, 2, 256, 1, 4), SUBSET(64, 2, 128, 1, 4)};
 
 const SubsetShape *find_subset(int block, int p, int tj, int groups, int minb, bool eps_zero) {
     for (const SubsetShape &s : kSubsetShapes)
@@ -659,10 +658,14 @@ __device__ void block_exclusive_scan(const int *in, int *out, int n, int *total)
 // queue head reset for the subset kernel.
 __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_units,
                           const int32_t *__restrict__ unit_first, int ncl,
-                          const ClusterDev *__restrict__ cl, int cs, int workers, int max_split,
-                          int *__restrict__ act_begin, int *__restrict__ act_n, int *__restrict__ ich_off,
-                          int *__restrict__ item_off, BlockScalars *sc, int *queue_head, int few_max) {
+                          const ClusterDev *__restrict__ cl, int cs_small, int workers_small,
+                          int max_split, int *__restrict__ act_begin, int *__restrict__ act_n,
+                          int *__restrict__ ich_off, int *__restrict__ item_off, BlockScalars *sc,
+                          int *queue_head, int few_max, int cs_large, int workers_large, int large_min) {
     const bool few = total > 0 && total <= few_max;
+    const bool large = !few && cs_large > 0 && total >= large_min;
+    const int cs = large ? cs_large : cs_small;
+    const int workers = large ? workers_large : workers_small;
     int chunks = 0, nf = 0, jb = 0;
     for (int c = 0; c < ncl; ++c) {
         const int b = unit_first[c], e = unit_first[c + 1];
@@ -698,11 +701,14 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
     sc->n_chunks = chunks;
     sc->split = split;
     sc->n_items = items;
+    sc->cs = cs;
+    sc->n_items_small = large ? 0 : items;
+    sc->n_items_large = large ? items : 0;
     if (total > 0) {
         sc->blocks += 1;
         sc->evals += total;
     }
-    if (queue_head) *queue_head = 0;
+    if (queue_head) queue_head[0] = queue_head[1] = 0;  // small and large subset kernels
 }
 
 // Compaction stage 2 (FP64 path, one CTA): chunk offsets and the plan.
@@ -716,7 +722,7 @@ __global__ void __launch_bounds__(kScan)
     __syncthreads();
     if (threadIdx.x == 0)
         plan_step(chunk_off, total, n_chunks, chunk_first, ncl, cl, cs, workers, max_split, act_begin,
-                  act_n, ich_off, item_off, sc, nullptr, 0);
+                  act_n, ich_off, item_off, sc, nullptr, 0, 0, 0, 0);
 }
 
 // F32C: one CTA per centre tile of the j-set.  Predicts the tile's particles to
@@ -741,6 +747,7 @@ struct BlockPackParams {
     BlockScalars *sc;
     int *queue_head;
     int few_max;
+    int cs_large, workers_large, large_min;
 };
 
 // Hermite predictor in Horner form for the packed j-set (F32C); its rounding
@@ -862,7 +869,8 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
     __syncthreads();
     if (threadIdx.x == 0) {
         plan_step(q.tile_off, total, q.n_tiles, q.tile_first, q.ncl, q.cl, q.cs, q.workers, q.max_split,
-                  q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max);
+                  q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max, q.cs_large,
+                  q.workers_large, q.large_min);
         q.sc->ticket_pack = 0;
     }
 }
@@ -929,13 +937,14 @@ __global__ void block_scatter_kernel(const uint8_t *__restrict__ flag, const Chu
 }
 
 // Work queue (FP64 path).
-__global__ void block_items_kernel(int ncl, const ClusterDev *__restrict__ cl, int cs,
+__global__ void block_items_kernel(int ncl, const ClusterDev *__restrict__ cl,
                                    const int *__restrict__ act_begin, const int *__restrict__ act_n,
                                    const int *__restrict__ ich_off, const int *__restrict__ item_off,
                                    const BlockScalars *__restrict__ sc, int max_items,
                                    SubItem *__restrict__ items, SubItem *__restrict__ info) {
     const int n_items = sc->n_items;
     const int split = sc->split;
+    const int cs = sc->cs;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_items && k < max_items;
          k += gridDim.x * blockDim.x) {
         const SubItem it = make_item(k, ncl, cl, cs, split, act_begin, act_n, ich_off, item_off);
@@ -950,7 +959,7 @@ template <int NT>
 __global__ void __launch_bounds__(NT)
     block_queue_kernel(const uint8_t *__restrict__ flag, int tc, const int *__restrict__ tile_cnt,
                        const int *__restrict__ tile_off, int32_t *__restrict__ act, int ncl,
-                       const ClusterDev *__restrict__ cl, int cs, const int *__restrict__ act_begin,
+                       const ClusterDev *__restrict__ cl, const int *__restrict__ act_begin,
                        const int *__restrict__ act_n, const int *__restrict__ ich_off,
                        const int *__restrict__ item_off, const BlockScalars *__restrict__ sc,
                        int max_items, SubItem *__restrict__ items, SubItem *__restrict__ info) {
@@ -959,6 +968,7 @@ __global__ void __launch_bounds__(NT)
         compact_run<NT>(flag, (int64_t)tile * tc, (int64_t)(tile + 1) * tc, __ldcg(tile_off + tile), act);
     const int n_items = sc->n_items;
     const int split = sc->split;
+    const int cs = sc->cs;
     for (int k = blockIdx.x * NT + threadIdx.x; k < n_items && k < max_items; k += gridDim.x * NT) {
         const SubItem it = make_item(k, ncl, cl, cs, split, act_begin, act_n, ich_off, item_off);
         items[k] = it;
@@ -1046,12 +1056,12 @@ int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap) 
     return n;
 }
 
-cudaError_t launch_subset_reduce(int max_chunks, int max_ctas, const F32CSubsetParams &prm,
-                                 const SubItem *info, const BlockScalars *sc, int cs, cudaStream_t s) {
-    const int64_t units = (int64_t)max_chunks * ((cs + 31) / 32);
+cudaError_t launch_subset_reduce(int max_chunks, int max_cs, int max_ctas, const F32CSubsetParams &prm,
+                                 const SubItem *info, const BlockScalars *sc, cudaStream_t s) {
+    const int64_t units = (int64_t)max_chunks * ((max_cs + 31) / 32);
     if (units <= 0) return cudaSuccess;
     const int grid = (int)std::min<int64_t>(units, max_ctas);
-    subset_reduce_kernel<<<grid, 32 * kReduceWarps, 0, s>>>(prm, info, sc, cs);
+    subset_reduce_kernel<<<grid, 32 * kReduceWarps, 0, s>>>(prm, info, sc);
     return cudaGetLastError();
 }
 
@@ -1094,6 +1104,7 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         q.ncl = b.ncl; q.cs = b.cs; q.workers = b.workers; q.max_split = b.max_split;
         q.act_begin = b.act_begin; q.act_n = b.act_n; q.ich_off = b.ich_off; q.item_off = b.item_off;
         q.sc = b.sc; q.queue_head = b.queue_head; q.few_max = b.few_max;
+        q.cs_large = b.cs_large; q.workers_large = b.workers_large; q.large_min = b.large_min;
         if (b.tc % 256 == 0) NB_BL((block_pack_kernel<256><<<b.n_tiles, 256, 0, s>>>(q)));
         else NB_BL((block_pack_kernel<128><<<b.n_tiles, 128, 0, s>>>(q)));
     } else {
@@ -1112,16 +1123,16 @@ cudaError_t launch_block_queue(const BlockLaunch &b, cudaStream_t s, int *kernel
     if (b.px) {
         if (b.tc % 256 == 0)
             NB_BL((block_queue_kernel<256><<<b.n_tiles, 256, 0, s>>>(
-                b.flag, b.tc, b.cnt, b.chunk_off, b.act, b.ncl, b.cl, b.cs, b.act_begin, b.act_n, b.ich_off,
+                b.flag, b.tc, b.cnt, b.chunk_off, b.act, b.ncl, b.cl, b.act_begin, b.act_n, b.ich_off,
                 b.item_off, b.sc, b.max_items, b.items, b.info)));
         else
             NB_BL((block_queue_kernel<128><<<b.n_tiles, 128, 0, s>>>(
-                b.flag, b.tc, b.cnt, b.chunk_off, b.act, b.ncl, b.cl, b.cs, b.act_begin, b.act_n, b.ich_off,
+                b.flag, b.tc, b.cnt, b.chunk_off, b.act, b.ncl, b.cl, b.act_begin, b.act_n, b.ich_off,
                 b.item_off, b.sc, b.max_items, b.items, b.info)));
     } else {
         NB_BL((block_scatter_kernel<<<b.n_chunks, 256, 0, s>>>(b.flag, b.chunks, b.chunk_off, b.act)));
         NB_BL((block_items_kernel<<<grid_of(b.max_items, 256), 256, 0, s>>>(
-            b.ncl, b.cl, b.cs, b.act_begin, b.act_n, b.ich_off, b.item_off, b.sc, b.max_items, b.items,
+            b.ncl, b.cl, b.act_begin, b.act_n, b.ich_off, b.item_off, b.sc, b.max_items, b.items,
             b.info)));
     }
     return cudaSuccess;

@@ -68,7 +68,10 @@ struct BlockState {
     // multiples of dt_max, at the start of the next 16-step batch
     int64_t reorder_epoch = 0;
     bool reorder_pending = false;
-    nbody_tiles sub{0, 0, 0, 0, 0};  // subset kernel shape (F32C)
+    // subset kernel shapes (F32C; split holds the thread-group count): small
+    // active sets, and large ones from large_min active particles on
+    nbody_tiles sub{0, 0, 0, 0, 0}, sub_large{0, 0, 0, 0, 0};
+    int cs_large = 0, workers_large = 0, large_min = 0;
     double *t = nullptr, *dt = nullptr, *part = nullptr, *partial = nullptr, *p1 = nullptr;
     double *few_part = nullptr;  // few-particle path: kFewCtas * kFewMax * 7
     uint8_t *flag = nullptr;
@@ -784,31 +787,34 @@ int alloc_block(nbody_ctx *ctx) {
     int rc;
     const size_t n = (size_t)ctx->n, nc = (size_t)std::max(ctx->n_chunks, 1), ncl = (size_t)ctx->ncl;
     if (ctx->mode == NBODY_F32C) {
-        // the subset kernel must stream the jerk geometry's j-tiles (same tj);
-        // the shape table is in order of preference
+        // the subset kernels must stream the jerk geometry's j-tiles (same tj):
+        // the small-set shape has several thread groups, the large-set one one
         int bl[16], pp[16], tj[16], gr[16], mb[16];
         const int ns = std::min(16, subset_shapes(bl, pp, tj, gr, mb, 16));
-        b.sub = nbody_tiles{0, 0, 0, 0, 0};  // split holds the group count
-        for (int k = 0; k < ns && b.sub.block == 0; ++k)
-            if (tj[k] == ctx->jp.tiles.tj) b.sub = nbody_tiles{bl[k], pp[k], tj[k], gr[k], mb[k]};
-        // NBODY_SUBSET_SHAPE="block,p,groups" picks another compiled shape
-        if (const char *env = getenv("NBODY_SUBSET_SHAPE")) {
-            int eb = 0, ep = 0, eg = 0;
-            if (sscanf(env, "%d,%d,%d", &eb, &ep, &eg) == 3)
-                for (int k = 0; k < ns; ++k)
-                    if (tj[k] == ctx->jp.tiles.tj && bl[k] == eb && pp[k] == ep && gr[k] == eg)
-                        b.sub = nbody_tiles{bl[k], pp[k], tj[k], gr[k], mb[k]};
+        b.sub = b.sub_large = nbody_tiles{0, 0, 0, 0, 0};
+        for (int k = 0; k < ns; ++k) {
+            if (tj[k] != ctx->jp.tiles.tj) continue;
+            nbody_tiles &dst = gr[k] > 1 ? b.sub : b.sub_large;
+            if (dst.block == 0) dst = nbody_tiles{bl[k], pp[k], tj[k], gr[k], mb[k]};
         }
-        if (b.sub.block == 0) return fail(ctx, NBODY_EUNSUPPORTED, "no subset kernel for the jerk tiles");
+        if (b.sub.block == 0 || b.sub_large.block == 0)
+            return fail(ctx, NBODY_EUNSUPPORTED, "no subset kernel for the jerk tiles");
         b.cs = b.sub.block * b.sub.p;
+        b.cs_large = b.sub_large.block * b.sub_large.p;
         const int occ = subset_occupancy(b.sub.block, b.sub.p, b.sub.tj, b.sub.split, b.sub.ctas_per_sm,
                                          ctx->eps_zero);
-        if (occ <= 0) return fail(ctx, NBODY_EUNSUPPORTED, "subset kernel not loadable");
+        const int occl = subset_occupancy(b.sub_large.block, b.sub_large.p, b.sub_large.tj,
+                                          b.sub_large.split, b.sub_large.ctas_per_sm, ctx->eps_zero);
+        if (occ <= 0 || occl <= 0) return fail(ctx, NBODY_EUNSUPPORTED, "subset kernel not loadable");
         b.workers = occ * ctx->sms;
+        b.workers_large = occl * ctx->sms;
+        b.large_min = 512;  // measured crossover at N = 102400
         b.max_split = 128;
-        b.max_chunks = (int)(ctx->n / b.cs) + ctx->ncl + 1;
-        b.max_items = std::max(2 * b.workers, b.max_chunks);
-        if ((rc = dev_alloc(ctx, &b.partial, (size_t)2 * b.workers * 7 * b.cs))) return rc;
+        const int cs_min = std::min(b.cs, b.cs_large), cs_max = std::max(b.cs, b.cs_large);
+        const int w_max = std::max(b.workers, b.workers_large);
+        b.max_chunks = (int)(ctx->n / cs_min) + ctx->ncl + 1;
+        b.max_items = std::max(2 * w_max, b.max_chunks);
+        if ((rc = dev_alloc(ctx, &b.partial, (size_t)2 * w_max * 7 * cs_max))) return rc;
         if ((rc = dev_alloc(ctx, &b.few_part, (size_t)kFewCtas * kFewMax * 7))) return rc;
     } else {
         b.cs = kF64Block;
@@ -883,6 +889,9 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
         b.chl = j.chl; b.vchl = j.vchl;
         b.queue_head = j.counters;
         b.few_max = kFewMax;
+        b.cs_large = bs.cs_large;
+        b.workers_large = bs.workers_large;
+        b.large_min = bs.large_min;
     }
     return b;
 }
@@ -912,10 +921,16 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
         q.tcj = j.tc;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
         NB_CUDA(launch_subset_few(q.base, bs.act, bs.sc, bs.few_part, s));
+        q.n_items = &bs.sc->n_items_small;
         NB_CUDA(launch_subset_f32c(bs.sub.block, bs.sub.p, bs.sub.tj, bs.sub.split,
                                    bs.sub.ctas_per_sm, ctx->eps_zero, bs.workers, q, s));
-        NB_CUDA(launch_subset_reduce(bs.max_chunks, 4 * ctx->sms, q, bs.info, bs.sc, bs.cs, s));
-        *kernels += 3;
+        q.n_items = &bs.sc->n_items_large;
+        q.base.counters = j.counters + 1;  // its own queue head
+        NB_CUDA(launch_subset_f32c(bs.sub_large.block, bs.sub_large.p, bs.sub_large.tj, bs.sub_large.split,
+                                   bs.sub_large.ctas_per_sm, ctx->eps_zero, bs.workers_large, q, s));
+        NB_CUDA(launch_subset_reduce(bs.max_chunks, std::max(bs.cs, bs.cs_large), 4 * ctx->sms, q, bs.info,
+                                     bs.sc, s));
+        *kernels += 4;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
     } else {
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;

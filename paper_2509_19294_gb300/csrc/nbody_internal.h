@@ -143,6 +143,9 @@ struct BlockScalars {
     // particles, their first active index and the prefix of their sizes
     int few, few_ncl;
     int few_cl[kFewMax], few_abeg[kFewMax], few_jbase[kFewMax + 1];
+    // i-chunk size of this step and the queue size seen by each subset kernel
+    // (the one not chosen reads 0 and returns at once)
+    int cs, n_items_small, n_items_large;
 };
 
 // Subset acceleration + jerk kernel: base carries the j-set (the jerk path's
@@ -177,8 +180,10 @@ struct BlockLaunch {
     int tc, n_tiles;
     float *px, *py, *pz, *pm, *pvx, *pvy, *pvz;
     float4 *chl, *vchl;
-    int *queue_head;
+    int *queue_head;  // [2]: the small- and large-set subset kernels' queue heads
     int few_max;  // 0 disables the few-particle path
+    // second subset kernel for large active sets (cs_large == 0: none)
+    int cs_large, workers_large, large_min;
 };
 
 cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, double dt_max,
@@ -192,8 +197,8 @@ cudaError_t launch_block_queue(const BlockLaunch &b, cudaStream_t s, int *kernel
 int subset_occupancy(int block, int p, int tj, int groups, int minb, bool eps_zero);
 int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap);
 // Deterministic parallel sum of the subset kernel's split partials + epilogue.
-cudaError_t launch_subset_reduce(int max_chunks, int max_ctas, const F32CSubsetParams &prm,
-                                 const SubItem *info, const BlockScalars *sc, int cs, cudaStream_t s);
+cudaError_t launch_subset_reduce(int max_chunks, int max_cs, int max_ctas, const F32CSubsetParams &prm,
+                                 const SubItem *info, const BlockScalars *sc, cudaStream_t s);
 // Few-particle path: all j of the active clusters in parallel, FP64 partials per
 // CTA (part: kFewCtas * kFewMax * 7 doubles) summed in order by the last CTA.
 cudaError_t launch_subset_few(const F32CJerkParams &prm, const int32_t *act, BlockScalars *sc,
