@@ -16,6 +16,7 @@
 // its particles, so the self pair is exactly zero, as in the full kernels.
 #include <algorithm>
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -92,6 +93,9 @@ struct SubsetKernel {
         __shared__ Smem sm;
         const F32CJerkParams &p = q.base;
         const int n_items = *q.n_items;
+        // CTAs beyond the item count would find the queue empty: they leave
+        // without touching its head (the others still drain it)
+        if ((int)blockIdx.x >= n_items) return;
         const int li = threadIdx.x % BLOCK, g = threadIdx.x / BLOCK;
         for (;;) {
             if (threadIdx.x == 0) sm.item = atomicAdd(p.counters, 1);
@@ -514,7 +518,7 @@ constexpr int kScan = 1024;
 
 // Initial steps: the largest power of two <= min(dt_max, eta_s |a| / |j|), >= dt_min.
 __global__ void block_init_kernel(int64_t n, const double *acc, const double *jerk, double dt_max,
-                                  double dt_min, double eta_s, double *t, double *dt) {
+                                  double dt_min, double eta_s, double *t, double *dt, long long *tq) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double an = sqrt(acc[i] * acc[i] + acc[n + i] * acc[n + i] + acc[2 * n + i] * acc[2 * n + i]);
@@ -526,24 +530,28 @@ __global__ void block_init_kernel(int64_t n, const double *acc, const double *je
         if (d < dt_min) d = dt_min;
         t[i] = 0.0;
         dt[i] = d;
+        tq[i] = (long long)(d / dt_min);
     }
 }
 
-// t_next = min_i (t_i + dt_i) (exact): per chunk minima, then the last CTA to
-// finish (ticket) takes the min over them.  No CTA waits for another.
-__global__ void block_min_kernel(const double *__restrict__ t, const double *__restrict__ dt,
-                                 const Chunk *__restrict__ chunks, double *__restrict__ part,
-                                 int n_chunks, BlockScalars *sc) {
-    __shared__ double red[8];
+// t_next = min_i (t_i + dt_i), exact: the times are integers in units of
+// dt_min, so the min is an integer one.  Per-chunk minima, then the last CTA
+// to finish (ticket) takes the min over them.  No CTA waits for another.
+constexpr int kMinThreads = 512;
+
+__global__ void __launch_bounds__(kMinThreads)
+    block_min_kernel(const long long *__restrict__ tq, const Chunk *__restrict__ chunks,
+                     long long *__restrict__ part, int n_chunks, double dt_min, BlockScalars *sc) {
+    __shared__ long long red[kMinThreads / 32];
     __shared__ bool last;
     const Chunk ch = chunks[blockIdx.x];
-    double m = INFINITY;
-    for (int64_t i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) m = fmin(m, t[i] + dt[i]);
-    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    long long m = LLONG_MAX;
+    for (int64_t i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) m = min(m, tq[i]);
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x / 32); ++w) m = fmin(m, red[w]);
+        for (int w = 1; w < kMinThreads / 32; ++w) m = min(m, red[w]);
         part[blockIdx.x] = m;
         __threadfence();
         last = atomicAdd(&sc->ticket_min, 1) == (int)gridDim.x - 1;
@@ -551,15 +559,16 @@ __global__ void block_min_kernel(const double *__restrict__ t, const double *__r
     __syncthreads();
     if (!last) return;
     __threadfence();
-    m = INFINITY;
-    for (int k = threadIdx.x; k < n_chunks; k += blockDim.x) m = fmin(m, __ldcg(part + k));
-    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    m = LLONG_MAX;
+    for (int k = threadIdx.x; k < n_chunks; k += blockDim.x) m = min(m, __ldcg(part + k));
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
     __syncthreads();
     if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x / 32); ++w) m = fmin(m, red[w]);
-        sc->t_next = m;
+        for (int w = 1; w < kMinThreads / 32; ++w) m = min(m, red[w]);
+        sc->t_next_q = m;
+        sc->t_next = (double)m * dt_min;
         sc->ticket_min = 0;
     }
 }
@@ -581,7 +590,7 @@ __device__ __forceinline__ void predict_row(int64_t n, int64_t u, double tn, con
 // Predict every particle to t_next and flag the active ones (FP64 path).
 __global__ void block_predict_kernel(int64_t n, const BlockScalars *__restrict__ sc,
                                      const double *__restrict__ t,
-                                     const double *__restrict__ dt, const double *__restrict__ pos,
+                                     const long long *__restrict__ tq, const double *__restrict__ pos,
                                      const double *__restrict__ vel, const double *__restrict__ acc,
                                      const double *__restrict__ jerk, double *xp, double *vp,
                                      uint8_t *flag) {
@@ -596,7 +605,7 @@ __global__ void block_predict_kernel(int64_t n, const BlockScalars *__restrict__
             xp[d * n + i] = x[d];
             vp[d * n + i] = x[3 + d];
         }
-        flag[i] = live && (t[i] + dt[i] == tn);
+        flag[i] = live && tq[i] == sc->t_next_q;
     }
 }
 
@@ -736,7 +745,8 @@ struct BlockPackParams {
     const int32_t *tile_cluster;
     int tc, n_tiles;
     int64_t n;
-    const double *mass, *t, *dt, *pos, *vel, *acc, *jerk;
+    const double *mass, *t, *pos, *vel, *acc, *jerk;
+    const long long *tq;
     float *px, *py, *pz, *pm, *pvx, *pvy, *pvz;
     float4 *chl, *vchl;
     uint8_t *flag;  // per slot
@@ -783,6 +793,7 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
     __shared__ int total;
     const int tile = blockIdx.x;
     const double tn = q.sc->t_next;
+    const long long tnq = q.sc->t_next_q;
     const bool live = tn <= q.sc->t_end;
     const ClusterDev cl = q.cl[q.tile_cluster[tile]];
     const int base = tile * q.tc;
@@ -800,7 +811,7 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
 #pragma unroll
             for (int d = 0; d < 6; ++d) sf[d] += (float)x[r][d];
             sf[6] += 1.0f;
-            act[r] = live && (q.t[u] + q.dt[u] == tn);
+            act[r] = live && q.tq[u] == tnq;
             sf[7] += act[r] ? 1.0f : 0.0f;
         }
     }
@@ -992,11 +1003,14 @@ __device__ __forceinline__ double recip_pow2(double h) {
 __global__ void block_correct_kernel(int64_t n, const int32_t *__restrict__ act,
                                      const int32_t *__restrict__ perm,
                                      const BlockScalars *__restrict__ sc, double *t, double *dt,
+                                     long long *tq,
                                      double *pos, double *vel, double *acc, double *jerk,
                                      double *pot, const double *__restrict__ a1,
                                      const double *__restrict__ j1, const double *__restrict__ p1,
                                      double dt_max, double dt_min, double eta) {
     const double tn = sc->t_next;
+    const long long tnq = sc->t_next_q;
+    const double inv_dt_min = recip_pow2(dt_min);
     const int n_active = sc->n_active;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_active; k += gridDim.x * blockDim.x) {
         const int64_t i = perm ? perm[act[k]] : act[k];
@@ -1028,6 +1042,7 @@ __global__ void block_correct_kernel(int64_t n, const int32_t *__restrict__ act,
         if (nd == h && da >= 2.0 * h && 2.0 * h <= dt_max && fmod(tn, 2.0 * h) == 0.0) nd = 2.0 * h;
         t[i] = tn;
         dt[i] = nd;
+        tq[i] = tnq + (long long)(nd * inv_dt_min);
     }
 }
 
@@ -1075,9 +1090,10 @@ int subset_occupancy(int block, int p, int tj, int groups, int minb, bool eps_ze
 }
 
 cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, double dt_max,
-                              double dt_min, double eta_s, double *t, double *dt, cudaStream_t s) {
+                              double dt_min, double eta_s, double *t, double *dt, long long *tq,
+                              cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    block_init_kernel<<<grid_of(n, 256), 256, 0, s>>>(n, acc, jerk, dt_max, dt_min, eta_s, t, dt);
+    block_init_kernel<<<grid_of(n, 256), 256, 0, s>>>(n, acc, jerk, dt_max, dt_min, eta_s, t, dt, tq);
     return cudaGetLastError();
 }
 
@@ -1090,13 +1106,14 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         if (e != cudaSuccess) return e; \
         ++*kernels;                     \
     } while (0)
-    NB_BL((block_min_kernel<<<b.n_chunks, 256, 0, s>>>(b.t, b.dt, b.chunks, b.part, b.n_chunks, b.sc)));
+    NB_BL((block_min_kernel<<<b.n_chunks, kMinThreads, 0, s>>>(
+        b.tq, b.chunks, reinterpret_cast<long long *>(b.part), b.n_chunks, b.dt_min, b.sc)));
     if (b.px) {
         if (b.tc <= 0 || b.tc % 128 != 0 || b.tc > kPackMaxPer * (b.tc % 256 == 0 ? 256 : 128))
             return cudaErrorInvalidValue;
         BlockPackParams q{};
         q.perm = b.perm; q.cl = b.cl; q.tile_cluster = b.tile_cluster; q.tc = b.tc;
-        q.n_tiles = b.n_tiles; q.n = b.n; q.mass = b.mass; q.t = b.t; q.dt = b.dt;
+        q.n_tiles = b.n_tiles; q.n = b.n; q.mass = b.mass; q.t = b.t; q.tq = b.tq;
         q.pos = b.pos; q.vel = b.vel; q.acc = b.acc; q.jerk = b.jerk;
         q.px = b.px; q.py = b.py; q.pz = b.pz; q.pm = b.pm;
         q.pvx = b.pvx; q.pvy = b.pvy; q.pvz = b.pvz; q.chl = b.chl; q.vchl = b.vchl;
@@ -1109,7 +1126,7 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         else NB_BL((block_pack_kernel<128><<<b.n_tiles, 128, 0, s>>>(q)));
     } else {
         NB_BL((block_predict_kernel<<<grid_of(b.n, 256), 256, 0, s>>>(
-            b.n, b.sc, b.t, b.dt, b.pos, b.vel, b.acc, b.jerk, b.xp, b.vp, b.flag)));
+            b.n, b.sc, b.t, b.tq, b.pos, b.vel, b.acc, b.jerk, b.xp, b.vp, b.flag)));
         NB_BL((block_count_kernel<<<b.n_chunks, 256, 0, s>>>(b.flag, b.chunks, b.cnt)));
         NB_BL((block_plan_kernel<<<1, kScan, 0, s>>>(b.cnt, b.n_chunks, b.chunk_first, b.ncl, b.cl, b.cs,
                                                       b.workers, b.max_split, b.chunk_off, b.act_begin,
@@ -1169,7 +1186,7 @@ cudaError_t launch_block_correct(const BlockLaunch &b, const double *a1, const d
                                  cudaStream_t s) {
     if (b.n <= 0) return cudaSuccess;
     block_correct_kernel<<<grid_of(b.n, 256), 256, 0, s>>>(b.n, b.act, b.px ? b.perm : nullptr, b.sc, b.t,
-                                                           b.dt, b.pos, b.vel, b.acc, b.jerk, pot, a1, j1,
+                                                           b.dt, b.tq, b.pos, b.vel, b.acc, b.jerk, pot, a1, j1,
                                                            p1, dt_max, dt_min, eta);
     return cudaGetLastError();
 }

@@ -74,6 +74,7 @@ struct BlockState {
     int cs_large = 0, workers_large = 0, large_min = 0;
     double *t = nullptr, *dt = nullptr, *part = nullptr, *partial = nullptr, *p1 = nullptr;
     double *few_part = nullptr;  // few-particle path: kFewCtas * kFewMax * 7
+    long long *tq = nullptr;     // t_i + dt_i in units of dt_min
     uint8_t *flag = nullptr;
     int *cnt = nullptr, *chunk_off = nullptr, *act_begin = nullptr, *act_n = nullptr;
     int *ich_off = nullptr, *item_off = nullptr;
@@ -772,6 +773,7 @@ int enqueue_hermite_step(nbody_ctx *ctx, const Arrays &a, double dt, bool reorde
 void free_block(nbody_ctx *ctx) {
     BlockState &b = ctx->bs;
     for (double **q : {&b.t, &b.dt, &b.part, &b.partial, &b.p1, &b.few_part}) dev_free(q);
+    dev_free(&b.tq);
     dev_free(&b.flag);
     for (int **q : {&b.cnt, &b.chunk_off, &b.act_begin, &b.act_n, &b.ich_off, &b.item_off}) dev_free(q);
     dev_free(&b.act);
@@ -829,6 +831,7 @@ int alloc_block(nbody_ctx *ctx) {
     const size_t nunit = f32c ? (size_t)std::max(ctx->jp.n_tiles, 1) : nc;
     for (double **q : {&b.t, &b.dt, &b.p1})
         if ((rc = dev_alloc(ctx, q, n))) return rc;
+    if ((rc = dev_alloc(ctx, &b.tq, n))) return rc;
     if ((rc = dev_alloc(ctx, &b.part, nc))) return rc;
     if ((rc = dev_alloc(ctx, &b.flag, nflag))) return rc;
     for (int **q : {&b.cnt, &b.chunk_off})
@@ -859,6 +862,8 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
     b.cl = ctx->mode == NBODY_F32C ? j.dcl : ctx->dcl;
     b.t = bs.t;
     b.dt = bs.dt;
+    b.tq = bs.tq;
+    b.dt_min = bs.dt_min;
     b.part = bs.part;
     b.pos = a.pos;
     b.vel = a.vel;
@@ -1479,7 +1484,7 @@ int nbody_block_start(nbody_ctx *ctx, const double *pos, const double *vel, cons
     b.dt_max = dt_max;
     b.dt_min = dt_min;
     b.eta = eta;
-    NB_CUDA(launch_block_init(ctx->n, acc, jerk, dt_max, dt_min, eta_s, b.t, b.dt, s));
+    NB_CUDA(launch_block_init(ctx->n, acc, jerk, dt_max, dt_min, eta_s, b.t, b.dt, b.tq, s));
     ctx->launches += 1;
     NB_CUDA(cudaMemsetAsync(b.sc, 0, sizeof(BlockScalars), s));
     NB_CUDA(cudaStreamSynchronize(s));

@@ -135,6 +135,7 @@ constexpr int kFewCtas = 64;
 
 struct BlockScalars {
     double t_next;   // time of the current block step
+    long long t_next_q;  // the same in units of dt_min
     double t_end;    // stop time (set by the host before each batch)
     int n_active, n_chunks, split, n_items;
     long long blocks, evals;  // block steps taken, single-particle evaluations
@@ -166,6 +167,8 @@ struct BlockLaunch {
     const int32_t *chunk_first;
     const ClusterDev *cl;
     double *t, *dt, *part;
+    long long *tq;  // t_i + dt_i in units of dt_min (exact: steps are powers of two >= dt_min)
+    double dt_min;
     double *pos, *vel, *acc, *jerk, *xp, *vp;
     const double *mass;
     uint8_t *flag;  // per row (FP64) or per j-set slot (F32C)
@@ -187,7 +190,8 @@ struct BlockLaunch {
 };
 
 cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, double dt_max,
-                              double dt_min, double eta_s, double *t, double *dt, cudaStream_t s);
+                              double dt_min, double eta_s, double *t, double *dt, long long *tq,
+                              cudaStream_t s);
 // t_next, prediction (+ the packed j-set for F32C), flags, counts and the plan
 // (offsets, split, queue size, queue head reset).
 cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kernels);
