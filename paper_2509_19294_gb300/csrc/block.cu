@@ -670,7 +670,8 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
                           const ClusterDev *__restrict__ cl, int cs_small, int workers_small,
                           int max_split, int *__restrict__ act_begin, int *__restrict__ act_n,
                           int *__restrict__ ich_off, int *__restrict__ item_off, BlockScalars *sc,
-                          int *queue_head, int few_max, int cs_large, int workers_large, int large_min) {
+                          int *queue_head, int few_max, int cs_large, int workers_large, int large_min,
+                          long long partial_cap) {
     const bool few = total > 0 && total <= few_max;
     const bool large = !few && cs_large > 0 && total >= large_min;
     const int cs = large ? cs_large : cs_small;
@@ -699,6 +700,24 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
     int split = chunks > 0 ? (2 * workers) / chunks : 1;
     if (split > max_split) split = max_split;
     if (split < 1) split = 1;
+    // equal-cost items drain in ceil(items / workers) rounds: among the next few
+    // split counts that fit the partial buffer, take the one whose last round
+    // is fullest (the smaller on ties)
+    if (chunks > 0) {
+        const long long max_slots = partial_cap / (7LL * cs);
+        double best = -1.0;
+        int pick = split;
+        for (int sp = split; sp <= split + 3 && sp <= max_split; ++sp) {
+            if (sp > 1 && (long long)chunks * sp > max_slots) break;
+            const double r = (double)chunks * sp / workers;
+            const double eff = r / ceil(r);
+            if (eff > best + 1e-9) {
+                best = eff;
+                pick = sp;
+            }
+        }
+        split = pick;
+    }
     int items = 0;
     for (int c = 0; c < ncl; ++c) {
         item_off[c] = items;
@@ -731,7 +750,7 @@ __global__ void __launch_bounds__(kScan)
     __syncthreads();
     if (threadIdx.x == 0)
         plan_step(chunk_off, total, n_chunks, chunk_first, ncl, cl, cs, workers, max_split, act_begin,
-                  act_n, ich_off, item_off, sc, nullptr, 0, 0, 0, 0);
+                  act_n, ich_off, item_off, sc, nullptr, 0, 0, 0, 0, 0);
 }
 
 // F32C: one CTA per centre tile of the j-set.  Predicts the tile's particles to
@@ -758,6 +777,7 @@ struct BlockPackParams {
     int *queue_head;
     int few_max;
     int cs_large, workers_large, large_min;
+    long long partial_cap;  // doubles in the split-partial buffer
 };
 
 // Hermite predictor in Horner form for the packed j-set (F32C); its rounding
@@ -881,7 +901,7 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
     if (threadIdx.x == 0) {
         plan_step(q.tile_off, total, q.n_tiles, q.tile_first, q.ncl, q.cl, q.cs, q.workers, q.max_split,
                   q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max, q.cs_large,
-                  q.workers_large, q.large_min);
+                  q.workers_large, q.large_min, q.partial_cap);
         q.sc->ticket_pack = 0;
     }
 }
@@ -1122,6 +1142,7 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         q.act_begin = b.act_begin; q.act_n = b.act_n; q.ich_off = b.ich_off; q.item_off = b.item_off;
         q.sc = b.sc; q.queue_head = b.queue_head; q.few_max = b.few_max;
         q.cs_large = b.cs_large; q.workers_large = b.workers_large; q.large_min = b.large_min;
+        q.partial_cap = b.partial_cap;
         if (b.tc % 256 == 0) NB_BL((block_pack_kernel<256><<<b.n_tiles, 256, 0, s>>>(q)));
         else NB_BL((block_pack_kernel<128><<<b.n_tiles, 128, 0, s>>>(q)));
     } else {

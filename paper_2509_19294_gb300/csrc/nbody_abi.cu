@@ -72,6 +72,7 @@ struct BlockState {
     // active sets, and large ones from large_min active particles on
     nbody_tiles sub{0, 0, 0, 0, 0}, sub_large{0, 0, 0, 0, 0};
     int cs_large = 0, workers_large = 0, large_min = 0;
+    long long partial_cap = 0;
     double *t = nullptr, *dt = nullptr, *part = nullptr, *partial = nullptr, *p1 = nullptr;
     double *few_part = nullptr;  // few-particle path: kFewCtas * kFewMax * 7
     long long *tq = nullptr;     // t_i + dt_i in units of dt_min
@@ -815,8 +816,16 @@ int alloc_block(nbody_ctx *ctx) {
         const int cs_min = std::min(b.cs, b.cs_large), cs_max = std::max(b.cs, b.cs_large);
         const int w_max = std::max(b.workers, b.workers_large);
         b.max_chunks = (int)(ctx->n / cs_min) + ctx->ncl + 1;
-        b.max_items = std::max(2 * w_max, b.max_chunks);
-        if ((rc = dev_alloc(ctx, &b.partial, (size_t)2 * w_max * 7 * cs_max))) return rc;
+        // the plan's split count: chunks * split <= 2 * workers, plus up to 3
+        // more splits per chunk to even out the last round
+        b.max_items = 2 * w_max + 4 * b.max_chunks;
+        // room for 2 partial slots per worker, or up to 4 per large-set i-chunk
+        // (the plan may split every chunk to even out the last round), at most
+        // 256 MiB beyond the former
+        const long long base_cap = 2LL * w_max * 7 * cs_max;
+        const long long big_cap = 4LL * ((long long)(ctx->n / b.cs_large) + ctx->ncl + 1) * 7 * b.cs_large;
+        b.partial_cap = std::max(base_cap, std::min(big_cap, base_cap + (256LL << 20) / 8));
+        if ((rc = dev_alloc(ctx, &b.partial, (size_t)b.partial_cap))) return rc;
         if ((rc = dev_alloc(ctx, &b.few_part, (size_t)kFewCtas * kFewMax * 7))) return rc;
     } else {
         b.cs = kF64Block;
@@ -897,6 +906,7 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
         b.cs_large = bs.cs_large;
         b.workers_large = bs.workers_large;
         b.large_min = bs.large_min;
+        b.partial_cap = bs.partial_cap;
     }
     return b;
 }

@@ -187,6 +187,7 @@ struct BlockLaunch {
     int few_max;  // 0 disables the few-particle path
     // second subset kernel for large active sets (cs_large == 0: none)
     int cs_large, workers_large, large_min;
+    long long partial_cap;  // doubles in the subset kernels' split-partial buffer
 };
 
 cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, double dt_max,
