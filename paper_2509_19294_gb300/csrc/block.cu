@@ -28,13 +28,70 @@ namespace nbody {
 
 namespace {
 
+// 1/h, exact for a power of two h (built from its exponent; FP64 division is
+// slow on this part), else the division.
+__device__ __forceinline__ double recip_pow2(double h) {
+    const long long b = __double_as_longlong(h);
+    if ((b & 0x000FFFFFFFFFFFFFLL) == 0 && b > 0 && b < 0x7FE0000000000000LL)
+        return __longlong_as_double(0x7FE0000000000000LL - b);
+    return 1.0 / h;
+}
+
+// Hermite corrector of active particle (row) i over its step h = dt_i with the
+// new acceleration A1, jerk J1 and potential p1, then its next step by
+// Aarseth's criterion.  Steps are powers of two >= dt_min and t_next is a
+// multiple of dt_min, so dividing by h, h^2, h^3 is the exact multiplication
+// by their reciprocals and "t_next is a multiple of 2h" is an integer test;
+// both give the oracle's results bit for bit.
+__device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t i, const double (&A1)[3],
+                                                 const double (&J1)[3], double p1, double tn,
+                                                 long long tnq) {
+    const double h = c.dt[i], h2 = h * h;
+    const double ih = recip_pow2(h), ih2 = ih * ih, ih3 = ih2 * ih;
+    double A2[3], A3[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int64_t q = d * c.n + i;
+        const double a0 = c.acc[q], j0 = c.jerk[q], v0 = c.vel[q];
+        const double v1 = v0 + (a0 + A1[d]) * h / 2.0 + (j0 - J1[d]) * h2 / 12.0;
+        c.pos[q] = c.pos[q] + (v0 + v1) * h / 2.0 + (a0 - A1[d]) * h2 / 12.0;
+        c.vel[q] = v1;
+        A3[d] = (12.0 * (a0 - A1[d]) + 6.0 * h * (j0 + J1[d])) * ih3;
+        A2[d] = (-6.0 * (a0 - A1[d]) - h * (4.0 * j0 + 2.0 * J1[d])) * ih2 + h * A3[d];
+        c.acc[q] = A1[d];
+        c.jerk[q] = J1[d];
+    }
+    if (c.pot) c.pot[i] = p1;
+    const double na = sqrt(A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2]);
+    const double nj = sqrt(J1[0] * J1[0] + J1[1] * J1[1] + J1[2] * J1[2]);
+    const double n2 = sqrt(A2[0] * A2[0] + A2[1] * A2[1] + A2[2] * A2[2]);
+    const double n3 = sqrt(A3[0] * A3[0] + A3[1] * A3[1] + A3[2] * A3[2]);
+    const double den = nj * n3 + n2 * n2;
+    const double da = den > 0.0 ? sqrt(c.eta * (na * n2 + nj * nj) / den) : c.dt_max;
+    const double inv_dt_min = recip_pow2(c.dt_min);
+    double nd = h;
+    while (nd > da && nd > c.dt_min) nd *= 0.5;
+    const long long q2 = (long long)(2.0 * h * inv_dt_min);  // 2h in units of dt_min
+    if (nd == h && da >= 2.0 * h && 2.0 * h <= c.dt_max && tnq % q2 == 0) nd = 2.0 * h;
+    c.t[i] = tn;
+    c.dt[i] = nd;
+    c.tq[i] = tnq + (long long)(nd * inv_dt_min);
+}
+
 // FP64 epilogue of one active particle: scale by G, remove the self term of
-// phi (its own j-tile contributed m_i rsqrt(eps^2) exactly), scatter to its row.
-__device__ __forceinline__ void subset_finalize(const F32CJerkParams &p, const ClusterDev &cl,
-                                                int slot, const double (&r)[7]) {
+// phi (its own j-tile contributed m_i rsqrt(eps^2) exactly), then correct the
+// particle (corr.sc set) or store a1, j1, p1 at its row.
+__device__ __forceinline__ void subset_finalize(const F32CJerkParams &p, const BlockCorrect &corr,
+                                                const ClusterDev &cl, int slot, const double (&r)[7]) {
     const int64_t u = p.perm[slot];
     double ph = r[6];
     if (cl.eps2f > 0.0f) ph -= (double)__fmul_rn(p.pm[slot], rsqrt_mufu(cl.eps2f));
+    if (corr.sc) {
+        const double A1[3] = {p.G * r[0], p.G * r[1], p.G * r[2]};
+        const double J1[3] = {p.G * r[3], p.G * r[4], p.G * r[5]};
+        correct_particle(corr, u, A1, J1, -p.G * ph, corr.sc->t_next, corr.sc->t_next_q);
+        return;
+    }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         p.acc[d * p.n + u] = p.G * r[d];
@@ -216,7 +273,7 @@ struct SubsetKernel {
             if (it.nsplit <= 1) {
 #pragma unroll
                 for (int k = 0; k < P; ++k)
-                    if (valid[k]) subset_finalize(p, cl, slot[k], res[k]);
+                    if (valid[k]) subset_finalize(p, q.corr, cl, slot[k], res[k]);
                 continue;
             }
             double *mine = q.partial + (size_t)(it.pbase + it.split) * NC * CS;
@@ -244,25 +301,35 @@ __global__ void __launch_bounds__(BLOCK * G, MINB) subset_jerk_kernel(const F32C
 // a fixed order by the last CTA (ticket), which also applies the epilogue.
 constexpr int kFewThreads = 256;
 constexpr int kFewBatch = 8;
+constexpr int kFewUnroll = 2;
 
 __global__ void __launch_bounds__(kFewThreads)
-    subset_few_kernel(const F32CJerkParams p, const int32_t *__restrict__ act, BlockScalars *sc,
+    subset_few_kernel(const F32CSubsetParams q, const int32_t *__restrict__ act, BlockScalars *sc,
                       double *__restrict__ part) {
+    const F32CJerkParams &p = q.base;
     __shared__ float own[kFewMax][6];
     __shared__ float4 oc[kFewMax][4];
     __shared__ int ocl[kFewMax];
     __shared__ float wsum[kFewThreads / 32][kFewBatch][7];
     __shared__ double csum[kFewMax][7];
-    __shared__ double fsum[kFewThreads / 32][kFewMax * 7];
-    __shared__ int fjb[kFewMax + 1], fcl[kFewMax];
+    __shared__ double fsum[kFewThreads];  // [group][output], ngrp * n_out <= kFewThreads
+    __shared__ int fjb[kFewMax + 1], fcl[kFewMax], fab[kFewMax], fsb[kFewMax];
+    __shared__ float fe2[kFewMax];
     __shared__ bool last;
     if (!sc->few) return;  // uniform: the plan chose the subset kernel
     const int na = sc->n_active;
     const int nf = sc->few_ncl;
     for (int e = threadIdx.x; e <= nf; e += blockDim.x) {
         fjb[e] = sc->few_jbase[e];
-        if (e < nf) fcl[e] = sc->few_cl[e];
+        if (e < nf) {
+            const int c = sc->few_cl[e];
+            fcl[e] = c;
+            fab[e] = sc->few_abeg[e];
+            fsb[e] = p.cl[c].slot_begin;
+            fe2[e] = p.cl[c].eps2f;
+        }
     }
+    __syncthreads();
     for (int a = threadIdx.x; a < na; a += blockDim.x) {
         const int slot = act[a];
         own[a][0] = p.px[slot];
@@ -277,65 +344,97 @@ __global__ void __launch_bounds__(kFewThreads)
         oc[a][2] = p.vchl[2 * tile];
         oc[a][3] = p.vchl[2 * tile + 1];
         int e = 0;
-        while (e + 1 < nf && sc->few_abeg[e + 1] <= a) ++e;
-        ocl[a] = sc->few_cl[e];
+        while (e + 1 < nf && fab[e + 1] <= a) ++e;
+        ocl[a] = e;  // index into the few-cluster list
     }
     __syncthreads();
     const int jtot = fjb[nf];
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    const int stride = gridDim.x * kFewThreads;
     for (int b0 = 0; b0 < na; b0 += kFewBatch) {
         float acc[kFewBatch][7];
 #pragma unroll
         for (int k = 0; k < kFewBatch; ++k)
 #pragma unroll
             for (int c = 0; c < 7; ++c) acc[k][c] = 0.0f;
-        for (int g = blockIdx.x * kFewThreads + threadIdx.x; g < jtot; g += gridDim.x * kFewThreads) {
-            int e = 0;
-            while (e + 1 < nf && fjb[e + 1] <= g) ++e;
-            const int c = fcl[e];
-            const ClusterDev d = p.cl[c];
-            const int js = d.slot_begin + (g - fjb[e]);
-            const float J[7] = {p.px[js], p.py[js], p.pz[js], p.pm[js], p.pvx[js], p.pvy[js], p.pvz[js]};
-            const int jt = js / p.tc;
-            const float4 jc0 = p.chl[2 * jt], jc1 = p.chl[2 * jt + 1];
-            const float4 jv0 = p.vchl[2 * jt], jv1 = p.vchl[2 * jt + 1];
-            const float jh[6] = {jc0.x, jc0.y, jc0.z, jv0.x, jv0.y, jv0.z};
-            const float jl[6] = {jc1.x, jc1.y, jc1.z, jv1.x, jv1.y, jv1.z};
+        for (int g0 = blockIdx.x * kFewThreads + threadIdx.x; g0 < jtot; g0 += kFewUnroll * stride) {
+            // the loads of kFewUnroll j-particles first, so their latencies overlap
+            float J[kFewUnroll][7];
+            float4 jcen[kFewUnroll][4];
+            int ej[kFewUnroll];
 #pragma unroll
-            for (int k = 0; k < kFewBatch; ++k) {
-                const int a = b0 + k;
-                if (a >= na || ocl[a] != c) continue;
-                const float ih[6] = {oc[a][0].x, oc[a][0].y, oc[a][0].z, oc[a][2].x, oc[a][2].y, oc[a][2].z};
-                const float il[6] = {oc[a][1].x, oc[a][1].y, oc[a][1].z, oc[a][3].x, oc[a][3].y, oc[a][3].z};
-                float r[6];
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    float hi, lo;
-                    centre_diff(ih[q], il[q], jh[q], jl[q], hi, lo);
-                    r[q] = __fsub_rn(J[q < 3 ? q : q + 1], __fadd_rn(__fadd_rn(own[a][q], hi), lo));
+            for (int u = 0; u < kFewUnroll; ++u) {
+                const int g = g0 + u * stride;
+                ej[u] = -1;
+                if (g < jtot) {
+                    int e = 0;
+                    while (e + 1 < nf && fjb[e + 1] <= g) ++e;
+                    ej[u] = e;
+                    const int js = fsb[e] + (g - fjb[e]);
+                    J[u][0] = p.px[js];
+                    J[u][1] = p.py[js];
+                    J[u][2] = p.pz[js];
+                    J[u][3] = p.pm[js];
+                    J[u][4] = p.pvx[js];
+                    J[u][5] = p.pvy[js];
+                    J[u][6] = p.pvz[js];
+                    const int jt = js / p.tc;
+                    jcen[u][0] = p.chl[2 * jt];
+                    jcen[u][1] = p.chl[2 * jt + 1];
+                    jcen[u][2] = p.vchl[2 * jt];
+                    jcen[u][3] = p.vchl[2 * jt + 1];
                 }
-                float r2 = __fmaf_rn(r[0], r[0], d.eps2f);
-                r2 = __fmaf_rn(r[1], r[1], r2);
-                r2 = __fmaf_rn(r[2], r[2], r2);
-                float rv = __fmul_rn(r[0], r[3]);
-                rv = __fmaf_rn(r[1], r[4], rv);
-                rv = __fmaf_rn(r[2], r[5], rv);
-                const float s = r2 > 0.0f ? rsqrt_mufu(r2) : 0.0f;
-                const float ms = __fmul_rn(J[3], s), s2 = __fmul_rn(s, s);
-                const float w3 = __fmul_rn(ms, s2);
-                const float beta = __fmul_rn(rv, __fmul_rn(s2, -3.0f));
-                acc[k][6] = __fadd_rn(acc[k][6], ms);
+            }
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    acc[k][q] = __fmaf_rn(w3, r[q], acc[k][q]);
-                    acc[k][3 + q] = __fmaf_rn(w3, __fmaf_rn(beta, r[q], r[3 + q]), acc[k][3 + q]);
+            for (int u = 0; u < kFewUnroll; ++u) {
+                if (ej[u] < 0) continue;
+                const int c = ej[u];
+                const float e2 = fe2[c];
+                const float jh[6] = {jcen[u][0].x, jcen[u][0].y, jcen[u][0].z,
+                                     jcen[u][2].x, jcen[u][2].y, jcen[u][2].z};
+                const float jl[6] = {jcen[u][1].x, jcen[u][1].y, jcen[u][1].z,
+                                     jcen[u][3].x, jcen[u][3].y, jcen[u][3].z};
+#pragma unroll
+                for (int k = 0; k < kFewBatch; ++k) {
+                    const int a = b0 + k;
+                    if (a >= na || ocl[a] != c) continue;
+                    const float ih[6] = {oc[a][0].x, oc[a][0].y, oc[a][0].z,
+                                         oc[a][2].x, oc[a][2].y, oc[a][2].z};
+                    const float il[6] = {oc[a][1].x, oc[a][1].y, oc[a][1].z,
+                                         oc[a][3].x, oc[a][3].y, oc[a][3].z};
+                    float r[6];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        float hi, lo;
+                        centre_diff(ih[q], il[q], jh[q], jl[q], hi, lo);
+                        r[q] = __fsub_rn(J[u][q < 3 ? q : q + 1],
+                                         __fadd_rn(__fadd_rn(own[a][q], hi), lo));
+                    }
+                    float r2 = __fmaf_rn(r[0], r[0], e2);
+                    r2 = __fmaf_rn(r[1], r[1], r2);
+                    r2 = __fmaf_rn(r[2], r[2], r2);
+                    float rv = __fmul_rn(r[0], r[3]);
+                    rv = __fmaf_rn(r[1], r[4], rv);
+                    rv = __fmaf_rn(r[2], r[5], rv);
+                    const float s = r2 > 0.0f ? rsqrt_mufu(r2) : 0.0f;
+                    const float ms = __fmul_rn(J[u][3], s), s2 = __fmul_rn(s, s);
+                    const float w3 = __fmul_rn(ms, s2);
+                    const float beta = __fmul_rn(rv, __fmul_rn(s2, -3.0f));
+                    acc[k][6] = __fadd_rn(acc[k][6], ms);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        acc[k][q] = __fmaf_rn(w3, r[q], acc[k][q]);
+                        acc[k][3 + q] =
+                            __fmaf_rn(w3, __fmaf_rn(beta, r[q], r[3 + q]), acc[k][3 + q]);
+                    }
                 }
             }
         }
         // warp trees in FP32 (no less accurate than the subset kernel's FP32
         // tile sums), then FP64: the warps in order
 #pragma unroll
-        for (int k = 0; k < kFewBatch; ++k)
+        for (int k = 0; k < kFewBatch; ++k) {
+            if (b0 + k >= na) break;  // uniform
 #pragma unroll
             for (int c = 0; c < 7; ++c) {
                 float v = acc[k][c];
@@ -343,6 +442,7 @@ __global__ void __launch_bounds__(kFewThreads)
                 for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
                 if (lane == 0) wsum[warp][k][c] = v;
             }
+        }
         __syncthreads();
         if (threadIdx.x < kFewBatch * 7) {
             const int k = threadIdx.x / 7, c = threadIdx.x % 7;
@@ -360,29 +460,40 @@ __global__ void __launch_bounds__(kFewThreads)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // CTA partials in order: warp w adds CTAs [w G/8, (w+1) G/8), then the
-    // warps' sums in warp order
+    // CTA partials: output o (of na * 7) is split over ngrp thread groups, each
+    // adding a fixed contiguous range of CTAs (loads issued together), then the
+    // group sums are added in group order
     {
-        const int nw = kFewThreads / 32;
-        const int b0 = (int)(warp * gridDim.x / nw), b1 = (int)((warp + 1) * gridDim.x / nw);
-        for (int t = lane; t < na * 7; t += 32) {
+        const int n_out = na * 7;
+        const int ngrp = min(kFewThreads / n_out, (int)gridDim.x);
+        const int o = threadIdx.x % n_out, grp = threadIdx.x / n_out;
+        if (grp < ngrp) {
+            const int b0 = (int)((long long)grp * gridDim.x / ngrp);
+            const int b1 = (int)((long long)(grp + 1) * gridDim.x / ngrp);
             double v = 0.0;
-            for (int b = b0; b < b1; ++b) v += __ldcg(part + (size_t)b * kFewMax * 7 + t);
-            fsum[warp][t] = v;
+            for (int b = b0; b < b1; b += 8) {
+                double x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    x[u] = b + u < b1 ? __ldcg(part + (size_t)(b + u) * kFewMax * 7 + o) : 0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v += x[u];
+            }
+            fsum[grp * n_out + o] = v;
         }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < na * 7; t += blockDim.x) {
-        double v = fsum[0][t];
-        for (int w = 1; w < kFewThreads / 32; ++w) v += fsum[w][t];
-        csum[t / 7][t % 7] = v;
+        __syncthreads();
+        if (threadIdx.x < n_out) {
+            double v = fsum[threadIdx.x];
+            for (int g2 = 1; g2 < ngrp; ++g2) v += fsum[g2 * n_out + threadIdx.x];
+            csum[threadIdx.x / 7][threadIdx.x % 7] = v;
+        }
     }
     __syncthreads();
     for (int a = threadIdx.x; a < na; a += blockDim.x) {
         double r[7];
 #pragma unroll
         for (int c = 0; c < 7; ++c) r[c] = csum[a][c];
-        subset_finalize(p, p.cl[ocl[a]], act[a], r);
+        subset_finalize(p, q.corr, p.cl[fcl[ocl[a]]], act[a], r);
     }
     if (threadIdx.x == 0) sc->ticket_few = 0;
 }
@@ -428,7 +539,7 @@ subset_reduce_kernel(const F32CSubsetParams q, const SubItem *__restrict__ info,
 #pragma unroll
                 for (int h = 1; h < kReduceWarps; ++h) r[c] += part[h][c][lane];
             }
-            subset_finalize(q.base, q.base.cl[it.cluster], q.act_slot[it.a0 + l], r);
+            subset_finalize(q.base, q.corr, q.base.cl[it.cluster], q.act_slot[it.a0 + l], r);
         }
         __syncthreads();
     }
@@ -1007,62 +1118,22 @@ __global__ void __launch_bounds__(NT)
     }
 }
 
-// 1/h, exact for a power of two h (built from its exponent; FP64 division is
-// slow on this part), else the division.
-__device__ __forceinline__ double recip_pow2(double h) {
-    const long long b = __double_as_longlong(h);
-    if ((b & 0x000FFFFFFFFFFFFFLL) == 0 && b > 0 && b < 0x7FE0000000000000LL)
-        return __longlong_as_double(0x7FE0000000000000LL - b);
-    return 1.0 / h;
-}
-
-// Correct the active particles over their own steps and choose the next step.
-// Work runs over the active list; row = perm[act[k]] (F32C, act holds j-set
-// slots) or act[k] (FP64).  Steps are powers of two, so dividing by h, h^2, h^3
-// is the exact multiplication by their reciprocals.
-__global__ void block_correct_kernel(int64_t n, const int32_t *__restrict__ act,
-                                     const int32_t *__restrict__ perm,
-                                     const BlockScalars *__restrict__ sc, double *t, double *dt,
-                                     long long *tq,
-                                     double *pos, double *vel, double *acc, double *jerk,
-                                     double *pot, const double *__restrict__ a1,
-                                     const double *__restrict__ j1, const double *__restrict__ p1,
-                                     double dt_max, double dt_min, double eta) {
-    const double tn = sc->t_next;
-    const long long tnq = sc->t_next_q;
-    const double inv_dt_min = recip_pow2(dt_min);
-    const int n_active = sc->n_active;
+// The corrector as a pass over the active list: row = act[k] (FP64 path).
+__global__ void block_correct_kernel(const BlockCorrect c, const int32_t *__restrict__ act,
+                                     const double *__restrict__ a1, const double *__restrict__ j1,
+                                     const double *__restrict__ p1) {
+    const double tn = c.sc->t_next;
+    const long long tnq = c.sc->t_next_q;
+    const int n_active = c.sc->n_active;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_active; k += gridDim.x * blockDim.x) {
-        const int64_t i = perm ? perm[act[k]] : act[k];
-        const double h = dt[i], h2 = h * h, h3 = h2 * h;
-        const double ih = recip_pow2(h), ih2 = ih * ih, ih3 = ih2 * ih;
-        double A1[3], J1[3], A2[3], A3[3];
+        const int64_t i = act[k];
+        double A1[3], J1[3];
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const int64_t q = d * n + i;
-            A1[d] = a1[q];
-            J1[d] = j1[q];
-            const double a0 = acc[q], j0 = jerk[q], v0 = vel[q];
-            const double v1 = v0 + (a0 + A1[d]) * h / 2.0 + (j0 - J1[d]) * h2 / 12.0;
-            pos[q] = pos[q] + (v0 + v1) * h / 2.0 + (a0 - A1[d]) * h2 / 12.0;
-            vel[q] = v1;
-            A3[d] = (12.0 * (a0 - A1[d]) + 6.0 * h * (j0 + J1[d])) * ih3;
-            A2[d] = (-6.0 * (a0 - A1[d]) - h * (4.0 * j0 + 2.0 * J1[d])) * ih2 + h * A3[d];
-            acc[q] = A1[d];
-            jerk[q] = J1[d];
+            A1[d] = a1[d * c.n + i];
+            J1[d] = j1[d * c.n + i];
         }
-        if (pot) pot[i] = p1[i];
-        const double na = sqrt(A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2]);
-        const double nj = sqrt(J1[0] * J1[0] + J1[1] * J1[1] + J1[2] * J1[2]);
-        const double n2 = sqrt(A2[0] * A2[0] + A2[1] * A2[1] + A2[2] * A2[2]);
-        const double n3 = sqrt(A3[0] * A3[0] + A3[1] * A3[1] + A3[2] * A3[2]);
-        const double den = nj * n3 + n2 * n2;
-        const double da = den > 0.0 ? sqrt(eta * (na * n2 + nj * nj) / den) : dt_max;
-        double nd = h;
-        while (nd > da && nd > dt_min) nd /= 2.0;
-        if (nd == h && da >= 2.0 * h && 2.0 * h <= dt_max && fmod(tn, 2.0 * h) == 0.0) nd = 2.0 * h;
-        t[i] = tn;
-        dt[i] = nd;
-        tq[i] = tnq + (long long)(nd * inv_dt_min);
+        correct_particle(c, i, A1, J1, p1[i], tn, tnq);
     }
 }
 
@@ -1177,7 +1248,7 @@ cudaError_t launch_block_queue(const BlockLaunch &b, cudaStream_t s, int *kernel
 }
 #undef NB_BL
 
-cudaError_t launch_subset_few(const F32CJerkParams &prm, const int32_t *act, BlockScalars *sc,
+cudaError_t launch_subset_few(const F32CSubsetParams &prm, const int32_t *act, BlockScalars *sc,
                               double *part, cudaStream_t s) {
     subset_few_kernel<<<kFewCtas, kFewThreads, 0, s>>>(prm, act, sc, part);
     return cudaGetLastError();
@@ -1202,13 +1273,12 @@ cudaError_t launch_subset_f64(int max_items, const double *xp, const double *vp,
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_correct(const BlockLaunch &b, const double *a1, const double *j1,
-                                 const double *p1, double *pot, double dt_max, double dt_min, double eta,
-                                 cudaStream_t s) {
-    if (b.n <= 0) return cudaSuccess;
-    block_correct_kernel<<<grid_of(b.n, 256), 256, 0, s>>>(b.n, b.act, b.px ? b.perm : nullptr, b.sc, b.t,
-                                                           b.dt, b.tq, b.pos, b.vel, b.acc, b.jerk, pot, a1, j1,
-                                                           p1, dt_max, dt_min, eta);
+cudaError_t launch_block_correct(const BlockCorrect &c, const int32_t *act, const double *a1,
+                                 const double *j1, const double *p1, cudaStream_t s) {
+    if (c.n <= 0) return cudaSuccess;
+    // grid-stride over the active list: a few waves suffice for every particle
+    const int grid = std::min(grid_of(c.n, 256), 2 * 152);
+    block_correct_kernel<<<grid, 256, 0, s>>>(c, act, a1, j1, p1);
     return cudaGetLastError();
 }
 

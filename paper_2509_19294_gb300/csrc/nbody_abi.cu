@@ -926,16 +926,32 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
                                j.perm, s, kernels));
     NB_CUDA(launch_block_prepare(b, s, kernels));
     NB_CUDA(launch_block_queue(b, s, kernels));
+    BlockCorrect corr{};
+    corr.sc = bs.sc;
+    corr.t = bs.t;
+    corr.dt = bs.dt;
+    corr.tq = bs.tq;
+    corr.pos = a.pos;
+    corr.vel = a.vel;
+    corr.acc = a.acc;
+    corr.jerk = a.jerk;
+    corr.pot = a.pot;
+    corr.n = ctx->n;
+    corr.dt_max = bs.dt_max;
+    corr.dt_min = bs.dt_min;
+    corr.eta = bs.eta;
     if (ctx->mode == NBODY_F32C) {
+        // the force kernels' epilogues apply the corrector (no separate pass)
         F32CSubsetParams q{};
         q.base = jerk_params(ctx, j.a1, j.j1, bs.p1);
+        q.corr = corr;
         q.act_slot = bs.act;
         q.items = bs.items;
         q.n_items = &bs.sc->n_items;
         q.partial = bs.partial;
         q.tcj = j.tc;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
-        NB_CUDA(launch_subset_few(q.base, bs.act, bs.sc, bs.few_part, s));
+        NB_CUDA(launch_subset_few(q, bs.act, bs.sc, bs.few_part, s));
         q.n_items = &bs.sc->n_items_small;
         NB_CUDA(launch_subset_f32c(bs.sub.block, bs.sub.p, bs.sub.tj, bs.sub.split,
                                    bs.sub.ctas_per_sm, ctx->eps_zero, bs.workers, q, s));
@@ -953,9 +969,9 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
                                   &bs.sc->n_items, bs.act, ctx->n, ctx->G, j.a1, j.j1, bs.p1, s));
         ++*kernels;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
+        NB_CUDA(launch_block_correct(corr, bs.act, j.a1, j.j1, bs.p1, s));
+        ++*kernels;
     }
-    NB_CUDA(launch_block_correct(b, j.a1, j.j1, bs.p1, a.pot, bs.dt_max, bs.dt_min, bs.eta, s));
-    ++*kernels;
     return NBODY_OK;
 }
 

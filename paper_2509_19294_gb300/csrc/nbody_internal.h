@@ -131,7 +131,7 @@ struct SubItem {
 // Block steps with at most kFewMax active particles take the few-particle
 // kernel (j-parallel) instead of the i-chunk subset kernel.
 constexpr int kFewMax = 32;
-constexpr int kFewCtas = 64;
+constexpr int kFewCtas = 152;
 
 struct BlockScalars {
     double t_next;   // time of the current block step
@@ -151,8 +151,19 @@ struct BlockScalars {
 
 // Subset acceleration + jerk kernel: base carries the j-set (the jerk path's
 // packed predicted particles), perm (slot -> row) and the outputs (rows).
+// Hermite corrector + next-step choice of the block scheme, applied where an
+// active particle's acceleration and jerk become final (block.cu).
+struct BlockCorrect {
+    const BlockScalars *sc;
+    double *t, *dt, *pos, *vel, *acc, *jerk, *pot;  // rows; acc, jerk: the particle's a0, j0
+    long long *tq;
+    int64_t n;
+    double dt_max, dt_min, eta;
+};
+
 struct F32CSubsetParams {
     F32CJerkParams base;
+    BlockCorrect corr;        // corr.sc == nullptr: store a1, j1, p1 instead
     const int32_t *act_slot;  // active list: j-set slot of each active particle
     const SubItem *items;
     const int *n_items;       // device count
@@ -206,7 +217,7 @@ cudaError_t launch_subset_reduce(int max_chunks, int max_cs, int max_ctas, const
                                  const SubItem *info, const BlockScalars *sc, cudaStream_t s);
 // Few-particle path: all j of the active clusters in parallel, FP64 partials per
 // CTA (part: kFewCtas * kFewMax * 7 doubles) summed in order by the last CTA.
-cudaError_t launch_subset_few(const F32CJerkParams &prm, const int32_t *act, BlockScalars *sc,
+cudaError_t launch_subset_few(const F32CSubsetParams &prm, const int32_t *act, BlockScalars *sc,
                               double *part, cudaStream_t s);
 // block * groups threads per CTA (see SubsetKernel in block.cu).
 cudaError_t launch_subset_f32c(int block, int p, int tj, int groups, int minb, bool eps_zero,
@@ -215,9 +226,10 @@ cudaError_t launch_subset_f64(int max_items, const double *xp, const double *vp,
                               const ClusterDev *cl, const SubItem *items, const int *n_items,
                               const int32_t *act, int64_t n, double G, double *acc, double *jerk,
                               double *pot, cudaStream_t s);
-cudaError_t launch_block_correct(const BlockLaunch &b, const double *a1, const double *j1,
-                                 const double *p1, double *pot, double dt_max, double dt_min, double eta,
-                                 cudaStream_t s);
+// The corrector as its own pass over the active list (the FP64 path; the F32C
+// force kernels apply it in their epilogues).
+cudaError_t launch_block_correct(const BlockCorrect &c, const int32_t *act, const double *a1,
+                                 const double *j1, const double *p1, cudaStream_t s);
 
 
 // ---- kernel launchers (all enqueue on `s`, return cudaGetLastError()) ----
