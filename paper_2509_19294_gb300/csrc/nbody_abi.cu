@@ -1537,11 +1537,26 @@ int nbody_block_advance(nbody_ctx *ctx, double *pos, double *vel, const double *
     cudaStream_t s = (cudaStream_t)stream;
     NB_CUDA(cudaMemcpyAsync(&b.sc->t_end, &t_end, sizeof(double), cudaMemcpyHostToDevice, s));
     BlockScalars h{};
+    NB_CUDA(cudaMemcpyAsync(&h, b.sc, sizeof h, cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    const double t0 = h.t_next;
+    const long long blocks0 = h.blocks;
+    int batch = 16;
     for (;;) {
-        if ((rc = step_common(ctx, pos, vel, mass, acc, jerk, pot, 0.0, 16, nullptr, stream, 2))) return rc;
+        // steps past t_end find no active particle and change nothing, so a
+        // batch may overshoot; its size follows the block-step rate so far
+        // (about half the steps still expected, 16..256), which keeps the
+        // host round trips few and the wasted steps bounded
+        if ((rc = step_common(ctx, pos, vel, mass, acc, jerk, pot, 0.0, batch, nullptr, stream, 2))) return rc;
         NB_CUDA(cudaMemcpyAsync(&h, b.sc, sizeof h, cudaMemcpyDeviceToHost, s));
         NB_CUDA(cudaStreamSynchronize(s));
         if (!(h.t_next <= t_end)) break;
+        const double done = h.t_next - t0;
+        if (done > 0.0) {
+            const double rate = (double)(h.blocks - blocks0) / done;
+            const double left = rate * (t_end - h.t_next);
+            batch = (int)std::min(256.0, std::max(16.0, 0.5 * left));
+        }
         if (ctx->mode == NBODY_F32C && ctx->reorder_every > 0) {
             const int64_t epoch = (int64_t)std::floor(h.t_next / (ctx->reorder_every * b.dt_max));
             if (epoch > b.reorder_epoch) {
