@@ -385,7 +385,7 @@ def run_ours(args):
 
     # individual (block) time steps on the paper's particle count
     block = None
-    if rank == 0 and not args.no_paper_scale:
+    if rank == 0 and not args.no_block_steps:
         from paper_2509_19294_gb300 import ic
         bp_, bv_, bm_ = ic.plummer(PAPER_N, seed=7)
         with nb.nbody_init(PAPER_N, 1e-3, mode=nb.NBODY_F32C, reorder_every=4,
@@ -589,6 +589,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-paper-scale", action="store_true")
+    ap.add_argument("--no-block-steps", action="store_true")
     ap.add_argument("--n-each", type=int, default=N_EACH,
                     help="particles per sphere (default 524288: the N=1M workload)")
     ap.add_argument("--tiles", default=None,
