@@ -415,7 +415,10 @@ def run_ours(args):
                  "subset_kernel_ms_total": kms,
                  "steps_histogram": {f"2^{int(round(np.log2(v)))}": int(c)
                                      for v, c in zip(*np.unique(dts, return_counts=True))},
-                 "shared_step_equivalent_evaluations": int(blocks) * PAPER_N}
+                 "shared_step_equivalent_evaluations": int(blocks) * PAPER_N,
+                 "subset_kernel_scope": "CUDA events around each step's force pass: the few-particle "
+                                        "or subset kernels, the split reduction and, fused into their "
+                                        "epilogues, the Hermite corrector"}
 
     # end to end through the same C ABI call with pinned host buffers
     e2e = None
