@@ -558,7 +558,8 @@ struct SubsetShape {
 // Small active sets: several thread groups per CTA split each j-tile (more
 // warps on few i-chunks); large ones: one group, P = 2 (more reuse per load).
 const SubsetShape kSubsetShapes[] = {SUBSET(64, 1, 256, 4, 2), SUBSET(64, 1, 128, 4, 2),
-                                     SUBSET(64, 2, 256, 1, 4), SUBSET(64, 2, 128, 1, 4)};
+                                     SUBSET(64, 1, 512, 4, 2), SUBSET(64, 2, 256, 1, 4),
+                                     SUBSET(64, 2, 128, 1, 4), SUBSET(64, 2, 512, 1, 4)};
 
 const SubsetShape *find_subset(int block, int p, int tj, int groups, int minb, bool eps_zero) {
     for (const SubsetShape &s : kSubsetShapes)

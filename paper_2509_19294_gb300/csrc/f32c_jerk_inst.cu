@@ -19,8 +19,8 @@ struct JerkShape {
     JerkShape{B, P, T, M, false, (const void *)forces_f32c_jerk_kernel<B, P, T, M, false>}, \
         JerkShape{B, P, T, M, true, (const void *)forces_f32c_jerk_kernel<B, P, T, M, true>}
 
-const JerkShape kJerkShapes[] = {SHAPE(128, 2, 256, 2), SHAPE(256, 2, 256, 1), SHAPE(128, 1, 128, 4),
-                                 SHAPE(64, 2, 128, 4), SHAPE(128, 2, 128, 3)};
+const JerkShape kJerkShapes[] = {SHAPE(128, 2, 256, 2), SHAPE(256, 2, 256, 1), SHAPE(256, 2, 512, 1),
+                                 SHAPE(128, 1, 128, 4), SHAPE(64, 2, 128, 4), SHAPE(128, 2, 128, 3)};
 constexpr int kNumJerkShapes = sizeof(kJerkShapes) / sizeof(kJerkShapes[0]);
 
 const JerkShape *find(int block, int p, int tj, int minb, bool eps_zero) {

@@ -32,9 +32,11 @@ def _built():
 
 
 def block_run(pos, vel, mass, eps, mode, eta=0.02, eta_s=0.01, t_end=T_END, offsets=None, flags=0,
-              **kw):
+              jerk_tiles=None, **kw):
     n = mass.shape[0]
     with nb.nbody_init(n, eps, mode=mode, cluster_offsets=offsets, flags=flags, **kw) as ctx:
+        if jerk_tiles is not None:
+            nb.nbody_set_jerk_tiles(ctx, jerk_tiles)
         p, v, m = dev(pos), dev(vel), dev(mass)
         a = torch.empty((3, n), dtype=torch.float64, device="cuda")
         j = torch.empty((3, n), dtype=torch.float64, device="cuda")
@@ -92,9 +94,12 @@ def test_equal_steps_reduce_to_shared_hermite(mode):
         assert np.median(dv) <= 4 * DT_MAX * 2e-6 * amax, np.median(dv)
 
 
-def test_f32c_block_steps_track_oracle(oracle):
+# j-tile widths 128 (default at this N), 256 and 512: each has its own subset kernels
+@pytest.mark.parametrize("jerk_tiles", [None, (128, 2, 256, 0, 2), (256, 2, 512, 0, 1)])
+def test_f32c_block_steps_track_oracle(oracle, jerk_tiles):
     pos, vel, mass = cluster_system(2000, 53)
-    gp, gv, ga, gj, gdt, gt, gb, ge = block_run(pos, vel, mass, 0.005, nb.NBODY_F32C)
+    gp, gv, ga, gj, gdt, gt, gb, ge = block_run(pos, vel, mass, 0.005, nb.NBODY_F32C,
+                                                jerk_tiles=jerk_tiles)
     rp, rv, ra, rj, _, rdt, rb, re = oracle.block_hermite(pos, vel, mass, 0.005, T_END, DT_MAX, DT_MIN,
                                                          0.02, 0.01)
     assert np.all(gt == T_END)

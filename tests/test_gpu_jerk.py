@@ -90,7 +90,8 @@ def test_ragged_sizes(oracle, n, eps):
 def test_every_jerk_shape_and_split(oracle):
     pos, vel, mass = ic.plummer(3001, seed=42)
     ra, rj, rp = oracle.forces_jerk(pos, vel, mass, 0.01)
-    shapes = [(128, 2, 256, 2), (256, 2, 256, 1), (128, 1, 128, 4), (64, 2, 128, 4), (128, 2, 128, 3)]
+    shapes = [(128, 2, 256, 2), (256, 2, 256, 1), (256, 2, 512, 1), (128, 1, 128, 4), (64, 2, 128, 4),
+              (128, 2, 128, 3)]
     for b, p_, tj, m in shapes:
         for split in (1, 3):
             a, j, p = forces_jerk(pos, vel, mass, 0.01, jerk_tiles=(b, p_, tj, split, m))
