@@ -177,16 +177,18 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None}
 
 
-def traffic_for_current_kernel():
+def traffic_for_current_kernel(tiles):
     """DRAM bytes per force launch from the committed ncu summary, if it was
-    taken on the kernel source as it is now (else null)."""
+    taken on the kernel source as it is now and with the same tile shape and
+    split (else null)."""
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f)
         with open(FORCE_SRC, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
-        if rec.get("source_sha256") == sha:
-            return rec.get("dram_bytes_per_launch")
+        for r in rec.get("records", [rec]):
+            if r.get("source_sha256") == sha and list(r.get("tiles", [])) == list(tiles):
+                return r.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
     return None
@@ -471,7 +473,7 @@ def run_ours(args):
     peak_mufu = MUFU_PER_SM * sms * sm_max * 1e6 / 1e9
     peak = min(peak_fp32, peak_mufu)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginteractions/s",
-            "frac": achieved / peak, "traffic": traffic_for_current_kernel(),
+            "frac": achieved / peak, "traffic": traffic_for_current_kernel(tiles),
             "kernel": "forces_f32c_kernel", "avg_launch_ms": kern_avg_s * 1e3,
             "launches": kern_n,
             "peak_basis": f"FP32 pipe: {FP32_LANES_PER_SM} lanes/SM x {sms} SMs x {sm_max:.0f} MHz "

@@ -9,7 +9,7 @@ namespace nbody {
     F32CShape{B, P, T, M, false, (const void *)forces_f32c_kernel<B, P, T, M, false>}, \
         F32CShape{B, P, T, M, true, (const void *)forces_f32c_kernel<B, P, T, M, true>}
 
-extern const F32CShape kShapesA[] = {SHAPE(256, 2, 256, 2), SHAPE(256, 2, 256, 3), SHAPE(128, 2, 256, 4), SHAPE(128, 2, 256, 5)};
+extern const F32CShape kShapesA[] = {SHAPE(256, 2, 256, 2), SHAPE(128, 2, 256, 4), SHAPE(256, 4, 1024, 1)};
 extern const int kNumShapesA = sizeof(kShapesA) / sizeof(kShapesA[0]);
 
 }  // namespace nbody

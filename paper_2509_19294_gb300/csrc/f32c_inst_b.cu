@@ -9,7 +9,7 @@ namespace nbody {
     F32CShape{B, P, T, M, false, (const void *)forces_f32c_kernel<B, P, T, M, false>}, \
         F32CShape{B, P, T, M, true, (const void *)forces_f32c_kernel<B, P, T, M, true>}
 
-extern const F32CShape kShapesB[] = {SHAPE(128, 4, 256, 3), SHAPE(128, 4, 256, 4), SHAPE(128, 2, 256, 6), SHAPE(128, 4, 512, 3)};
+extern const F32CShape kShapesB[] = {SHAPE(128, 4, 256, 3), SHAPE(128, 4, 512, 3)};
 extern const int kNumShapesB = sizeof(kShapesB) / sizeof(kShapesB[0]);
 
 }  // namespace nbody

@@ -9,7 +9,7 @@ namespace nbody {
     F32CShape{B, P, T, M, false, (const void *)forces_f32c_kernel<B, P, T, M, false>}, \
         F32CShape{B, P, T, M, true, (const void *)forces_f32c_kernel<B, P, T, M, true>}
 
-extern const F32CShape kShapesC[] = {SHAPE(256, 4, 512, 1), SHAPE(256, 4, 512, 2), SHAPE(128, 3, 384, 4), SHAPE(256, 1, 256, 6)};
+extern const F32CShape kShapesC[] = {SHAPE(256, 4, 512, 1), SHAPE(128, 3, 384, 4)};
 extern const int kNumShapesC = sizeof(kShapesC) / sizeof(kShapesC[0]);
 
 }  // namespace nbody

@@ -9,7 +9,7 @@ namespace nbody {
     F32CShape{B, P, T, M, false, (const void *)forces_f32c_kernel<B, P, T, M, false>}, \
         F32CShape{B, P, T, M, true, (const void *)forces_f32c_kernel<B, P, T, M, true>}
 
-extern const F32CShape kShapesD[] = {SHAPE(64, 2, 128, 8), SHAPE(64, 2, 128, 12), SHAPE(128, 1, 128, 8), SHAPE(64, 4, 256, 6)};
+extern const F32CShape kShapesD[] = {SHAPE(64, 2, 128, 8), SHAPE(64, 4, 256, 6)};
 extern const int kNumShapesD = sizeof(kShapesD) / sizeof(kShapesD[0]);
 
 }  // namespace nbody

@@ -331,7 +331,7 @@ int choose_split(const nbody_ctx *c, int tc, int tj, int workers) {
 }
 
 nbody_tiles default_tiles(const nbody_ctx *c) {
-    if (c->max_cluster >= 65536) return {256, 4, 512, 0, 1};
+    if (c->max_cluster >= 65536) return {256, 4, 1024, 0, 1};
     if (c->max_cluster >= 8192) return {128, 2, 256, 0, 4};
     return {64, 2, 128, 0, 8};
 }
@@ -1108,7 +1108,9 @@ int run_tuner(nbody_ctx *ctx, cudaStream_t s) {
                          [](const std::pair<double, nbody_tiles> &x, const std::pair<double, nbody_tiles> &y) {
                              return x.first < y.first;
                          });
-        const double jfrac2 = std::min(1.0, 4.0 * jfrac);
+        // the three best again on a longer run: the full evaluation up to 2e12
+        // pairs (a few seconds), else 4x the first proxy
+        const double jfrac2 = std::min(1.0, std::max(4.0 * jfrac, 2.0e12 / std::max(total_pairs, 1.0)));
         for (size_t k = 0; k < std::min<size_t>(3, timed.size()) && rc == NBODY_OK; ++k) {
             const double ms = jfrac2 > jfrac ? time_shape(ctx, timed[k].second, jfrac2, 2, acc, e0, e1, s, &rc)
                                              : timed[k].first;
