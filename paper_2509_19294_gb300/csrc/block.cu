@@ -1,16 +1,22 @@
-// block.cu -- individual (block) time steps: forces on the active subset.
+// block.cu -- individual (block) time steps: scheduling and forces on the
+// active subset.
 //
 // Around the Hermite scheme each particle keeps its own time t_i and a
 // power-of-two step dt_i (Makino & Aarseth 1992; the paper computes the jerk,
 // Sec. 3, but does not describe its stepping).  One block step, all on the
-// device so that it is a fixed kernel sequence a CUDA graph can replay:
-//   1. t_next = min_i (t_i + dt_i)              (two-stage exact min)
-//   2. predict every particle to t_next, flag the active ones
-//   3. ordered compaction of the active set per cluster, i-chunk counts,
-//      split count and the work queue, built on the device
-//   4. pack every predicted particle as the j-set (the jerk path's geometry)
-//   5. forces + jerks of the active i-chunks against all j (this file)
-//   6. correct the active particles and choose their next steps
+// device so that it is a fixed kernel sequence a CUDA graph can replay
+// (F32C; the FP64 path keeps separate predict / count / plan / scatter /
+// items / correct kernels around its own subset kernel):
+//   1. block_min_kernel: t_next = min_i (t_i + dt_i), an integer min in units
+//      of dt_min (exact)
+//   2. block_pack_kernel: predict every particle to t_next, pack it as the
+//      j-set (the jerk path's geometry), flag and count the active slots per
+//      tile; the last CTA plans the step (offsets, regime, split, queue size)
+//   3. block_queue_kernel: ordered compaction of the active slots, work items
+//   4. the force pass, one of: subset_few_kernel (<= kFewMax active), the
+//      small-set or the large-set subset kernel; split j-ranges summed by
+//      subset_reduce_kernel
+//   5. the Hermite corrector and next-step choice, in the epilogue of 4
 // An active particle is evaluated with its own j-set offset and its own tile
 // centre: per j-tile each thread forms the exact centre difference for each of
 // its particles, so the self pair is exactly zero, as in the full kernels.
