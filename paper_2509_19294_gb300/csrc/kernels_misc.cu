@@ -10,42 +10,70 @@ namespace nbody {
 
 namespace {
 
-// One CTA per centre tile: centre = FP64 mean of the tile's real particles
-// (fixed reduction tree, so bitwise reproducible), FP32 offsets from it, FP32
-// masses; pad slots get mass 0 and a far offset.  The centre is stored as a
-// float pair hi + lo for the force kernels.  With VEL the tile's velocities are
-// packed the same way (mean velocity as a float pair, offsets; pads 0).
+// One CTA per centre tile: FP32 offsets of the tile's particles from its
+// centre, FP32 masses; pad slots get mass 0 and a far offset.  The centre is
+// the mean of the FP32-rounded positions, summed in FP32 in a fixed order (so
+// bitwise reproducible); any point near the tile serves, since the offsets are
+// FP64 differences from it rounded once, and FP64 work is scarce on this part
+// (one FP32 reduction instead of an FP64 one and six divisions per thread).
+// The centre is stored as a float pair (hi, lo = 0) for the force kernels.
+// With VEL the velocities are packed the same way (pads get offset 0).
 template <int NT, bool VEL>
 __global__ void __launch_bounds__(NT) pack_kernel(const PackParams p) {
     constexpr int NV = VEL ? 7 : 4;
-    __shared__ double red[NT / 32][NV];
+    __shared__ float red[NT / 32][NV];
+    __shared__ float cen[6];
     const int t = blockIdx.x;
     const ClusterDev cl = p.cl[p.tile_cluster[t]];
     const int base = t * p.tc;
     const int per = p.tc / NT;
-    double s[NV];
+    float s[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) s[k] = 0.0;
+    for (int k = 0; k < NV; ++k) s[k] = 0.0f;
     for (int r = 0; r < per; ++r) {
         const int slot = base + threadIdx.x + NT * r;
         if (slot - cl.slot_begin < cl.n) {
             const int64_t u = p.perm[slot];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) s[d] += p.pos[d * p.n + u];
-            s[3] += 1.0;
+            for (int d = 0; d < 3; ++d) s[d] += (float)p.pos[d * p.n + u];
+            s[3] += 1.0f;
             if (VEL)
 #pragma unroll
-                for (int d = 0; d < 3; ++d) s[4 + d] += p.vel[d * p.n + u];
+                for (int d = 0; d < 3; ++d) s[4 + d] += (float)p.vel[d * p.n + u];
         }
     }
-    block_sum<NT, NV>(s, red);
-    const double cnt = s[3] > 0.0 ? s[3] : 1.0;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    if (threadIdx.x % 32 == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[threadIdx.x / 32][k] = s[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            float v = red[0][k];
+            for (int w = 1; w < NT / 32; ++w) v += red[w][k];
+            s[k] = v;
+        }
+        const float inv = s[3] > 0.0f ? 1.0f / s[3] : 0.0f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            cen[d] = s[d] * inv;
+            cen[3 + d] = VEL ? s[4 + d] * inv : 0.0f;
+        }
+        p.chl[2 * t + 0] = make_float4(cen[0], cen[1], cen[2], 0.0f);
+        p.chl[2 * t + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (VEL) {
+            p.vchl[2 * t + 0] = make_float4(cen[3], cen[4], cen[5], 0.0f);
+            p.vchl[2 * t + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+    }
+    __syncthreads();
     double c[6];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        c[d] = s[d] / cnt;
-        c[3 + d] = VEL ? s[4 + d] / cnt : 0.0;
-    }
+    for (int d = 0; d < 6; ++d) c[d] = (double)cen[d];
     for (int r = 0; r < per; ++r) {
         const int slot = base + threadIdx.x + NT * r;
         if (slot - cl.slot_begin < cl.n) {
@@ -65,18 +93,6 @@ __global__ void __launch_bounds__(NT) pack_kernel(const PackParams p) {
             p.pz[slot] = kPadOffset;
             p.pm[slot] = 0.0f;
             if (VEL) p.pvx[slot] = p.pvy[slot] = p.pvz[slot] = 0.0f;
-        }
-    }
-    if (threadIdx.x == 0) {
-        float h[6];
-#pragma unroll
-        for (int d = 0; d < 6; ++d) h[d] = (float)c[d];
-        p.chl[2 * t + 0] = make_float4(h[0], h[1], h[2], 0.0f);
-        p.chl[2 * t + 1] = make_float4((float)(c[0] - h[0]), (float)(c[1] - h[1]), (float)(c[2] - h[2]), 0.0f);
-        if (VEL) {
-            p.vchl[2 * t + 0] = make_float4(h[3], h[4], h[5], 0.0f);
-            p.vchl[2 * t + 1] =
-                make_float4((float)(c[3] - h[3]), (float)(c[4] - h[4]), (float)(c[5] - h[5]), 0.0f);
         }
     }
 }
