@@ -84,6 +84,58 @@ __device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t 
     c.tq[i] = tnq + (long long)(nd * inv_dt_min);
 }
 
+// correct_particle spread over four consecutive lanes of a warp: lane sub
+// (0..2) corrects component sub, the norms are summed across the three lanes
+// in component order, and lane 0 chooses the step.  Every lane of the warp
+// calls it (the shuffles need them); lanes with valid == false store nothing.
+__device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64_t i, bool valid, int sub,
+                                                    double a1, double j1, double p1, double tn,
+                                                    long long tnq) {
+    const double h = c.dt[i], h2 = h * h;
+    const double ih = recip_pow2(h), ih2 = ih * ih, ih3 = ih2 * ih;
+    double sq[4] = {0.0, 0.0, 0.0, 0.0};  // this component's a1^2, j1^2, a2^2, a3^2
+    if (sub < 3) {
+        const int64_t q = sub * c.n + i;
+        const double a0 = c.acc[q], j0 = c.jerk[q], v0 = c.vel[q];
+        const double v1 = v0 + (a0 + a1) * h / 2.0 + (j0 - j1) * h2 / 12.0;
+        const double x1 = c.pos[q] + (v0 + v1) * h / 2.0 + (a0 - a1) * h2 / 12.0;
+        const double a3 = (12.0 * (a0 - a1) + 6.0 * h * (j0 + j1)) * ih3;
+        const double a2 = (-6.0 * (a0 - a1) - h * (4.0 * j0 + 2.0 * j1)) * ih2 + h * a3;
+        if (valid) {
+            c.pos[q] = x1;
+            c.vel[q] = v1;
+            c.acc[q] = a1;
+            c.jerk[q] = j1;
+        }
+        sq[0] = a1 * a1;
+        sq[1] = j1 * j1;
+        sq[2] = a2 * a2;
+        sq[3] = a3 * a3;
+    }
+    const int lane = threadIdx.x % 32, base = lane & ~3;
+    double nrm[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double x = __shfl_sync(0xffffffffu, sq[k], base);
+        const double y = __shfl_sync(0xffffffffu, sq[k], base + 1);
+        const double z = __shfl_sync(0xffffffffu, sq[k], base + 2);
+        nrm[k] = sqrt(x + y + z);
+    }
+    if (sub != 0 || !valid) return;
+    if (c.pot) c.pot[i] = p1;
+    const double na = nrm[0], nj = nrm[1], n2 = nrm[2], n3 = nrm[3];
+    const double den = nj * n3 + n2 * n2;
+    const double da = den > 0.0 ? sqrt(c.eta * (na * n2 + nj * nj) / den) : c.dt_max;
+    const double inv_dt_min = recip_pow2(c.dt_min);
+    double nd = h;
+    while (nd > da && nd > c.dt_min) nd *= 0.5;
+    const long long q2 = (long long)(2.0 * h * inv_dt_min);
+    if (nd == h && da >= 2.0 * h && 2.0 * h <= c.dt_max && tnq % q2 == 0) nd = 2.0 * h;
+    c.t[i] = tn;
+    c.dt[i] = nd;
+    c.tq[i] = tnq + (long long)(nd * inv_dt_min);
+}
+
 // FP64 epilogue of one active particle: scale by G, remove the self term of
 // phi (its own j-tile contributed m_i rsqrt(eps^2) exactly), then correct the
 // particle (corr.sc set) or store a1, j1, p1 at its row.
@@ -495,11 +547,29 @@ __global__ void __launch_bounds__(kFewThreads)
         }
     }
     __syncthreads();
-    for (int a = threadIdx.x; a < na; a += blockDim.x) {
-        double r[7];
+    if (q.corr.sc) {
+        // epilogue + corrector with four lanes per particle (one per
+        // component, the first also for the step choice): the FP64 chain of
+        // a single particle is what a small step waits for
+        if (threadIdx.x < 4 * kFewMax) {
+            const int a = threadIdx.x / 4, sub = threadIdx.x % 4;
+            const bool valid = a < na;
+            const int aa = valid ? a : 0;
+            const ClusterDev cl = p.cl[fcl[ocl[aa]]];
+            const int slot = act[aa];
+            double ph = csum[aa][6];
+            if (cl.eps2f > 0.0f) ph -= (double)__fmul_rn(p.pm[slot], rsqrt_mufu(cl.eps2f));
+            correct_particle_x4(q.corr, p.perm[slot], valid, sub, p.G * csum[aa][sub < 3 ? sub : 0],
+                                p.G * csum[aa][sub < 3 ? 3 + sub : 3], -p.G * ph, sc->t_next,
+                                sc->t_next_q);
+        }
+    } else {
+        for (int a = threadIdx.x; a < na; a += blockDim.x) {
+            double r[7];
 #pragma unroll
-        for (int c = 0; c < 7; ++c) r[c] = csum[a][c];
-        subset_finalize(p, q.corr, p.cl[fcl[ocl[a]]], act[a], r);
+            for (int c = 0; c < 7; ++c) r[c] = csum[a][c];
+            subset_finalize(p, q.corr, p.cl[fcl[ocl[a]]], act[a], r);
+        }
     }
     if (threadIdx.x == 0) sc->ticket_few = 0;
 }
