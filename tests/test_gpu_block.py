@@ -142,6 +142,26 @@ def test_block_graph_equals_eager(mode):
         assert np.array_equal(np.asarray(x), np.asarray(y))
 
 
+@pytest.mark.parametrize("mode", [nb.NBODY_F64, nb.NBODY_F32C])
+def test_block_steps_without_softening(oracle, mode):
+    # eps = 0: the EPS_ZERO kernel variants (and the few-particle path's
+    # r^2 > 0 guard); a loose cluster so that no pair comes too close
+    pos, vel, mass = ic.plummer(400, seed=58)
+    pos = pos * 4.0
+    vel = vel / 2.0
+    gp, gv, ga, gj, gdt, gt, gb, ge = block_run(pos, vel, mass, 0.0, mode)
+    rp, rv, ra, rj, _, rdt, rb, re = oracle.block_hermite(pos, vel, mass, 0.0, T_END, DT_MAX, DT_MIN,
+                                                         0.02, 0.01)
+    assert len(np.unique(rdt)) > 1
+    if mode == nb.NBODY_F64:
+        assert np.array_equal(gdt, rdt) and gb == rb and ge == re
+        np.testing.assert_allclose(gp, rp, rtol=0, atol=1e-12)
+    else:
+        assert np.mean(gdt == rdt) >= 0.98
+        assert np.abs(gp - rp).max() <= 1e-7
+        assert metrics.summary(ga, ra)["median"] <= 1e-6
+
+
 def test_block_steps_save_evaluations():
     pos, vel, mass = cluster_system(3000, 56)
     *_, gb, ge = block_run(pos, vel, mass, 0.002, nb.NBODY_F32C)
