@@ -134,6 +134,26 @@ def test_ensemble_block_steps_equal_independent_clusters(oracle, mode):
 
 
 @pytest.mark.parametrize("mode", [nb.NBODY_F64, nb.NBODY_F32C])
+def test_block_steps_with_an_empty_cluster(oracle, mode):
+    p1, v1, m1 = ic.plummer(300, seed=59)
+    p2, v2, m2 = ic.plummer(400, seed=60)
+    pos, vel, mass = np.hstack([p1, p2]), np.hstack([v1, v2]), np.concatenate([m1, m2])
+    offsets = np.array([0, 300, 300, 700])
+    gp, gv, ga, gj, gdt, gt, gb, ge = block_run(pos, vel, mass, np.array([0.01, 0.02, 0.01]), mode,
+                                                offsets=offsets)
+    assert np.all(gt == T_END)
+    for (b, e), (pp, vv, mm) in zip([(0, 300), (300, 700)], [(p1, v1, m1), (p2, v2, m2)]):
+        rp, rv, ra, rj, _, rdt, rb, re = oracle.block_hermite(pp, vv, mm, 0.01, T_END, DT_MAX, DT_MIN,
+                                                             0.02, 0.01)
+        if mode == nb.NBODY_F64:
+            assert np.array_equal(gdt[b:e], rdt)
+            np.testing.assert_allclose(gp[:, b:e], rp, rtol=0, atol=1e-12)
+        else:
+            assert np.mean(gdt[b:e] == rdt) >= 0.98
+            assert np.abs(gp[:, b:e] - rp).max() <= 1e-7
+
+
+@pytest.mark.parametrize("mode", [nb.NBODY_F64, nb.NBODY_F32C])
 def test_block_graph_equals_eager(mode):
     pos, vel, mass = cluster_system(700, 55)
     g = block_run(pos, vel, mass, 0.01, mode, reorder_every=5)
