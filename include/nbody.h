@@ -197,7 +197,9 @@ int nbody_step_hermite(nbody_ctx *ctx, double *pos, double *vel, const double *m
  *
  * nbody_block_start: computes a, jerk, pot at the current state (t = 0) and the
  *   initial steps, the largest power of two <= min(dt_max, eta_s |a|/|a'|),
- *   not below dt_min.  dt_max and dt_min are powers of two.  Unless jerk tiles
+ *   not below dt_min.  dt_max and dt_min are powers of two with
+ *   dt_max / dt_min <= 2^40, and t_end / dt_min <= 2^60 (times are counted in
+ *   units of dt_min; NBODY_EINVAL otherwise).  Unless jerk tiles
  *   were set (nbody_set_jerk_tiles) or built by an earlier jerk call, it picks
  *   a tile shape suited to block steps (narrower j-tiles for large N).
  * nbody_block_advance: block steps until every particle reaches t_end (a

@@ -79,6 +79,10 @@ __device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t 
     while (nd > da && nd > c.dt_min) nd *= 0.5;
     const long long q2 = (long long)(2.0 * h * inv_dt_min);  // 2h in units of dt_min
     if (nd == h && da >= 2.0 * h && 2.0 * h <= c.dt_max && tnq % q2 == 0) nd = 2.0 * h;
+    if (c.level && nd != h) {
+        atomicSub(&c.level[block_level(h, c.dt_max)], 1);
+        atomicAdd(&c.level[block_level(nd, c.dt_max)], 1);
+    }
     c.t[i] = tn;
     c.dt[i] = nd;
     c.tq[i] = tnq + (long long)(nd * inv_dt_min);
@@ -131,6 +135,10 @@ __device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64
     while (nd > da && nd > c.dt_min) nd *= 0.5;
     const long long q2 = (long long)(2.0 * h * inv_dt_min);
     if (nd == h && da >= 2.0 * h && 2.0 * h <= c.dt_max && tnq % q2 == 0) nd = 2.0 * h;
+    if (c.level && nd != h) {
+        atomicSub(&c.level[block_level(h, c.dt_max)], 1);
+        atomicAdd(&c.level[block_level(nd, c.dt_max)], 1);
+    }
     c.t[i] = tn;
     c.dt[i] = nd;
     c.tq[i] = tnq + (long long)(nd * inv_dt_min);
@@ -722,6 +730,20 @@ __global__ void block_init_kernel(int64_t n, const double *acc, const double *je
     }
 }
 
+// Count the particles per step level (start of block stepping).
+__global__ void block_levels_kernel(int64_t n, const double *__restrict__ dt, double dt_max,
+                                    BlockScalars *sc) {
+    __shared__ int cnt[64];
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) cnt[k] = 0;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[block_level(dt[i], dt_max)], 1);
+    __syncthreads();
+    for (int k = threadIdx.x; k < 64; k += blockDim.x)
+        if (cnt[k]) atomicAdd(&sc->level[k], cnt[k]);
+}
+
 // t_next = min_i (t_i + dt_i), exact: the times are integers in units of
 // dt_min, so the min is an integer one.  Per-chunk minima, then the last CTA
 // to finish (ticket) takes the min over them.  No CTA waits for another.
@@ -966,6 +988,7 @@ struct BlockPackParams {
     int few_max;
     int cs_large, workers_large, large_min;
     long long partial_cap;  // doubles in the split-partial buffer
+    double dt_max, dt_min;
 };
 
 // Hermite predictor in Horner form for the packed j-set (F32C); its rounding
@@ -1000,8 +1023,10 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
     __shared__ bool last;
     __shared__ int total;
     const int tile = blockIdx.x;
-    const double tn = q.sc->t_next;
-    const long long tnq = q.sc->t_next_q;
+    // this step's time from the previous step's state (every CTA reads it
+    // before the last one, below, stores it)
+    const long long tnq = block_next_time_q(q.sc->t_next_q, q.sc->n_active, q.sc->level, q.dt_max, q.dt_min);
+    const double tn = (double)tnq * q.dt_min;
     const bool live = tn <= q.sc->t_end;
     const ClusterDev cl = q.cl[q.tile_cluster[tile]];
     const int base = tile * q.tc;
@@ -1087,6 +1112,8 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
     block_exclusive_scan<NT>(q.tile_cnt, q.tile_off, q.n_tiles, &total);
     __syncthreads();
     if (threadIdx.x == 0) {
+        q.sc->t_next_q = tnq;
+        q.sc->t_next = tn;
         plan_step(q.tile_off, total, q.n_tiles, q.tile_first, q.ncl, q.cl, q.cs, q.workers, q.max_split,
                   q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max, q.cs_large,
                   q.workers_large, q.large_min, q.partial_cap);
@@ -1265,6 +1292,18 @@ cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_block_levels(int64_t n, const double *dt, double dt_max, double dt_min,
+                                const Chunk *chunks, int n_chunks, const long long *tq, double *part,
+                                BlockScalars *sc, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    block_levels_kernel<<<grid_of(n, 256), 256, 0, s>>>(n, dt, dt_max, sc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    block_min_kernel<<<n_chunks, kMinThreads, 0, s>>>(tq, chunks, reinterpret_cast<long long *>(part),
+                                                      n_chunks, dt_min, sc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kernels) {
     cudaError_t e;
 #define NB_BL(x)                        \
@@ -1274,8 +1313,9 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         if (e != cudaSuccess) return e; \
         ++*kernels;                     \
     } while (0)
-    NB_BL((block_min_kernel<<<b.n_chunks, kMinThreads, 0, s>>>(
-        b.tq, b.chunks, reinterpret_cast<long long *>(b.part), b.n_chunks, b.dt_min, b.sc)));
+    if (!b.px)  // the F32C path has t_next from the previous step's last kernel
+        NB_BL((block_min_kernel<<<b.n_chunks, kMinThreads, 0, s>>>(
+            b.tq, b.chunks, reinterpret_cast<long long *>(b.part), b.n_chunks, b.dt_min, b.sc)));
     if (b.px) {
         if (b.tc <= 0 || b.tc % 128 != 0 || b.tc > kPackMaxPer * (b.tc % 256 == 0 ? 256 : 128))
             return cudaErrorInvalidValue;
@@ -1291,6 +1331,8 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         q.sc = b.sc; q.queue_head = b.queue_head; q.few_max = b.few_max;
         q.cs_large = b.cs_large; q.workers_large = b.workers_large; q.large_min = b.large_min;
         q.partial_cap = b.partial_cap;
+        q.dt_max = b.dt_max;
+        q.dt_min = b.dt_min;
         if (b.tc % 256 == 0) NB_BL((block_pack_kernel<256><<<b.n_tiles, 256, 0, s>>>(q)));
         else NB_BL((block_pack_kernel<128><<<b.n_tiles, 128, 0, s>>>(q)));
     } else {

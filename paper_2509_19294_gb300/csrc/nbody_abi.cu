@@ -875,6 +875,7 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
     b.dt = bs.dt;
     b.tq = bs.tq;
     b.dt_min = bs.dt_min;
+    b.dt_max = bs.dt_max;
     b.part = bs.part;
     b.pos = a.pos;
     b.vel = a.vel;
@@ -930,6 +931,7 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
     NB_CUDA(launch_block_queue(b, s, kernels));
     BlockCorrect corr{};
     corr.sc = bs.sc;
+    corr.level = bs.sc->level;
     corr.t = bs.t;
     corr.dt = bs.dt;
     corr.tq = bs.tq;
@@ -1501,6 +1503,8 @@ int nbody_block_start(nbody_ctx *ctx, const double *pos, const double *vel, cons
     if (!pow2(dt_max) || !pow2(dt_min) || dt_min > dt_max || !(eta > 0.0) || !(eta_s > 0.0) ||
         !std::isfinite(eta) || !std::isfinite(eta_s))
         return fail(ctx, NBODY_EINVAL, "block steps: dt_max, dt_min must be powers of two, eta > 0");
+    if (dt_max / dt_min > 0x1p40)
+        return fail(ctx, NBODY_EINVAL, "block steps: dt_max / dt_min must be at most 2^40");
     if (ctx->n == 0) return NBODY_OK;
     for (const void *q : {(const void *)pos, (const void *)vel, (const void *)mass, (const void *)acc,
                           (const void *)jerk})
@@ -1515,8 +1519,11 @@ int nbody_block_start(nbody_ctx *ctx, const double *pos, const double *vel, cons
     b.dt_min = dt_min;
     b.eta = eta;
     NB_CUDA(launch_block_init(ctx->n, acc, jerk, dt_max, dt_min, eta_s, b.t, b.dt, b.tq, s));
-    ctx->launches += 1;
     NB_CUDA(cudaMemsetAsync(b.sc, 0, sizeof(BlockScalars), s));
+    // level counts and the first t_next (later steps set the next one themselves)
+    NB_CUDA(launch_block_levels(ctx->n, b.dt, dt_max, dt_min, ctx->chunks, ctx->n_chunks, b.tq, b.part,
+                                b.sc, s));
+    ctx->launches += 3;
     NB_CUDA(cudaStreamSynchronize(s));
     b.reorder_epoch = 0;
     b.reorder_pending = false;
@@ -1534,6 +1541,8 @@ int nbody_block_advance(nbody_ctx *ctx, double *pos, double *vel, const double *
     if (!b.started) return fail(ctx, NBODY_EINVAL, "nbody_block_start was not called");
     if (!std::isfinite(t_end) || t_end < 0.0 || std::fmod(t_end, b.dt_max) != 0.0)
         return fail(ctx, NBODY_EINVAL, "t_end must be a non-negative multiple of dt_max");
+    if (t_end / b.dt_min > 0x1p60)
+        return fail(ctx, NBODY_EINVAL, "t_end / dt_min must be at most 2^60 (times are counted in dt_min)");
     for (const void *q : {(const void *)pos, (const void *)vel, (const void *)mass, (const void *)acc,
                           (const void *)jerk})
         if (!q || !is_device_ptr(q)) return fail(ctx, NBODY_EINVAL, "block steps need device arrays");
@@ -1554,7 +1563,8 @@ int nbody_block_advance(nbody_ctx *ctx, double *pos, double *vel, const double *
         if ((rc = step_common(ctx, pos, vel, mass, acc, jerk, pot, 0.0, batch, nullptr, stream, 2))) return rc;
         NB_CUDA(cudaMemcpyAsync(&h, b.sc, sizeof h, cudaMemcpyDeviceToHost, s));
         NB_CUDA(cudaStreamSynchronize(s));
-        if (!(h.t_next <= t_end)) break;
+        const double next = (double)block_next_time_q(h.t_next_q, h.n_active, h.level, b.dt_max, b.dt_min) * b.dt_min;
+        if (!(next <= t_end)) break;
         const double done = h.t_next - t0;
         if (done > 0.0) {
             const double rate = (double)(h.blocks - blocks0) / done;

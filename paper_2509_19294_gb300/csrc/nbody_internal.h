@@ -18,6 +18,8 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
+#include <string.h>
 
 namespace nbody {
 
@@ -140,6 +142,9 @@ struct BlockScalars {
     int n_active, n_chunks, split, n_items;
     long long blocks, evals;  // block steps taken, single-particle evaluations
     int ticket_min, ticket_pack, ticket_few;  // last-CTA tickets (each reset by its last CTA)
+    // particles per step level k (dt = dt_max 2^-k), kept by the corrector; the
+    // smallest occupied step gives the next step's time
+    int level[64];
     // few-particle path (F32C, n_active <= kFewMax): the clusters holding active
     // particles, their first active index and the prefix of their sizes
     int few, few_ncl;
@@ -155,11 +160,37 @@ struct BlockScalars {
 // active particle's acceleration and jerk become final (block.cu).
 struct BlockCorrect {
     const BlockScalars *sc;
+    int *level;  // BlockScalars::level (the corrector moves particles between levels)
     double *t, *dt, *pos, *vel, *acc, *jerk, *pot;  // rows; acc, jerk: the particle's a0, j0
     long long *tq;
     int64_t n;
     double dt_max, dt_min, eta;
 };
+
+// Level of a power-of-two step h below dt_max: dt_max / h = 2^level (from the
+// exponent fields, exact).
+__host__ __device__ __forceinline__ int block_level(double h, double dt_max) {
+    long long bh, bm;
+    memcpy(&bh, &h, sizeof bh);
+    memcpy(&bm, &dt_max, sizeof bm);
+    return (int)((bm >> 52) & 0x7FF) - (int)((bh >> 52) & 0x7FF);
+}
+
+// The next block time (in units of dt_min) after a step at time tq_now that
+// moved n_moved particles.  Every t_i is a multiple of its step dt_i with
+// t_i <= t_now < t_i + dt_i, so min (t_i + dt_i) is the next multiple of the
+// smallest occupied step; a step that moved nobody (past t_end, or the start)
+// leaves the time pending.
+__host__ __device__ __forceinline__ long long block_next_time_q(long long tq_now, int n_moved,
+                                                                const int *level, double dt_max,
+                                                                double dt_min) {
+    if (n_moved == 0) return tq_now;
+    const int kmax = block_level(dt_min, dt_max);
+    int k = kmax;
+    while (k > 0 && level[k] == 0) --k;
+    const long long step_q = 1LL << (kmax - k);
+    return (tq_now / step_q + 1) * step_q;
+}
 
 struct F32CSubsetParams {
     F32CJerkParams base;
@@ -179,7 +210,7 @@ struct BlockLaunch {
     const ClusterDev *cl;
     double *t, *dt, *part;
     long long *tq;  // t_i + dt_i in units of dt_min (exact: steps are powers of two >= dt_min)
-    double dt_min;
+    double dt_min, dt_max;
     double *pos, *vel, *acc, *jerk, *xp, *vp;
     const double *mass;
     uint8_t *flag;  // per row (FP64) or per j-set slot (F32C)
@@ -204,8 +235,9 @@ struct BlockLaunch {
 cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, double dt_max,
                               double dt_min, double eta_s, double *t, double *dt, long long *tq,
                               cudaStream_t s);
-// t_next, prediction (+ the packed j-set for F32C), flags, counts and the plan
-// (offsets, split, queue size, queue head reset).
+// t_next (FP64 path: integer min; F32C: from the level counts), prediction
+// (+ the packed j-set for F32C), flags, counts and the plan (offsets, split,
+// queue size, queue head reset).
 cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kernels);
 // Ordered compaction of the active particles (rows, or j-set slots for F32C)
 // and the work queue.
@@ -215,6 +247,10 @@ int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap);
 // Deterministic parallel sum of the subset kernel's split partials + epilogue.
 cudaError_t launch_subset_reduce(int max_chunks, int max_cs, int max_ctas, const F32CSubsetParams &prm,
                                  const SubItem *info, const BlockScalars *sc, cudaStream_t s);
+// Level counts of all particles and the first t_next (start of block stepping).
+cudaError_t launch_block_levels(int64_t n, const double *dt, double dt_max, double dt_min,
+                                const Chunk *chunks, int n_chunks, const long long *tq, double *part,
+                                BlockScalars *sc, cudaStream_t s);
 // Few-particle path: all j of the active clusters in parallel, FP64 partials per
 // CTA (part: kFewCtas * kFewMax * 7 doubles) summed in order by the last CTA.
 cudaError_t launch_subset_few(const F32CSubsetParams &prm, const int32_t *act, BlockScalars *sc,
