@@ -66,6 +66,10 @@ __device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t 
         A2[d] = (-6.0 * (a0 - A1[d]) - h * (4.0 * j0 + 2.0 * J1[d])) * ih2 + h * A3[d];
         c.acc[q] = A1[d];
         c.jerk[q] = J1[d];
+        if (c.af) {
+            c.af[q] = (float)A1[d];
+            c.jf[q] = (float)J1[d];
+        }
     }
     if (c.pot) c.pot[i] = p1;
     const double na = sqrt(A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2]);
@@ -110,6 +114,10 @@ __device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64
             c.vel[q] = v1;
             c.acc[q] = a1;
             c.jerk[q] = j1;
+            if (c.af) {
+                c.af[q] = (float)a1;
+                c.jf[q] = (float)j1;
+            }
         }
         sq[0] = a1 * a1;
         sq[1] = j1 * j1;
@@ -730,6 +738,16 @@ __global__ void block_init_kernel(int64_t n, const double *acc, const double *je
     }
 }
 
+// FP32 copies of a and a' for the packing predictor (start of block stepping).
+__global__ void block_shadow_kernel(int64_t n3, const double *__restrict__ acc,
+                                    const double *__restrict__ jerk, float *af, float *jf) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        af[k] = (float)acc[k];
+        jf[k] = (float)jerk[k];
+    }
+}
+
 // Count the particles per step level (start of block stepping).
 __global__ void block_levels_kernel(int64_t n, const double *__restrict__ dt, double dt_max,
                                     BlockScalars *sc) {
@@ -974,7 +992,8 @@ struct BlockPackParams {
     const int32_t *tile_cluster;
     int tc, n_tiles;
     int64_t n;
-    const double *mass, *t, *pos, *vel, *acc, *jerk;
+    const double *mass, *t, *pos, *vel;
+    const float *af, *jf;  // FP32 copies of each particle's a, a' (kept by the corrector)
     const long long *tq;
     float *px, *py, *pz, *pm, *pvx, *pvy, *pvz;
     float4 *chl, *vchl;
@@ -991,32 +1010,39 @@ struct BlockPackParams {
     double dt_max, dt_min;
 };
 
-// Hermite predictor in Horner form for the packed j-set (F32C); its rounding
-// differs from predict_row's only at the FP64 level, far below the FP32 offsets.
-__device__ __forceinline__ void predict_horner(int64_t n, int64_t u, double tn,
-                                               const double *__restrict__ t,
-                                               const double *__restrict__ pos,
-                                               const double *__restrict__ vel,
-                                               const double *__restrict__ acc,
-                                               const double *__restrict__ jerk, double (&x)[6]) {
-    const double h = tn - t[u];
+// Hermite predictor for the packed j-set (F32C): x + h v in FP64, the
+// higher-order terms h^2 (a/2 + h a'/6) and h (a + h a'/2) in FP32 from FP32
+// copies of a and a'.  They are small against the step's displacement, so
+// their FP32 rounding stays far below that of the packed FP32 offsets; FP64
+// operations, scarce on this part, drop from 24 to 15 per particle.
+__device__ __forceinline__ void predict_mixed(const BlockPackParams &q, int64_t u, double tn,
+                                              double (&x)[6]) {
+    const double h = tn - q.t[u];
+    const float hf = (float)h;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const int64_t q = d * n + u;
-        const double a = acc[q], j = jerk[q], v = vel[q];
-        x[d] = pos[q] + h * (v + h * (0.5 * a + h * (j * (1.0 / 6.0))));
-        x[3 + d] = v + h * (a + h * (0.5 * j));
+        const int64_t k = d * q.n + u;
+        const float a = q.af[k], j = q.jf[k];
+        const float dx = hf * hf * (0.5f * a + hf * (j * (1.0f / 6.0f)));
+        const float dv = hf * (a + hf * (0.5f * j));
+        const double v = q.vel[k];
+        x[d] = fma(h, v, q.pos[k]) + (double)dx;
+        x[3 + d] = v + (double)dv;
     }
 }
 
 constexpr int kPackMaxPer = 4;  // slots per thread in block_pack_kernel (tc <= 4 NT)
 
 // FP64 is scarce on this part (about 1/64 of the FP32 rate), so the tile
-// centre comes from an FP32 tree: the mean of the FP32-rounded predicted
-// positions (velocities), stored as a float (lo = 0).  Any centre near the tile
-// serves -- offsets are FP64 differences from it, rounded once to FP32 -- and
-// the mean keeps them small.
-template <int NT>
+// centre never needs an FP64 reduction.  After a re-sort (FRESH) it is the
+// mean of the FP32-rounded predicted positions (velocities); otherwise the
+// tile holds the same particles as at the previous pack, and the centre is
+// that pack's centre moved by the mean of its FP32 offsets (their mean
+// position then) -- FP32 data only.  Any centre near the tile serves: offsets
+// are FP64 differences from it, rounded once to FP32.  It is stored as a
+// float (lo = 0).  One CTA per tile, so the previous offsets are all read
+// before the CTA overwrites them.
+template <int NT, bool FRESH>
 __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q) {
     __shared__ float redf[NT / 32][8];
     __shared__ double cen[6];
@@ -1040,9 +1066,18 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
         const int slot = base + threadIdx.x + NT * r;
         if (r < per && slot - cl.slot_begin < cl.n) {
             const int64_t u = q.perm[slot];
-            predict_horner(q.n, u, tn, q.t, q.pos, q.vel, q.acc, q.jerk, x[r]);
+            predict_mixed(q, u, tn, x[r]);
+            if (FRESH) {
 #pragma unroll
-            for (int d = 0; d < 6; ++d) sf[d] += (float)x[r][d];
+                for (int d = 0; d < 6; ++d) sf[d] += (float)x[r][d];
+            } else {
+                sf[0] += q.px[slot];
+                sf[1] += q.py[slot];
+                sf[2] += q.pz[slot];
+                sf[3] += q.pvx[slot];
+                sf[4] += q.pvy[slot];
+                sf[5] += q.pvz[slot];
+            }
             sf[6] += 1.0f;
             act[r] = live && q.tq[u] == tnq;
             sf[7] += act[r] ? 1.0f : 0.0f;
@@ -1066,11 +1101,17 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
         }
         const float inv = sf[6] > 0.0f ? 1.0f / sf[6] : 0.0f;
         float h[6];
+        if (!FRESH) {
+            const float4 p0 = q.chl[2 * tile], v0 = q.vchl[2 * tile];
+            const float prev[6] = {p0.x, p0.y, p0.z, v0.x, v0.y, v0.z};
 #pragma unroll
-        for (int d = 0; d < 6; ++d) {
-            h[d] = sf[d] * inv;
-            cen[d] = (double)h[d];
+            for (int d = 0; d < 6; ++d) h[d] = prev[d] + sf[d] * inv;
+        } else {
+#pragma unroll
+            for (int d = 0; d < 6; ++d) h[d] = sf[d] * inv;
         }
+#pragma unroll
+        for (int d = 0; d < 6; ++d) cen[d] = (double)h[d];
         q.chl[2 * tile + 0] = make_float4(h[0], h[1], h[2], 0.0f);
         q.chl[2 * tile + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         q.vchl[2 * tile + 0] = make_float4(h[3], h[4], h[5], 0.0f);
@@ -1089,7 +1130,7 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
             q.px[slot] = (float)(x[r][0] - c[0]);
             q.py[slot] = (float)(x[r][1] - c[1]);
             q.pz[slot] = (float)(x[r][2] - c[2]);
-            q.pm[slot] = (float)q.mass[q.perm[slot]];
+            if (FRESH) q.pm[slot] = (float)q.mass[q.perm[slot]];  // else unchanged
             q.pvx[slot] = (float)(x[r][3] - c[3]);
             q.pvy[slot] = (float)(x[r][4] - c[4]);
             q.pvz[slot] = (float)(x[r][5] - c[5]);
@@ -1103,9 +1144,13 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
             q.flag[slot] = 0;
         }
     }
-    __threadfence();
+    // the last CTA reads only the tile counts (thread 0's writes); the packed
+    // data is for later kernels
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&q.sc->ticket_pack, 1) == (int)gridDim.x - 1;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&q.sc->ticket_pack, 1) == (int)gridDim.x - 1;
+    }
     __syncthreads();
     if (!last) return;
     __threadfence();
@@ -1292,6 +1337,13 @@ cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_block_shadow(int64_t n, const double *acc, const double *jerk, float *af, float *jf,
+                                cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    block_shadow_kernel<<<grid_of(3 * n, 256), 256, 0, s>>>(3 * n, acc, jerk, af, jf);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_block_levels(int64_t n, const double *dt, double dt_max, double dt_min,
                                 const Chunk *chunks, int n_chunks, const long long *tq, double *part,
                                 BlockScalars *sc, cudaStream_t s) {
@@ -1321,8 +1373,8 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
             return cudaErrorInvalidValue;
         BlockPackParams q{};
         q.perm = b.perm; q.cl = b.cl; q.tile_cluster = b.tile_cluster; q.tc = b.tc;
-        q.n_tiles = b.n_tiles; q.n = b.n; q.mass = b.mass; q.t = b.t; q.tq = b.tq;
-        q.pos = b.pos; q.vel = b.vel; q.acc = b.acc; q.jerk = b.jerk;
+        q.n_tiles = b.n_tiles; q.n = b.n; q.mass = b.mass; q.t = b.t; q.tq = b.tq; q.af = b.af; q.jf = b.jf;
+        q.pos = b.pos; q.vel = b.vel;
         q.px = b.px; q.py = b.py; q.pz = b.pz; q.pm = b.pm;
         q.pvx = b.pvx; q.pvy = b.pvy; q.pvz = b.pvz; q.chl = b.chl; q.vchl = b.vchl;
         q.flag = b.flag; q.tile_cnt = b.cnt; q.tile_off = b.chunk_off; q.tile_first = b.tile_first;
@@ -1333,8 +1385,13 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         q.partial_cap = b.partial_cap;
         q.dt_max = b.dt_max;
         q.dt_min = b.dt_min;
-        if (b.tc % 256 == 0) NB_BL((block_pack_kernel<256><<<b.n_tiles, 256, 0, s>>>(q)));
-        else NB_BL((block_pack_kernel<128><<<b.n_tiles, 128, 0, s>>>(q)));
+        if (b.tc % 256 == 0) {
+            if (b.fresh) NB_BL((block_pack_kernel<256, true><<<b.n_tiles, 256, 0, s>>>(q)));
+            else NB_BL((block_pack_kernel<256, false><<<b.n_tiles, 256, 0, s>>>(q)));
+        } else {
+            if (b.fresh) NB_BL((block_pack_kernel<128, true><<<b.n_tiles, 128, 0, s>>>(q)));
+            else NB_BL((block_pack_kernel<128, false><<<b.n_tiles, 128, 0, s>>>(q)));
+        }
     } else {
         NB_BL((block_predict_kernel<<<grid_of(b.n, 256), 256, 0, s>>>(
             b.n, b.sc, b.t, b.tq, b.pos, b.vel, b.acc, b.jerk, b.xp, b.vp, b.flag)));

@@ -76,6 +76,7 @@ struct BlockState {
     double *t = nullptr, *dt = nullptr, *part = nullptr, *partial = nullptr, *p1 = nullptr;
     double *few_part = nullptr;  // few-particle path: kFewCtas * kFewMax * 7
     long long *tq = nullptr;     // t_i + dt_i in units of dt_min
+    float *af = nullptr, *jf = nullptr;  // FP32 copies of a, a' (F32C packing predictor)
     uint8_t *flag = nullptr;
     int *cnt = nullptr, *chunk_off = nullptr, *act_begin = nullptr, *act_n = nullptr;
     int *ich_off = nullptr, *item_off = nullptr;
@@ -636,9 +637,10 @@ void free_jerk(nbody_ctx *ctx) {
 }
 
 nbody_tiles default_jerk_tiles(const nbody_ctx *c, bool block_steps = false) {
-    // block steps split j-ranges finely for small active sets: 256-wide j-tiles
-    // there (measured faster at N = 102 400), 512-wide for full evaluations
-    if (c->max_cluster >= 65536) return {256, 2, block_steps ? 256 : 512, 0, 1};
+    // block steps split j-ranges finely for small active sets and pack every
+    // particle each step: 256-wide j-tiles and 256-particle centre tiles there
+    // (measured faster at N = 102 400), 512-wide j-tiles for full evaluations
+    if (c->max_cluster >= 65536) return block_steps ? nbody_tiles{128, 2, 256, 0, 2} : nbody_tiles{256, 2, 512, 0, 1};
     if (c->max_cluster >= 8192) return {128, 2, 256, 0, 2};
     return {64, 2, 128, 0, 4};
 }
@@ -777,6 +779,8 @@ void free_block(nbody_ctx *ctx) {
     BlockState &b = ctx->bs;
     for (double **q : {&b.t, &b.dt, &b.part, &b.partial, &b.p1, &b.few_part}) dev_free(q);
     dev_free(&b.tq);
+    dev_free(&b.af);
+    dev_free(&b.jf);
     dev_free(&b.flag);
     for (int **q : {&b.cnt, &b.chunk_off, &b.act_begin, &b.act_n, &b.ich_off, &b.item_off}) dev_free(q);
     dev_free(&b.act);
@@ -843,6 +847,9 @@ int alloc_block(nbody_ctx *ctx) {
     for (double **q : {&b.t, &b.dt, &b.p1})
         if ((rc = dev_alloc(ctx, q, n))) return rc;
     if ((rc = dev_alloc(ctx, &b.tq, n))) return rc;
+    if (f32c)
+        for (float **q : {&b.af, &b.jf})
+            if ((rc = dev_alloc(ctx, q, 3 * n))) return rc;
     if ((rc = dev_alloc(ctx, &b.part, nc))) return rc;
     if ((rc = dev_alloc(ctx, &b.flag, nflag))) return rc;
     for (int **q : {&b.cnt, &b.chunk_off})
@@ -874,6 +881,8 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
     b.t = bs.t;
     b.dt = bs.dt;
     b.tq = bs.tq;
+    b.af = bs.af;
+    b.jf = bs.jf;
     b.dt_min = bs.dt_min;
     b.dt_max = bs.dt_max;
     b.part = bs.part;
@@ -921,7 +930,8 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
     if (ctx->n == 0) return NBODY_OK;
     BlockState &bs = ctx->bs;
     JerkPath &j = ctx->jp;
-    const BlockLaunch b = block_launch(ctx, a);
+    BlockLaunch b = block_launch(ctx, a);
+    b.fresh = reorder;
     int rc;
     if (ctx->mode == NBODY_F32C && reorder)
         NB_CUDA(launch_reorder(a.pos, ctx->n, ctx->chunks, ctx->n_chunks, ctx->chunk_first, ctx->ncl, j.dcl,
@@ -932,6 +942,8 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
     BlockCorrect corr{};
     corr.sc = bs.sc;
     corr.level = bs.sc->level;
+    corr.af = bs.af;  // null on the FP64 path
+    corr.jf = bs.jf;
     corr.t = bs.t;
     corr.dt = bs.dt;
     corr.tq = bs.tq;
@@ -1520,6 +1532,10 @@ int nbody_block_start(nbody_ctx *ctx, const double *pos, const double *vel, cons
     b.eta = eta;
     NB_CUDA(launch_block_init(ctx->n, acc, jerk, dt_max, dt_min, eta_s, b.t, b.dt, b.tq, s));
     NB_CUDA(cudaMemsetAsync(b.sc, 0, sizeof(BlockScalars), s));
+    if (b.af) {
+        NB_CUDA(launch_block_shadow(ctx->n, acc, jerk, b.af, b.jf, s));
+        ctx->launches += 1;
+    }
     // level counts and the first t_next (later steps set the next one themselves)
     NB_CUDA(launch_block_levels(ctx->n, b.dt, dt_max, dt_min, ctx->chunks, ctx->n_chunks, b.tq, b.part,
                                 b.sc, s));

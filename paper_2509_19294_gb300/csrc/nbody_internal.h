@@ -161,6 +161,7 @@ struct BlockScalars {
 struct BlockCorrect {
     const BlockScalars *sc;
     int *level;  // BlockScalars::level (the corrector moves particles between levels)
+    float *af, *jf;  // FP32 copies of a, a' (F32C packing predictor), or null
     double *t, *dt, *pos, *vel, *acc, *jerk, *pot;  // rows; acc, jerk: the particle's a0, j0
     long long *tq;
     int64_t n;
@@ -212,6 +213,8 @@ struct BlockLaunch {
     long long *tq;  // t_i + dt_i in units of dt_min (exact: steps are powers of two >= dt_min)
     double dt_min, dt_max;
     double *pos, *vel, *acc, *jerk, *xp, *vp;
+    const float *af, *jf;  // FP32 copies of a, a' (F32C)
+    bool fresh;            // the j-set was just re-sorted (tile centres from scratch)
     const double *mass;
     uint8_t *flag;  // per row (FP64) or per j-set slot (F32C)
     // per row chunk (FP64) or per centre tile (F32C): active counts, offsets
@@ -247,6 +250,9 @@ int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap);
 // Deterministic parallel sum of the subset kernel's split partials + epilogue.
 cudaError_t launch_subset_reduce(int max_chunks, int max_cs, int max_ctas, const F32CSubsetParams &prm,
                                  const SubItem *info, const BlockScalars *sc, cudaStream_t s);
+// FP32 copies of a, a' (start of block stepping, F32C).
+cudaError_t launch_block_shadow(int64_t n, const double *acc, const double *jerk, float *af, float *jf,
+                                cudaStream_t s);
 // Level counts of all particles and the first t_next (start of block stepping).
 cudaError_t launch_block_levels(int64_t n, const double *dt, double dt_max, double dt_min,
                                 const Chunk *chunks, int n_chunks, const long long *tq, double *part,
