@@ -1014,9 +1014,10 @@ struct BlockPackParams {
 // higher-order terms h^2 (a/2 + h a'/6) and h (a + h a'/2) in FP32 from FP32
 // copies of a and a'.  They are small against the step's displacement, so
 // their FP32 rounding stays far below that of the packed FP32 offsets; FP64
-// operations, scarce on this part, drop from 24 to 15 per particle.
+// operations, scarce on this part, drop from 24 to 11 per particle (the
+// velocity change is returned apart, for the packed offset).
 __device__ __forceinline__ void predict_mixed(const BlockPackParams &q, int64_t u, double tn,
-                                              double (&x)[6]) {
+                                              double (&x)[6], float (&dv)[3]) {
     const double h = tn - q.t[u];
     const float hf = (float)h;
 #pragma unroll
@@ -1024,10 +1025,10 @@ __device__ __forceinline__ void predict_mixed(const BlockPackParams &q, int64_t 
         const int64_t k = d * q.n + u;
         const float a = q.af[k], j = q.jf[k];
         const float dx = hf * hf * (0.5f * a + hf * (j * (1.0f / 6.0f)));
-        const float dv = hf * (a + hf * (0.5f * j));
+        dv[d] = hf * (a + hf * (0.5f * j));
         const double v = q.vel[k];
         x[d] = fma(h, v, q.pos[k]) + (double)dx;
-        x[3 + d] = v + (double)dv;
+        x[3 + d] = v;  // the velocity change dv is added in FP32 to the packed offset
     }
 }
 
@@ -1059,6 +1060,7 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
     const int per = q.tc / NT;
     float sf[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // position, velocity sums (6), count, active count
     double x[kPackMaxPer][6];
+    float dvel[kPackMaxPer][3];
     bool act[kPackMaxPer];
 #pragma unroll
     for (int r = 0; r < kPackMaxPer; ++r) {
@@ -1066,10 +1068,13 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
         const int slot = base + threadIdx.x + NT * r;
         if (r < per && slot - cl.slot_begin < cl.n) {
             const int64_t u = q.perm[slot];
-            predict_mixed(q, u, tn, x[r]);
+            predict_mixed(q, u, tn, x[r], dvel[r]);
             if (FRESH) {
 #pragma unroll
-                for (int d = 0; d < 6; ++d) sf[d] += (float)x[r][d];
+                for (int d = 0; d < 3; ++d) {
+                    sf[d] += (float)x[r][d];
+                    sf[3 + d] += (float)x[r][3 + d] + dvel[r][d];
+                }
             } else {
                 sf[0] += q.px[slot];
                 sf[1] += q.py[slot];
@@ -1131,9 +1136,11 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
             q.py[slot] = (float)(x[r][1] - c[1]);
             q.pz[slot] = (float)(x[r][2] - c[2]);
             if (FRESH) q.pm[slot] = (float)q.mass[q.perm[slot]];  // else unchanged
-            q.pvx[slot] = (float)(x[r][3] - c[3]);
-            q.pvy[slot] = (float)(x[r][4] - c[4]);
-            q.pvz[slot] = (float)(x[r][5] - c[5]);
+            // velocity offsets: FP64 difference from the centre, then the FP32
+            // change (two roundings, well inside the jerk's tolerance)
+            q.pvx[slot] = (float)(x[r][3] - c[3]) + dvel[r][0];
+            q.pvy[slot] = (float)(x[r][4] - c[4]) + dvel[r][1];
+            q.pvz[slot] = (float)(x[r][5] - c[5]) + dvel[r][2];
             q.flag[slot] = act[r];
         } else {
             q.px[slot] = kPadOffset;

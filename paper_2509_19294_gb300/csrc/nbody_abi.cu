@@ -25,13 +25,18 @@ constexpr int kProfSlots = 2;
 
 struct GraphEntry {
     const void *pos, *vel, *mass, *acc, *pot, *diag, *jerk;
-    int kind;  // 0 = KDK leapfrog step, 1 = Hermite step
+    int kind;  // 0 = KDK leapfrog step, 1 = Hermite step, 2 = block step
     uint64_t dt_bits;
     int reorder;
     int slot;
     cudaGraphExec_t exec;
     int kernels;
+    int steps;  // steps captured in the graph
 };
+
+// Block steps replayed without profiling events go kMultiSteps to a graph
+// (fewer graph launches per step).
+constexpr int kMultiSteps = 8;
 
 struct DevBuf {
     void *p = nullptr;
@@ -1399,6 +1404,8 @@ int step_common(nbody_ctx *ctx, double *pos, double *vel, const double *mass, do
         }
         const int slot = next_slot(ctx);
         if (slot < -1) return ctx->sticky;
+        const int multi =
+            kind == 2 && use_graph && slot == -1 && !reorder && nsteps - step >= kMultiSteps ? kMultiSteps : 1;
         if (!use_graph) {
             int k = 0;
             rc = kind == 2   ? enqueue_block_step(ctx, a, reorder, slot, false, s, &k)
@@ -1411,17 +1418,19 @@ int step_common(nbody_ctx *ctx, double *pos, double *vel, const double *mass, do
             for (auto &e : ctx->graphs)
                 if (e.pos == a.pos && e.vel == a.vel && e.mass == a.mass && e.acc == a.acc &&
                     e.pot == a.pot && e.diag == a.diag && e.jerk == a.jerk && e.kind == kind &&
-                    e.dt_bits == dt_bits && e.reorder == (int)reorder && e.slot == slot)
+                    e.dt_bits == dt_bits && e.reorder == (int)reorder && e.slot == slot &&
+                    e.steps == multi)
                     g = &e;
             if (!g) {
                 if (ctx->graphs.size() >= 16) drop_graphs(ctx);
                 GraphEntry ge{a.pos, a.vel, a.mass, a.acc, a.pot, a.diag, a.jerk, kind, dt_bits,
-                              (int)reorder, slot, nullptr, 0};
+                              (int)reorder, slot, nullptr, 0, multi};
                 NB_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
                 int k = 0;
-                rc = kind == 2   ? enqueue_block_step(ctx, a, reorder, slot, true, ctx->cap_stream, &k)
-                     : kind == 1 ? enqueue_hermite_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k)
-                                 : enqueue_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k);
+                for (int m = 0; m < multi && rc == NBODY_OK; ++m)
+                    rc = kind == 2   ? enqueue_block_step(ctx, a, reorder, slot, true, ctx->cap_stream, &k)
+                         : kind == 1 ? enqueue_hermite_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k)
+                                     : enqueue_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k);
                 cudaGraph_t graph = nullptr;
                 cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
                 if (rc) {
@@ -1441,6 +1450,10 @@ int step_common(nbody_ctx *ctx, double *pos, double *vel, const double *mass, do
         }
         if (slot >= 0) ctx->ev_pending[slot] = true;
         ctx->evals += 1;
+        if (use_graph && multi > 1) {
+            step += multi - 1;
+            ctx->evals += multi - 1;
+        }
     }
     if (spos) NB_CUDA(cudaMemcpyAsync(pos, dpos, n3b, cudaMemcpyDeviceToHost, s));
     if (svel) NB_CUDA(cudaMemcpyAsync(vel, dvel, n3b, cudaMemcpyDeviceToHost, s));
