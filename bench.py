@@ -520,7 +520,8 @@ def run_ours(args):
         ensemble["step_frac"] = ensemble["value"] / 1e9 / peak
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+        "ms_per_step_median": float(np.median(step_ms)), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(n),
                    "n": n, "eps": EPS, "dt": DT, "seed": SEED,
@@ -591,7 +592,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
