@@ -43,6 +43,30 @@ __device__ __forceinline__ double recip_pow2(double h) {
     return 1.0 / h;
 }
 
+// Next step of particle i after a step h, by Aarseth's criterion from the
+// norms of the acceleration and its first three derivatives at the end of the
+// step: halved while above it (not below dt_min), doubled once when allowed
+// (<= dt_max, <= the criterion, and t_next a multiple of the doubled step --
+// an integer test in units of dt_min).  Records the particle's new time, step
+// and level.
+__device__ __forceinline__ void choose_step(const BlockCorrect &c, int64_t i, double h, double na,
+                                            double nj, double n2, double n3, double tn, long long tnq) {
+    const double den = nj * n3 + n2 * n2;
+    const double da = den > 0.0 ? sqrt(c.eta * (na * n2 + nj * nj) / den) : c.dt_max;
+    const double inv_dt_min = recip_pow2(c.dt_min);
+    double nd = h;
+    while (nd > da && nd > c.dt_min) nd *= 0.5;
+    const long long q2 = (long long)(2.0 * h * inv_dt_min);  // 2h in units of dt_min
+    if (nd == h && da >= 2.0 * h && 2.0 * h <= c.dt_max && tnq % q2 == 0) nd = 2.0 * h;
+    if (c.level && nd != h) {
+        atomicSub(&c.level[block_level(h, c.dt_max)], 1);
+        atomicAdd(&c.level[block_level(nd, c.dt_max)], 1);
+    }
+    c.t[i] = tn;
+    c.dt[i] = nd;
+    c.tq[i] = tnq + (long long)(nd * inv_dt_min);
+}
+
 // Hermite corrector of active particle (row) i over its step h = dt_i with the
 // new acceleration A1, jerk J1 and potential p1, then its next step by
 // Aarseth's criterion.  Steps are powers of two >= dt_min and t_next is a
@@ -76,20 +100,7 @@ __device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t 
     const double nj = sqrt(J1[0] * J1[0] + J1[1] * J1[1] + J1[2] * J1[2]);
     const double n2 = sqrt(A2[0] * A2[0] + A2[1] * A2[1] + A2[2] * A2[2]);
     const double n3 = sqrt(A3[0] * A3[0] + A3[1] * A3[1] + A3[2] * A3[2]);
-    const double den = nj * n3 + n2 * n2;
-    const double da = den > 0.0 ? sqrt(c.eta * (na * n2 + nj * nj) / den) : c.dt_max;
-    const double inv_dt_min = recip_pow2(c.dt_min);
-    double nd = h;
-    while (nd > da && nd > c.dt_min) nd *= 0.5;
-    const long long q2 = (long long)(2.0 * h * inv_dt_min);  // 2h in units of dt_min
-    if (nd == h && da >= 2.0 * h && 2.0 * h <= c.dt_max && tnq % q2 == 0) nd = 2.0 * h;
-    if (c.level && nd != h) {
-        atomicSub(&c.level[block_level(h, c.dt_max)], 1);
-        atomicAdd(&c.level[block_level(nd, c.dt_max)], 1);
-    }
-    c.t[i] = tn;
-    c.dt[i] = nd;
-    c.tq[i] = tnq + (long long)(nd * inv_dt_min);
+    choose_step(c, i, h, na, nj, n2, n3, tn, tnq);
 }
 
 // correct_particle spread over four consecutive lanes of a warp: lane sub
@@ -135,21 +146,7 @@ __device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64
     }
     if (sub != 0 || !valid) return;
     if (c.pot) c.pot[i] = p1;
-    const double na = nrm[0], nj = nrm[1], n2 = nrm[2], n3 = nrm[3];
-    const double den = nj * n3 + n2 * n2;
-    const double da = den > 0.0 ? sqrt(c.eta * (na * n2 + nj * nj) / den) : c.dt_max;
-    const double inv_dt_min = recip_pow2(c.dt_min);
-    double nd = h;
-    while (nd > da && nd > c.dt_min) nd *= 0.5;
-    const long long q2 = (long long)(2.0 * h * inv_dt_min);
-    if (nd == h && da >= 2.0 * h && 2.0 * h <= c.dt_max && tnq % q2 == 0) nd = 2.0 * h;
-    if (c.level && nd != h) {
-        atomicSub(&c.level[block_level(h, c.dt_max)], 1);
-        atomicAdd(&c.level[block_level(nd, c.dt_max)], 1);
-    }
-    c.t[i] = tn;
-    c.dt[i] = nd;
-    c.tq[i] = tnq + (long long)(nd * inv_dt_min);
+    choose_step(c, i, h, nrm[0], nrm[1], nrm[2], nrm[3], tn, tnq);
 }
 
 // FP64 epilogue of one active particle: scale by G, remove the self term of
