@@ -15,7 +15,7 @@ no fast-math).  This module only builds it and marshals numpy arrays:
   integration in double precision on the host, Sec. 3).
 * ``energy``       -- K, W, E, P, L.
 * ``forces_jerk``  -- a_i, its time derivative (jerk) and phi_i, which the paper
-  computes together (Sec. 3).
+  computes together (Sec. 3); ``forces_jerk_rows`` for a subset of rows.
 * ``hermite``      -- the fourth-order Hermite predictor-corrector integrator
   that uses the jerk (shared time step).
 * ``block_hermite`` -- the same scheme with individual power-of-two block time
@@ -86,6 +86,8 @@ class Oracle:
         lib.oracle_kdk.restype = None
         lib.oracle_forces_jerk.argtypes = [i64, vp, vp, vp, d, d, vp, vp, vp]
         lib.oracle_forces_jerk.restype = None
+        lib.oracle_forces_jerk_rows.argtypes = [i64, vp, vp, vp, d, d, vp, i64, vp, vp, vp]
+        lib.oracle_forces_jerk_rows.restype = None
         lib.oracle_hermite.argtypes = [i64, vp, vp, vp, d, d, d, i64, vp, vp, vp, ctypes.c_int, vp]
         lib.oracle_hermite.restype = None
         lib.oracle_block_hermite.argtypes = [i64, vp, vp, vp, d, d, d, d, d, d, d, vp, vp, vp, vp,
@@ -170,6 +172,22 @@ def _forces_jerk(self, pos, vel, mass, eps: float, G: float = 1.0):
     return acc, jerk, pot
 
 
+def _forces_jerk_rows(self, pos, vel, mass, eps: float, rows, G: float = 1.0):
+    """Return (acc[3, k], jerk[3, k], pot[k]) in FP64 for the given rows."""
+    mass = _c(mass)
+    n = mass.shape[0]
+    pos = _c(pos, (3, n))
+    vel = _c(vel, (3, n))
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    k = rows.shape[0]
+    acc = np.empty((3, k), np.float64)
+    jerk = np.empty((3, k), np.float64)
+    pot = np.empty(k, np.float64)
+    self.lib.oracle_forces_jerk_rows(n, _p(pos), _p(vel), _p(mass), float(eps), float(G), _p(rows), k,
+                                     _p(acc), _p(jerk), _p(pot))
+    return acc, jerk, pot
+
+
 def _hermite(self, pos, vel, mass, eps: float, dt: float, nsteps: int, G: float = 1.0,
              diag: bool = False):
     """Advance copies of (pos, vel) by ``nsteps`` Hermite steps.
@@ -211,6 +229,7 @@ def _block_hermite(self, pos, vel, mass, eps: float, t_end: float, dt_max: float
 
 Oracle.block_hermite = _block_hermite
 Oracle.forces_jerk = _forces_jerk
+Oracle.forces_jerk_rows = _forces_jerk_rows
 Oracle.hermite = _hermite
 
 

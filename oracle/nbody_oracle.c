@@ -244,6 +244,22 @@ void oracle_forces_jerk(int64_t n, const double *pos, const double *vel, const d
     }
 }
 
+/* The same for rows[0..k): acc, jerk [3][k], pot [k] (sampled checks at large n). */
+void oracle_forces_jerk_rows(int64_t n, const double *pos, const double *vel, const double *mass,
+                             double eps, double G, const int64_t *rows, int64_t k, double *acc,
+                             double *jerk, double *pot) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < k; ++r) {
+        double o[7];
+        oracle_one_jerk(n, pos, vel, mass, eps, G, rows[r], o);
+        for (int d = 0; d < 3; ++d) {
+            acc[d * k + r] = o[d];
+            jerk[d * k + r] = o[3 + d];
+        }
+        pot[r] = o[6];
+    }
+}
+
 /*
  * nsteps Hermite steps in place on pos and vel; acc/jerk/pot as in oracle_kdk
  * (computed first unless have != 0), diag as in oracle_kdk.

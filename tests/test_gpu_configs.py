@@ -12,6 +12,9 @@ C4  512 clusters, N_c ~ U{256..8192}, eps_c = 0.01 N_c^(-1/3): every cluster's
 C5  two Plummer spheres of 524288 on a head-on approach, eps=1e-3: sampled rows
     of the full-size launch (the configuration bench.py times) against the
     oracle row by row.
+Paper scale (N=102400, the paper's particle count): acceleration, jerk and
+    potential of the launch configuration bench.py times, sampled rows against
+    the oracle; the block-step workload's state after its first dt_max.
 
 FP32C tolerance: per-particle relative acceleration error median <= 1e-6 and
 max <= 1e-4, potential likewise, and the paper's 0.05 % bound (each component
@@ -152,6 +155,55 @@ def test_c5_full_size_sampled_rows(oracle):
         ph = host(p)
         ra, rp = oracle.forces_rows(ph, mass, 1e-3, rows)
         check_f32c(host(acc)[:, rows], host(pot)[rows], ra, rp)
+
+
+def test_paper_scale_jerk_full_size_sampled_rows(oracle):
+    # the paper's N with the configuration bench.py's paper-scale section times
+    # (default 512-wide j-tiles from 65 536 particles), rows against the oracle
+    n = 102400
+    pos, vel, mass = ic.plummer(n, seed=6)
+    with nb.nbody_init(n, 1e-3, reorder_every=1) as ctx:
+        assert nb.nbody_get_jerk_tiles(ctx) == (0, 0, 0, 0, 0)   # built on first use
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        jerk = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        pot = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_forces_jerk(ctx, p, v, m, acc, jerk, pot)
+        assert nb.nbody_get_jerk_tiles(ctx)[2] == 512
+        rows = ic.sample_rows(n, 512, 78)
+        ra, rj, rp = oracle.forces_jerk_rows(pos, vel, mass, 1e-3, rows)
+        check_f32c(host(acc)[:, rows], host(pot)[rows], ra, rp)
+        s = metrics.summary(host(jerk)[:, rows], rj)
+        assert s["median"] <= 1e-5, s
+        assert metrics.paper_metric(host(jerk)[:, rows], rj) <= 2e-3
+
+
+def test_block_steps_full_size_synchronised_state(oracle):
+    # bench.py's block-step workload over its first dt_max: every particle
+    # ends at t_end with a power-of-two step, and its stored acceleration and
+    # jerk (taken at its last predicted state) agree with a fresh oracle
+    # evaluation at the final state to the last correction's O(dt^4) plus the
+    # F32C error
+    n = 102400
+    pos, vel, mass = ic.plummer(n, seed=7)
+    dt_max, dt_min = 2.0 ** -7, 2.0 ** -22
+    with nb.nbody_init(n, 1e-3, reorder_every=4) as ctx:
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        jerk = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        pot = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_block_start(ctx, p, v, m, acc, jerk, pot, dt_max, dt_min, 0.02, 0.01)
+        blocks, evals = nb.nbody_block_advance(ctx, p, v, m, acc, jerk, pot, dt_max)
+        t, dt = nb.nbody_block_state(ctx)
+    assert blocks > 10 and n <= evals < blocks * n
+    assert np.all(t == dt_max)
+    lg = np.log2(dt)
+    assert np.all(lg == np.round(lg)) and dt.max() <= dt_max and dt.min() >= dt_min
+    rows = ic.sample_rows(n, 256, 79)
+    ra, rj, rp = oracle.forces_jerk_rows(host(p), host(v), mass, 1e-3, rows)
+    s = metrics.summary(host(acc)[:, rows], ra)
+    assert s["median"] <= 1e-6 and s["max"] <= 1e-4, s
+    assert metrics.summary(host(jerk)[:, rows], rj)["median"] <= 1e-4
 
 
 def test_measured_pipe_rates_are_plausible():

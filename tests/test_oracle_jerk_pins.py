@@ -100,3 +100,17 @@ def test_hermite_is_fourth_order(oracle):
     assert 13.0 < ratio < 19.0, ratio
     assert err2 < 1e-6
     assert np.abs(dg[:, 2] - (-0.3 * 0.7 / 2.0)).max() < 1e-7
+
+
+def test_rows_variant_indexes_the_same_evaluation(oracle):
+    # the sampled-row form (used at full size) returns exactly the full
+    # evaluation's values at those rows, in the order asked
+    rng = np.random.default_rng(77)
+    n = 40
+    pos, vel = rng.normal(size=(3, n)), rng.normal(size=(3, n))
+    mass = rng.uniform(0.5, 1.5, n) / n
+    a, j, p = oracle.forces_jerk(pos, vel, mass, 0.05)
+    rows = np.array([7, 0, 39, 7, 21])
+    ar, jr, pr = oracle.forces_jerk_rows(pos, vel, mass, 0.05, rows)
+    assert np.array_equal(ar, a[:, rows]) and np.array_equal(jr, j[:, rows])
+    assert np.array_equal(pr, p[rows])
