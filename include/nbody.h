@@ -192,8 +192,13 @@ int nbody_step_hermite(nbody_ctx *ctx, double *pos, double *vel, const double *m
  *     dt = sqrt(eta (|a| |a''| + |a'|^2) / (|a'| |a'''| + |a''|^2)),
  * halving it until below that value (not below dt_min) or doubling it when
  * allowed (<= dt_max, t_next a multiple of the doubled step).  The schedule
- * (min, compaction of the active set, work queue) runs on the device, so each
- * block step is one replayed CUDA graph.
+ * (the next block time -- the next multiple of the smallest occupied step --,
+ * compaction of the active set, work queue) runs on the device, so block steps
+ * are replayed CUDA graphs (eight steps to a graph unless NBODY_FLAG_PROFILE
+ * records per-step events); the host checks progress every 16-256 steps.
+ * With NBODY_F32C the predicted j-set is packed as FP32 offsets (position and
+ * velocity corrections over the prediction interval in FP32); with NBODY_F64
+ * every pair is FP64 and the step decisions equal the FP64 oracle's.
  *
  * nbody_block_start: computes a, jerk, pot at the current state (t = 0) and the
  *   initial steps, the largest power of two <= min(dt_max, eta_s |a|/|a'|),
@@ -203,7 +208,9 @@ int nbody_step_hermite(nbody_ctx *ctx, double *pos, double *vel, const double *m
  *   were set (nbody_set_jerk_tiles) or built by an earlier jerk call, it picks
  *   a tile shape suited to block steps (narrower j-tiles for large N).
  * nbody_block_advance: block steps until every particle reaches t_end (a
- *   multiple of dt_max, so all particles are synchronised there); *blocks and
+ *   multiple of dt_max, so all particles are synchronised there; a batch may
+ *   run a few steps past it, which find no active particle and change
+ *   nothing); *blocks and
  *   *evals (may be NULL) receive the totals since nbody_block_start.  Pass the
  *   same arrays as to nbody_block_start; acc/jerk/pot hold each particle's last
  *   corrector values (taken at its last predicted state).
