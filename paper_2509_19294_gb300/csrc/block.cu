@@ -13,9 +13,10 @@
 //      j-set (the jerk path's geometry), flag and count the active slots per
 //      tile; the last CTA plans the step (offsets, regime, split, queue size)
 //   3. block_queue_kernel: ordered compaction of the active slots, work items
-//   4. the force pass, one of: subset_few_kernel (<= kFewMax active), the
-//      small-set or the large-set subset kernel; split j-ranges summed by
-//      subset_reduce_kernel
+//   4. the force pass: the small-set and the large-set subset kernels, then
+//      subset_tail_kernel, which either runs the few-particle pass (<= kFewMax
+//      active; the subset kernels then find an empty queue) or sums the
+//      subset kernels' split partials in order
 //   5. the Hermite corrector and next-step choice, in the epilogue of 4
 // An active particle is evaluated with its own j-set offset and its own tile
 // centre: per j-tile each thread forms the exact centre difference for each of
@@ -177,7 +178,7 @@ __device__ __forceinline__ void subset_finalize(const F32CJerkParams &p, const B
 // each takes one G-th of every shared-memory j-tile, so a small active set
 // still keeps G times more warps busy.  The groups' Kahan sums are added in
 // group order (FP64, shared memory); a j-range split is written as an FP64
-// partial that subset_reduce_kernel sums in split order.
+// partial that subset_tail_kernel sums in split order.
 template <int BLOCK, int P, int TJ, int G, bool EPS_ZERO>
 struct SubsetKernel {
     using JK = F32CJerkKernel<BLOCK, P, TJ, EPS_ZERO>;
@@ -374,9 +375,9 @@ constexpr int kFewThreads = 256;
 constexpr int kFewBatch = 8;
 constexpr int kFewUnroll = 2;
 
-__global__ void __launch_bounds__(kFewThreads)
-    subset_few_kernel(const F32CSubsetParams q, const int32_t *__restrict__ act, BlockScalars *sc,
-                      double *__restrict__ part) {
+__device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ act, BlockScalars *sc,
+                         double *__restrict__ part) {
+    constexpr int nctas = kFewCtas;  // the CTAs taking part: blockIdx.x < kFewCtas
     const F32CJerkParams &p = q.base;
     __shared__ float own[kFewMax][6];
     __shared__ float4 oc[kFewMax][4];
@@ -421,7 +422,7 @@ __global__ void __launch_bounds__(kFewThreads)
     __syncthreads();
     const int jtot = fjb[nf];
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-    const int stride = gridDim.x * kFewThreads;
+    const int stride = nctas * kFewThreads;
     for (int b0 = 0; b0 < na; b0 += kFewBatch) {
         float acc[kFewBatch][7];
 #pragma unroll
@@ -527,7 +528,7 @@ __global__ void __launch_bounds__(kFewThreads)
     for (int t = threadIdx.x; t < na * 7; t += blockDim.x) mine[t] = csum[t / 7][t % 7];
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&sc->ticket_few, 1) == (int)gridDim.x - 1;
+    if (threadIdx.x == 0) last = atomicAdd(&sc->ticket_few, 1) == nctas - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
@@ -536,11 +537,11 @@ __global__ void __launch_bounds__(kFewThreads)
     // group sums are added in group order
     {
         const int n_out = na * 7;
-        const int ngrp = min(kFewThreads / n_out, (int)gridDim.x);
+        const int ngrp = min(kFewThreads / n_out, nctas);
         const int o = threadIdx.x % n_out, grp = threadIdx.x / n_out;
         if (grp < ngrp) {
-            const int b0 = (int)((long long)grp * gridDim.x / ngrp);
-            const int b1 = (int)((long long)(grp + 1) * gridDim.x / ngrp);
+            const int b0 = (int)((long long)grp * nctas / ngrp);
+            const int b1 = (int)((long long)(grp + 1) * nctas / ngrp);
             double v = 0.0;
             for (int b = b0; b < b1; b += 8) {
                 double x[8];
@@ -594,9 +595,8 @@ __global__ void __launch_bounds__(kFewThreads)
 // (nsplit, particle), so the result does not depend on scheduling.
 constexpr int kReduceWarps = 8;
 
-__global__ void __launch_bounds__(32 * kReduceWarps)
-subset_reduce_kernel(const F32CSubsetParams q, const SubItem *__restrict__ info,
-                     const BlockScalars *__restrict__ sc) {
+__device__ void reduce_pass(const F32CSubsetParams &q, const SubItem *__restrict__ info,
+                            const BlockScalars *__restrict__ sc) {
     const int cs = sc->cs;
     __shared__ double part[kReduceWarps][7][32];
     const int subs = (cs + 31) / 32;
@@ -632,6 +632,22 @@ subset_reduce_kernel(const F32CSubsetParams q, const SubItem *__restrict__ info,
         }
         __syncthreads();
     }
+}
+
+// The force pass's last kernel: the few-particle pass when the plan chose it
+// (on kFewCtas CTAs), else the ordered sum of the subset kernels' split
+// partials.  One launch for either, after the subset kernels (which find an
+// empty queue in the few-particle case).
+static_assert(kFewThreads == 32 * kReduceWarps, "one block size for both passes");
+
+__global__ void __launch_bounds__(kFewThreads)
+    subset_tail_kernel(const F32CSubsetParams q, const int32_t *__restrict__ act, BlockScalars *sc,
+                       double *__restrict__ few_part, const SubItem *__restrict__ info) {
+    if (sc->few) {  // uniform
+        if ((int)blockIdx.x < kFewCtas) few_pass(q, act, sc, few_part);
+        return;
+    }
+    reduce_pass(q, info, sc);
 }
 
 struct SubsetShape {
@@ -1315,12 +1331,12 @@ int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap) 
     return n;
 }
 
-cudaError_t launch_subset_reduce(int max_chunks, int max_cs, int max_ctas, const F32CSubsetParams &prm,
-                                 const SubItem *info, const BlockScalars *sc, cudaStream_t s) {
+cudaError_t launch_subset_tail(int max_chunks, int max_cs, int max_ctas, const F32CSubsetParams &prm,
+                               const int32_t *act, BlockScalars *sc, double *few_part, const SubItem *info,
+                               cudaStream_t s) {
     const int64_t units = (int64_t)max_chunks * ((max_cs + 31) / 32);
-    if (units <= 0) return cudaSuccess;
-    const int grid = (int)std::min<int64_t>(units, max_ctas);
-    subset_reduce_kernel<<<grid, 32 * kReduceWarps, 0, s>>>(prm, info, sc);
+    const int grid = (int)std::max<int64_t>(kFewCtas, std::min<int64_t>(units, max_ctas));
+    subset_tail_kernel<<<grid, kFewThreads, 0, s>>>(prm, act, sc, few_part, info);
     return cudaGetLastError();
 }
 
@@ -1428,11 +1444,6 @@ cudaError_t launch_block_queue(const BlockLaunch &b, cudaStream_t s, int *kernel
 }
 #undef NB_BL
 
-cudaError_t launch_subset_few(const F32CSubsetParams &prm, const int32_t *act, BlockScalars *sc,
-                              double *part, cudaStream_t s) {
-    subset_few_kernel<<<kFewCtas, kFewThreads, 0, s>>>(prm, act, sc, part);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_subset_f32c(int block, int p, int tj, int groups, int minb, bool eps_zero,
                                int grid, const F32CSubsetParams &prm, cudaStream_t st) {

@@ -962,7 +962,8 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
     corr.dt_min = bs.dt_min;
     corr.eta = bs.eta;
     if (ctx->mode == NBODY_F32C) {
-        // the force kernels' epilogues apply the corrector (no separate pass)
+        // the force kernels' epilogues apply the corrector (no separate pass);
+        // the large-set kernel gets its own queue head
         F32CSubsetParams q{};
         q.base = jerk_params(ctx, j.a1, j.j1, bs.p1);
         q.corr = corr;
@@ -972,7 +973,6 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
         q.partial = bs.partial;
         q.tcj = j.tc;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
-        NB_CUDA(launch_subset_few(q, bs.act, bs.sc, bs.few_part, s));
         q.n_items = &bs.sc->n_items_small;
         NB_CUDA(launch_subset_f32c(bs.sub.block, bs.sub.p, bs.sub.tj, bs.sub.split,
                                    bs.sub.ctas_per_sm, ctx->eps_zero, bs.workers, q, s));
@@ -980,9 +980,10 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
         q.base.counters = j.counters + 1;  // its own queue head
         NB_CUDA(launch_subset_f32c(bs.sub_large.block, bs.sub_large.p, bs.sub_large.tj, bs.sub_large.split,
                                    bs.sub_large.ctas_per_sm, ctx->eps_zero, bs.workers_large, q, s));
-        NB_CUDA(launch_subset_reduce(bs.max_chunks, std::max(bs.cs, bs.cs_large), 4 * ctx->sms, q, bs.info,
-                                     bs.sc, s));
-        *kernels += 4;
+        // few-particle pass or split-partial sum, whichever the plan chose
+        NB_CUDA(launch_subset_tail(bs.max_chunks, std::max(bs.cs, bs.cs_large), 4 * ctx->sms, q, bs.act, bs.sc,
+                                   bs.few_part, bs.info, s));
+        *kernels += 3;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
     } else {
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;

@@ -247,9 +247,14 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
 cudaError_t launch_block_queue(const BlockLaunch &b, cudaStream_t s, int *kernels);
 int subset_occupancy(int block, int p, int tj, int groups, int minb, bool eps_zero);
 int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap);
-// Deterministic parallel sum of the subset kernel's split partials + epilogue.
-cudaError_t launch_subset_reduce(int max_chunks, int max_cs, int max_ctas, const F32CSubsetParams &prm,
-                                 const SubItem *info, const BlockScalars *sc, cudaStream_t s);
+// The force pass's last kernel: the few-particle pass (all j of the active
+// clusters in parallel, FP64 partials per CTA in few_part: kFewCtas * kFewMax
+// * 7 doubles, summed in order by the last CTA) when the plan chose it, else
+// the deterministic parallel sum of the subset kernels' split partials; both
+// apply the epilogue and the corrector.
+cudaError_t launch_subset_tail(int max_chunks, int max_cs, int max_ctas, const F32CSubsetParams &prm,
+                               const int32_t *act, BlockScalars *sc, double *few_part, const SubItem *info,
+                               cudaStream_t s);
 // FP32 copies of a, a' (start of block stepping, F32C).
 cudaError_t launch_block_shadow(int64_t n, const double *acc, const double *jerk, float *af, float *jf,
                                 cudaStream_t s);
@@ -257,10 +262,6 @@ cudaError_t launch_block_shadow(int64_t n, const double *acc, const double *jerk
 cudaError_t launch_block_levels(int64_t n, const double *dt, double dt_max, double dt_min,
                                 const Chunk *chunks, int n_chunks, const long long *tq, double *part,
                                 BlockScalars *sc, cudaStream_t s);
-// Few-particle path: all j of the active clusters in parallel, FP64 partials per
-// CTA (part: kFewCtas * kFewMax * 7 doubles) summed in order by the last CTA.
-cudaError_t launch_subset_few(const F32CSubsetParams &prm, const int32_t *act, BlockScalars *sc,
-                              double *part, cudaStream_t s);
 // block * groups threads per CTA (see SubsetKernel in block.cu).
 cudaError_t launch_subset_f32c(int block, int p, int tj, int groups, int minb, bool eps_zero,
                                int grid, const F32CSubsetParams &prm, cudaStream_t s);
