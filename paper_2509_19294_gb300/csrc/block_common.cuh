@@ -1,0 +1,161 @@
+// block_common.cuh -- device helpers shared by the block-step kernels
+// (block_sched.cu, block_force.cu): the Hermite corrector, the step choice and
+// the epilogue of an active particle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "forces_f32c.cuh"
+#include "nbody_internal.h"
+
+namespace nbody {
+
+// Grid for a grid-stride loop over `work` items (capped; the loops cover the rest).
+inline int grid_of(int64_t work, int threads) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+
+// 1/h, exact for a power of two h (built from its exponent; FP64 division is
+// slow on this part), else the division.
+__device__ __forceinline__ double recip_pow2(double h) {
+    const long long b = __double_as_longlong(h);
+    if ((b & 0x000FFFFFFFFFFFFFLL) == 0 && b > 0 && b < 0x7FE0000000000000LL)
+        return __longlong_as_double(0x7FE0000000000000LL - b);
+    return 1.0 / h;
+}
+
+// Next step of particle i after a step h, by Aarseth's criterion from the
+// norms of the acceleration and its first three derivatives at the end of the
+// step: halved while above it (not below dt_min), doubled once when allowed
+// (<= dt_max, <= the criterion, and t_next a multiple of the doubled step --
+// an integer test in units of dt_min).  Records the particle's new time, step
+// and level.
+__device__ __forceinline__ void choose_step(const BlockCorrect &c, int64_t i, double h, double na,
+                                            double nj, double n2, double n3, double tn, long long tnq) {
+    const double den = nj * n3 + n2 * n2;
+    const double da = den > 0.0 ? sqrt(c.eta * (na * n2 + nj * nj) / den) : c.dt_max;
+    const double inv_dt_min = recip_pow2(c.dt_min);
+    double nd = h;
+    while (nd > da && nd > c.dt_min) nd *= 0.5;
+    const long long q2 = (long long)(2.0 * h * inv_dt_min);  // 2h in units of dt_min
+    if (nd == h && da >= 2.0 * h && 2.0 * h <= c.dt_max && tnq % q2 == 0) nd = 2.0 * h;
+    if (c.level && nd != h) {
+        atomicSub(&c.level[block_level(h, c.dt_max)], 1);
+        atomicAdd(&c.level[block_level(nd, c.dt_max)], 1);
+    }
+    c.t[i] = tn;
+    c.dt[i] = nd;
+    c.tq[i] = tnq + (long long)(nd * inv_dt_min);
+}
+
+// Hermite corrector of active particle (row) i over its step h = dt_i with the
+// new acceleration A1, jerk J1 and potential p1, then its next step by
+// Aarseth's criterion.  Steps are powers of two >= dt_min and t_next is a
+// multiple of dt_min, so dividing by h, h^2, h^3 is the exact multiplication
+// by their reciprocals and "t_next is a multiple of 2h" is an integer test;
+// both give the oracle's results bit for bit.
+__device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t i, const double (&A1)[3],
+                                                 const double (&J1)[3], double p1, double tn,
+                                                 long long tnq) {
+    const double h = c.dt[i], h2 = h * h;
+    const double ih = recip_pow2(h), ih2 = ih * ih, ih3 = ih2 * ih;
+    double A2[3], A3[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int64_t q = d * c.n + i;
+        const double a0 = c.acc[q], j0 = c.jerk[q], v0 = c.vel[q];
+        const double v1 = v0 + (a0 + A1[d]) * h / 2.0 + (j0 - J1[d]) * h2 / 12.0;
+        c.pos[q] = c.pos[q] + (v0 + v1) * h / 2.0 + (a0 - A1[d]) * h2 / 12.0;
+        c.vel[q] = v1;
+        A3[d] = (12.0 * (a0 - A1[d]) + 6.0 * h * (j0 + J1[d])) * ih3;
+        A2[d] = (-6.0 * (a0 - A1[d]) - h * (4.0 * j0 + 2.0 * J1[d])) * ih2 + h * A3[d];
+        c.acc[q] = A1[d];
+        c.jerk[q] = J1[d];
+        if (c.af) {
+            c.af[q] = (float)A1[d];
+            c.jf[q] = (float)J1[d];
+        }
+    }
+    if (c.pot) c.pot[i] = p1;
+    const double na = sqrt(A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2]);
+    const double nj = sqrt(J1[0] * J1[0] + J1[1] * J1[1] + J1[2] * J1[2]);
+    const double n2 = sqrt(A2[0] * A2[0] + A2[1] * A2[1] + A2[2] * A2[2]);
+    const double n3 = sqrt(A3[0] * A3[0] + A3[1] * A3[1] + A3[2] * A3[2]);
+    choose_step(c, i, h, na, nj, n2, n3, tn, tnq);
+}
+
+// correct_particle spread over four consecutive lanes of a warp: lane sub
+// (0..2) corrects component sub, the norms are summed across the three lanes
+// in component order, and lane 0 chooses the step.  Every lane of the warp
+// calls it (the shuffles need them); lanes with valid == false store nothing.
+__device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64_t i, bool valid, int sub,
+                                                    double a1, double j1, double p1, double tn,
+                                                    long long tnq) {
+    const double h = c.dt[i], h2 = h * h;
+    const double ih = recip_pow2(h), ih2 = ih * ih, ih3 = ih2 * ih;
+    double sq[4] = {0.0, 0.0, 0.0, 0.0};  // this component's a1^2, j1^2, a2^2, a3^2
+    if (sub < 3) {
+        const int64_t q = sub * c.n + i;
+        const double a0 = c.acc[q], j0 = c.jerk[q], v0 = c.vel[q];
+        const double v1 = v0 + (a0 + a1) * h / 2.0 + (j0 - j1) * h2 / 12.0;
+        const double x1 = c.pos[q] + (v0 + v1) * h / 2.0 + (a0 - a1) * h2 / 12.0;
+        const double a3 = (12.0 * (a0 - a1) + 6.0 * h * (j0 + j1)) * ih3;
+        const double a2 = (-6.0 * (a0 - a1) - h * (4.0 * j0 + 2.0 * j1)) * ih2 + h * a3;
+        if (valid) {
+            c.pos[q] = x1;
+            c.vel[q] = v1;
+            c.acc[q] = a1;
+            c.jerk[q] = j1;
+            if (c.af) {
+                c.af[q] = (float)a1;
+                c.jf[q] = (float)j1;
+            }
+        }
+        sq[0] = a1 * a1;
+        sq[1] = j1 * j1;
+        sq[2] = a2 * a2;
+        sq[3] = a3 * a3;
+    }
+    const int lane = threadIdx.x % 32, base = lane & ~3;
+    double nrm[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double x = __shfl_sync(0xffffffffu, sq[k], base);
+        const double y = __shfl_sync(0xffffffffu, sq[k], base + 1);
+        const double z = __shfl_sync(0xffffffffu, sq[k], base + 2);
+        nrm[k] = sqrt(x + y + z);
+    }
+    if (sub != 0 || !valid) return;
+    if (c.pot) c.pot[i] = p1;
+    choose_step(c, i, h, nrm[0], nrm[1], nrm[2], nrm[3], tn, tnq);
+}
+
+// FP64 epilogue of one active particle: scale by G, remove the self term of
+// phi (its own j-tile contributed m_i rsqrt(eps^2) exactly), then correct the
+// particle (corr.sc set) or store a1, j1, p1 at its row.
+__device__ __forceinline__ void subset_finalize(const F32CJerkParams &p, const BlockCorrect &corr,
+                                                const ClusterDev &cl, int slot, const double (&r)[7]) {
+    const int64_t u = p.perm[slot];
+    double ph = r[6];
+    if (cl.eps2f > 0.0f) ph -= (double)__fmul_rn(p.pm[slot], rsqrt_mufu(cl.eps2f));
+    if (corr.sc) {
+        const double A1[3] = {p.G * r[0], p.G * r[1], p.G * r[2]};
+        const double J1[3] = {p.G * r[3], p.G * r[4], p.G * r[5]};
+        correct_particle(corr, u, A1, J1, -p.G * ph, corr.sc->t_next, corr.sc->t_next_q);
+        return;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        p.acc[d * p.n + u] = p.G * r[d];
+        p.jerk[d * p.n + u] = p.G * r[3 + d];
+    }
+    if (p.pot) p.pot[u] = -p.G * ph;
+}
+
+}  // namespace nbody

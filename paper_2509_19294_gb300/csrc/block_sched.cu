@@ -1,0 +1,718 @@
+// block_sched.cu -- individual (block) time steps: the device-side schedule
+// (times, prediction and packing, plan, compaction, corrector pass).
+//
+// Around the Hermite scheme each particle keeps its own time t_i and a
+// power-of-two step dt_i (Makino & Aarseth 1992; the paper computes the jerk,
+// Sec. 3, but does not describe its stepping).  One block step, all on the
+// device so that it is a fixed kernel sequence a CUDA graph can replay
+// (F32C; the FP64 path keeps separate predict / count / plan / scatter /
+// items / correct kernels around its own subset kernel):
+//   1. the step's time t_next = min_i (t_i + dt_i): the next multiple of the
+//      smallest occupied step (per-level counts kept by the corrector), taken
+//      by every CTA of block_pack_kernel (block_min_kernel, an integer min in
+//      units of dt_min, runs at the start and on the FP64 path)
+//   2. block_pack_kernel: predict every particle to t_next, pack it as the
+//      j-set (the jerk path's geometry), flag and count the active slots per
+//      tile; the last CTA plans the step (offsets, regime, split, queue size)
+//   3. block_queue_kernel: ordered compaction of the active slots, work items
+//   4. the force pass (block_force.cu): the small-set and the large-set subset
+//      kernels, then subset_tail_kernel, which either runs the few-particle
+//      pass (<= kFewMax active; the subset kernels then find an empty queue)
+//      or sums the subset kernels' split partials in order
+//   5. the Hermite corrector and next-step choice, in the epilogue of 4
+#include <algorithm>
+#include <cuda_runtime.h>
+#include <limits.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "block_common.cuh"
+#include "nbody_internal.h"
+
+namespace nbody {
+
+namespace {
+
+constexpr int kScan = 1024;
+
+// Initial steps: the largest power of two <= min(dt_max, eta_s |a| / |j|), >= dt_min.
+__global__ void block_init_kernel(int64_t n, const double *acc, const double *jerk, double dt_max,
+                                  double dt_min, double eta_s, double *t, double *dt, long long *tq) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double an = sqrt(acc[i] * acc[i] + acc[n + i] * acc[n + i] + acc[2 * n + i] * acc[2 * n + i]);
+        const double jn =
+            sqrt(jerk[i] * jerk[i] + jerk[n + i] * jerk[n + i] + jerk[2 * n + i] * jerk[2 * n + i]);
+        double d = jn > 0.0 ? eta_s * an / jn : dt_max;
+        if (!(d < dt_max)) d = dt_max;
+        d = exp2(floor(log2(d)));
+        if (d < dt_min) d = dt_min;
+        t[i] = 0.0;
+        dt[i] = d;
+        tq[i] = (long long)(d / dt_min);
+    }
+}
+
+// FP32 copies of a and a' for the packing predictor (start of block stepping).
+__global__ void block_shadow_kernel(int64_t n3, const double *__restrict__ acc,
+                                    const double *__restrict__ jerk, float *af, float *jf) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        af[k] = (float)acc[k];
+        jf[k] = (float)jerk[k];
+    }
+}
+
+// Count the particles per step level (start of block stepping).
+__global__ void block_levels_kernel(int64_t n, const double *__restrict__ dt, double dt_max,
+                                    BlockScalars *sc) {
+    __shared__ int cnt[64];
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) cnt[k] = 0;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[block_level(dt[i], dt_max)], 1);
+    __syncthreads();
+    for (int k = threadIdx.x; k < 64; k += blockDim.x)
+        if (cnt[k]) atomicAdd(&sc->level[k], cnt[k]);
+}
+
+// t_next = min_i (t_i + dt_i), exact: the times are integers in units of
+// dt_min, so the min is an integer one.  Per-chunk minima, then the last CTA
+// to finish (ticket) takes the min over them.  No CTA waits for another.
+constexpr int kMinThreads = 512;
+
+__global__ void __launch_bounds__(kMinThreads)
+    block_min_kernel(const long long *__restrict__ tq, const Chunk *__restrict__ chunks,
+                     long long *__restrict__ part, int n_chunks, double dt_min, BlockScalars *sc) {
+    __shared__ long long red[kMinThreads / 32];
+    __shared__ bool last;
+    const Chunk ch = chunks[blockIdx.x];
+    long long m = LLONG_MAX;
+    for (int64_t i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) m = min(m, tq[i]);
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kMinThreads / 32; ++w) m = min(m, red[w]);
+        part[blockIdx.x] = m;
+        __threadfence();
+        last = atomicAdd(&sc->ticket_min, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    m = LLONG_MAX;
+    for (int k = threadIdx.x; k < n_chunks; k += blockDim.x) m = min(m, __ldcg(part + k));
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kMinThreads / 32; ++w) m = min(m, red[w]);
+        sc->t_next_q = m;
+        sc->t_next = (double)m * dt_min;
+        sc->ticket_min = 0;
+    }
+}
+
+// Hermite predictor of particle (row) u to time tn: x[0..2] position, x[3..5] velocity.
+__device__ __forceinline__ void predict_row(int64_t n, int64_t u, double tn, const double *__restrict__ t,
+                                            const double *__restrict__ pos, const double *__restrict__ vel,
+                                            const double *__restrict__ acc,
+                                            const double *__restrict__ jerk, double (&x)[6]) {
+    const double h = tn - t[u], h2 = h * h, h3 = h2 * h;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int64_t q = d * n + u;
+        x[d] = pos[q] + vel[q] * h + acc[q] * h2 / 2.0 + jerk[q] * h3 / 6.0;
+        x[3 + d] = vel[q] + acc[q] * h + jerk[q] * h2 / 2.0;
+    }
+}
+
+// Predict every particle to t_next and flag the active ones (FP64 path).
+__global__ void block_predict_kernel(int64_t n, const BlockScalars *__restrict__ sc,
+                                     const double *__restrict__ t,
+                                     const long long *__restrict__ tq, const double *__restrict__ pos,
+                                     const double *__restrict__ vel, const double *__restrict__ acc,
+                                     const double *__restrict__ jerk, double *xp, double *vp,
+                                     uint8_t *flag) {
+    const double tn = sc->t_next;
+    const bool live = tn <= sc->t_end;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double x[6];
+        predict_row(n, i, tn, t, pos, vel, acc, jerk, x);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xp[d * n + i] = x[d];
+            vp[d * n + i] = x[3 + d];
+        }
+        flag[i] = live && tq[i] == sc->t_next_q;
+    }
+}
+
+// Compaction stage 1 (FP64 path): active count per chunk.
+__global__ void block_count_kernel(const uint8_t *__restrict__ flag, const Chunk *__restrict__ chunks,
+                                   int *__restrict__ cnt) {
+    __shared__ int red[8];
+    const Chunk ch = chunks[blockIdx.x];
+    int c = 0;
+    for (int64_t i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) c += flag[i];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x / 32); ++w) c += red[w];
+        cnt[blockIdx.x] = c;
+    }
+}
+
+// Block-wide exclusive scan of int values by a CTA of NT threads (L2 reads, so
+// the last CTA of a kernel sees what the others wrote).
+template <int NT>
+__device__ void block_exclusive_scan(const int *in, int *out, int n, int *total) {
+    __shared__ int warp_sums[NT / 32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += NT) {
+        const int i = base + threadIdx.x;
+        const int v = i < n ? __ldcg(in + i) : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x % 32) >= o) x += y;
+        }
+        if (threadIdx.x % 32 == 31) warp_sums[threadIdx.x / 32] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int w = threadIdx.x < NT / 32 ? warp_sums[threadIdx.x] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (threadIdx.x >= o) w += y;
+            }
+            if (threadIdx.x < NT / 32) warp_sums[threadIdx.x] = w;
+        }
+        __syncthreads();
+        const int warp_off = threadIdx.x >= 32 ? warp_sums[threadIdx.x / 32 - 1] : 0;
+        if (i < n) out[i] = carry + warp_off + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_sums[NT / 32 - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// The step's plan (one thread, after the scan of the per-unit active counts;
+// cluster c owns units [unit_first[c], unit_first[c + 1])): per-cluster active
+// ranges and i-chunk counts, the split count, the work-queue size, and the
+// queue head reset for the subset kernel.
+__device__ void plan_step(const int *__restrict__ unit_off, int total, int n_units,
+                          const int32_t *__restrict__ unit_first, int ncl,
+                          const ClusterDev *__restrict__ cl, int cs_small, int workers_small,
+                          int max_split, int *__restrict__ act_begin, int *__restrict__ act_n,
+                          int *__restrict__ ich_off, int *__restrict__ item_off, BlockScalars *sc,
+                          int *queue_head, int few_max, int cs_large, int workers_large, int large_min,
+                          long long partial_cap) {
+    const bool few = total > 0 && total <= few_max;
+    const bool large = !few && cs_large > 0 && total >= large_min;
+    const int cs = large ? cs_large : cs_small;
+    const int workers = large ? workers_large : workers_small;
+    int chunks = 0, nf = 0, jb = 0;
+    for (int c = 0; c < ncl; ++c) {
+        const int b = unit_first[c], e = unit_first[c + 1];
+        const int a0 = b < n_units ? unit_off[b] : total;
+        const int a1 = e < n_units ? unit_off[e] : total;
+        act_begin[c] = a0;
+        act_n[c] = a1 - a0;
+        ich_off[c] = chunks;
+        if (!few) chunks += (a1 - a0 + cs - 1) / cs;
+        if (few && a1 > a0) {  // at most total (<= kFewMax) clusters
+            sc->few_cl[nf] = c;
+            sc->few_abeg[nf] = a0;
+            sc->few_jbase[nf] = jb;
+            jb += cl[c].n;
+            ++nf;
+        }
+    }
+    ich_off[ncl] = chunks;
+    sc->few = few;
+    sc->few_ncl = nf;
+    sc->few_jbase[nf] = jb;
+    int split = chunks > 0 ? (2 * workers) / chunks : 1;
+    if (split > max_split) split = max_split;
+    if (split < 1) split = 1;
+    // equal-cost items drain in ceil(items / workers) rounds: among the next few
+    // split counts that fit the partial buffer, take the one whose last round
+    // is fullest (the smaller on ties)
+    if (chunks > 0) {
+        const long long max_slots = partial_cap / (7LL * cs);
+        double best = -1.0;
+        int pick = split;
+        for (int sp = split; sp <= split + 3 && sp <= max_split; ++sp) {
+            if (sp > 1 && (long long)chunks * sp > max_slots) break;
+            const double r = (double)chunks * sp / workers;
+            const double eff = r / ceil(r);
+            if (eff > best + 1e-9) {
+                best = eff;
+                pick = sp;
+            }
+        }
+        split = pick;
+    }
+    int items = 0;
+    for (int c = 0; c < ncl; ++c) {
+        item_off[c] = items;
+        const int sc_c = split < cl[c].n_jt ? split : (cl[c].n_jt > 0 ? cl[c].n_jt : 1);
+        items += (ich_off[c + 1] - ich_off[c]) * sc_c;
+    }
+    item_off[ncl] = items;
+    sc->n_active = total;
+    sc->n_chunks = chunks;
+    sc->split = split;
+    sc->n_items = items;
+    sc->cs = cs;
+    sc->n_items_small = large ? 0 : items;
+    sc->n_items_large = large ? items : 0;
+    if (total > 0) {
+        sc->blocks += 1;
+        sc->evals += total;
+    }
+    if (queue_head) queue_head[0] = queue_head[1] = 0;  // small and large subset kernels
+}
+
+// Compaction stage 2 (FP64 path, one CTA): chunk offsets and the plan.
+__global__ void __launch_bounds__(kScan)
+    block_plan_kernel(const int *__restrict__ cnt, int n_chunks, const int32_t *__restrict__ chunk_first,
+                      int ncl, const ClusterDev *__restrict__ cl, int cs, int workers, int max_split,
+                      int *__restrict__ chunk_off, int *__restrict__ act_begin, int *__restrict__ act_n,
+                      int *__restrict__ ich_off, int *__restrict__ item_off, BlockScalars *sc) {
+    __shared__ int total;
+    block_exclusive_scan<kScan>(cnt, chunk_off, n_chunks, &total);
+    __syncthreads();
+    if (threadIdx.x == 0)
+        plan_step(chunk_off, total, n_chunks, chunk_first, ncl, cl, cs, workers, max_split, act_begin,
+                  act_n, ich_off, item_off, sc, nullptr, 0, 0, 0, 0, 0);
+}
+
+// F32C: one CTA per centre tile of the j-set.  Predicts the tile's particles to
+// t_next (FP64, as block_predict_kernel), packs them as pack_kernel does
+// (FP64 mean position and velocity as float pairs, FP32 offsets, FP32 masses,
+// pads far away with mass 0), flags the active slots and counts them.  The
+// last CTA to finish (ticket) scans the tile counts and plans the step.
+struct BlockPackParams {
+    const int32_t *perm;
+    const ClusterDev *cl;
+    const int32_t *tile_cluster;
+    int tc, n_tiles;
+    int64_t n;
+    const double *mass, *t, *pos, *vel;
+    const float *af, *jf;  // FP32 copies of each particle's a, a' (kept by the corrector)
+    const long long *tq;
+    float *px, *py, *pz, *pm, *pvx, *pvy, *pvz;
+    float4 *chl, *vchl;
+    uint8_t *flag;  // per slot
+    int *tile_cnt, *tile_off;
+    const int32_t *tile_first;
+    int ncl, cs, workers, max_split;
+    int *act_begin, *act_n, *ich_off, *item_off;
+    BlockScalars *sc;
+    int *queue_head;
+    int few_max;
+    int cs_large, workers_large, large_min;
+    long long partial_cap;  // doubles in the split-partial buffer
+    double dt_max, dt_min;
+};
+
+// Hermite predictor for the packed j-set (F32C): x + h v in FP64, the
+// higher-order terms h^2 (a/2 + h a'/6) and h (a + h a'/2) in FP32 from FP32
+// copies of a and a'.  They are small against the step's displacement, so
+// their FP32 rounding stays far below that of the packed FP32 offsets; FP64
+// operations, scarce on this part, drop from 24 to 11 per particle (the
+// velocity change is returned apart, for the packed offset).
+__device__ __forceinline__ void predict_mixed(const BlockPackParams &q, int64_t u, double tn,
+                                              double (&x)[6], float (&dv)[3]) {
+    const double h = tn - q.t[u];
+    const float hf = (float)h;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int64_t k = d * q.n + u;
+        const float a = q.af[k], j = q.jf[k];
+        const float dx = hf * hf * (0.5f * a + hf * (j * (1.0f / 6.0f)));
+        dv[d] = hf * (a + hf * (0.5f * j));
+        const double v = q.vel[k];
+        x[d] = fma(h, v, q.pos[k]) + (double)dx;
+        x[3 + d] = v;  // the velocity change dv is added in FP32 to the packed offset
+    }
+}
+
+constexpr int kPackMaxPer = 4;  // slots per thread in block_pack_kernel (tc <= 4 NT)
+
+// FP64 is scarce on this part (about 1/64 of the FP32 rate), so the tile
+// centre never needs an FP64 reduction.  After a re-sort (FRESH) it is the
+// mean of the FP32-rounded predicted positions (velocities); otherwise the
+// tile holds the same particles as at the previous pack, and the centre is
+// that pack's centre moved by the mean of its FP32 offsets (their mean
+// position then) -- FP32 data only.  Any centre near the tile serves: offsets
+// are FP64 differences from it, rounded once to FP32.  It is stored as a
+// float (lo = 0).  One CTA per tile, so the previous offsets are all read
+// before the CTA overwrites them.
+template <int NT, bool FRESH>
+__global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q) {
+    __shared__ float redf[NT / 32][8];
+    __shared__ double cen[6];
+    __shared__ bool last;
+    __shared__ int total;
+    const int tile = blockIdx.x;
+    // this step's time from the previous step's state (every CTA reads it
+    // before the last one, below, stores it)
+    const long long tnq = block_next_time_q(q.sc->t_next_q, q.sc->n_active, q.sc->level, q.dt_max, q.dt_min);
+    const double tn = (double)tnq * q.dt_min;
+    const bool live = tn <= q.sc->t_end;
+    const ClusterDev cl = q.cl[q.tile_cluster[tile]];
+    const int base = tile * q.tc;
+    const int per = q.tc / NT;
+    float sf[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // position, velocity sums (6), count, active count
+    double x[kPackMaxPer][6];
+    float dvel[kPackMaxPer][3];
+    bool act[kPackMaxPer];
+#pragma unroll
+    for (int r = 0; r < kPackMaxPer; ++r) {
+        act[r] = false;
+        const int slot = base + threadIdx.x + NT * r;
+        if (r < per && slot - cl.slot_begin < cl.n) {
+            const int64_t u = q.perm[slot];
+            predict_mixed(q, u, tn, x[r], dvel[r]);
+            if (FRESH) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    sf[d] += (float)x[r][d];
+                    sf[3 + d] += (float)x[r][3 + d] + dvel[r][d];
+                }
+            } else {
+                sf[0] += q.px[slot];
+                sf[1] += q.py[slot];
+                sf[2] += q.pz[slot];
+                sf[3] += q.pvx[slot];
+                sf[4] += q.pvy[slot];
+                sf[5] += q.pvz[slot];
+            }
+            sf[6] += 1.0f;
+            act[r] = live && q.tq[u] == tnq;
+            sf[7] += act[r] ? 1.0f : 0.0f;
+        }
+    }
+    // CTA sum in FP32, fixed order (counts are exact: at most tc)
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sf[k] += __shfl_xor_sync(0xffffffffu, sf[k], o);
+    if (threadIdx.x % 32 == 0)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) redf[threadIdx.x / 32][k] = sf[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float v = redf[0][k];
+            for (int w = 1; w < NT / 32; ++w) v += redf[w][k];
+            sf[k] = v;
+        }
+        const float inv = sf[6] > 0.0f ? 1.0f / sf[6] : 0.0f;
+        float h[6];
+        if (!FRESH) {
+            const float4 p0 = q.chl[2 * tile], v0 = q.vchl[2 * tile];
+            const float prev[6] = {p0.x, p0.y, p0.z, v0.x, v0.y, v0.z};
+#pragma unroll
+            for (int d = 0; d < 6; ++d) h[d] = prev[d] + sf[d] * inv;
+        } else {
+#pragma unroll
+            for (int d = 0; d < 6; ++d) h[d] = sf[d] * inv;
+        }
+#pragma unroll
+        for (int d = 0; d < 6; ++d) cen[d] = (double)h[d];
+        q.chl[2 * tile + 0] = make_float4(h[0], h[1], h[2], 0.0f);
+        q.chl[2 * tile + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        q.vchl[2 * tile + 0] = make_float4(h[3], h[4], h[5], 0.0f);
+        q.vchl[2 * tile + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        q.tile_cnt[tile] = (int)sf[7];
+    }
+    __syncthreads();
+    double c[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) c[d] = cen[d];
+#pragma unroll
+    for (int r = 0; r < kPackMaxPer; ++r) {
+        const int slot = base + threadIdx.x + NT * r;
+        if (r >= per) break;
+        if (slot - cl.slot_begin < cl.n) {
+            q.px[slot] = (float)(x[r][0] - c[0]);
+            q.py[slot] = (float)(x[r][1] - c[1]);
+            q.pz[slot] = (float)(x[r][2] - c[2]);
+            if (FRESH) q.pm[slot] = (float)q.mass[q.perm[slot]];  // else unchanged
+            // velocity offsets: FP64 difference from the centre, then the FP32
+            // change (two roundings, well inside the jerk's tolerance)
+            q.pvx[slot] = (float)(x[r][3] - c[3]) + dvel[r][0];
+            q.pvy[slot] = (float)(x[r][4] - c[4]) + dvel[r][1];
+            q.pvz[slot] = (float)(x[r][5] - c[5]) + dvel[r][2];
+            q.flag[slot] = act[r];
+        } else {
+            q.px[slot] = kPadOffset;
+            q.py[slot] = kPadOffset;
+            q.pz[slot] = kPadOffset;
+            q.pm[slot] = 0.0f;
+            q.pvx[slot] = q.pvy[slot] = q.pvz[slot] = 0.0f;
+            q.flag[slot] = 0;
+        }
+    }
+    // the last CTA reads only the tile counts (thread 0's writes); the packed
+    // data is for later kernels
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&q.sc->ticket_pack, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    block_exclusive_scan<NT>(q.tile_cnt, q.tile_off, q.n_tiles, &total);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        q.sc->t_next_q = tnq;
+        q.sc->t_next = tn;
+        plan_step(q.tile_off, total, q.n_tiles, q.tile_first, q.ncl, q.cl, q.cs, q.workers, q.max_split,
+                  q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max, q.cs_large,
+                  q.workers_large, q.large_min, q.partial_cap);
+        q.sc->ticket_pack = 0;
+    }
+}
+
+// Work item k -> (cluster, i-chunk of the active list, j-range split).
+__device__ __forceinline__ SubItem make_item(int k, int ncl, const ClusterDev *__restrict__ cl, int cs,
+                                             int split, const int *__restrict__ act_begin,
+                                             const int *__restrict__ act_n,
+                                             const int *__restrict__ ich_off,
+                                             const int *__restrict__ item_off) {
+    int lo = 0, hi = ncl;  // cluster c with item_off[c] <= k < item_off[c + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (item_off[mid] <= k) lo = mid;
+        else hi = mid;
+    }
+    const int c = lo;
+    const ClusterDev d = cl[c];
+    const int sc_c = split < d.n_jt ? split : (d.n_jt > 0 ? d.n_jt : 1);
+    const int local = k - item_off[c];
+    const int ch = local / sc_c, s = local % sc_c;
+    SubItem it;
+    it.a0 = act_begin[c] + ch * cs;
+    it.na = min(cs, act_n[c] - ch * cs);
+    it.cluster = c;
+    it.chunk = ich_off[c] + ch;
+    it.jt0 = (int)((int64_t)s * d.n_jt / sc_c);
+    it.jt1 = (int)((int64_t)(s + 1) * d.n_jt / sc_c);
+    it.split = s;
+    it.nsplit = sc_c;
+    it.pbase = sc_c > 1 ? it.chunk * split : 0;
+    it.pad = 0;
+    return it;
+}
+
+// Ordered compaction of one run of flags [begin, end): the k-th set flag in
+// order writes its index to act[off + k] (warp ballots, warps in order).
+template <int NT>
+__device__ __forceinline__ void compact_run(const uint8_t *__restrict__ flag, int64_t begin, int64_t end,
+                                            int off, int32_t *__restrict__ act) {
+    __shared__ int warp_cnt[NT / 32];
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    for (int64_t b = begin; b < end; b += NT) {
+        const int64_t i = b + threadIdx.x;
+        const int f = i < end ? flag[i] : 0;
+        const unsigned mask = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) warp_cnt[w] = __popc(mask);
+        __syncthreads();
+        int o = off;
+        for (int k = 0; k < w; ++k) o += warp_cnt[k];
+        if (f) act[o + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
+        for (int k = 0; k < NT / 32; ++k) off += warp_cnt[k];
+        __syncthreads();
+    }
+}
+
+// Compaction stage 3 (FP64 path): ordered scatter of the active rows to act[]
+// in row order within each cluster.
+__global__ void block_scatter_kernel(const uint8_t *__restrict__ flag, const Chunk *__restrict__ chunks,
+                                     const int *__restrict__ chunk_off, int32_t *__restrict__ act) {
+    const Chunk ch = chunks[blockIdx.x];
+    const int off = __ldcg(chunk_off + blockIdx.x);
+    compact_run<256>(flag, ch.begin, ch.end, off, act);
+}
+
+// Work queue (FP64 path).
+__global__ void block_items_kernel(int ncl, const ClusterDev *__restrict__ cl,
+                                   const int *__restrict__ act_begin, const int *__restrict__ act_n,
+                                   const int *__restrict__ ich_off, const int *__restrict__ item_off,
+                                   const BlockScalars *__restrict__ sc, int max_items,
+                                   SubItem *__restrict__ items, SubItem *__restrict__ info) {
+    const int n_items = sc->n_items;
+    const int split = sc->split;
+    const int cs = sc->cs;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_items && k < max_items;
+         k += gridDim.x * blockDim.x) {
+        const SubItem it = make_item(k, ncl, cl, cs, split, act_begin, act_n, ich_off, item_off);
+        items[k] = it;
+        if (it.split == 0) info[it.chunk] = it;
+    }
+}
+
+// F32C queue: one CTA per centre tile compacts the tile's active slots to
+// act[] (slot order within each cluster), and all threads build the items.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+    block_queue_kernel(const uint8_t *__restrict__ flag, int tc, const int *__restrict__ tile_cnt,
+                       const int *__restrict__ tile_off, int32_t *__restrict__ act, int ncl,
+                       const ClusterDev *__restrict__ cl, const int *__restrict__ act_begin,
+                       const int *__restrict__ act_n, const int *__restrict__ ich_off,
+                       const int *__restrict__ item_off, const BlockScalars *__restrict__ sc,
+                       int max_items, SubItem *__restrict__ items, SubItem *__restrict__ info) {
+    const int tile = blockIdx.x;
+    if (tile_cnt[tile] > 0)  // uniform over the CTA
+        compact_run<NT>(flag, (int64_t)tile * tc, (int64_t)(tile + 1) * tc, __ldcg(tile_off + tile), act);
+    const int n_items = sc->n_items;
+    const int split = sc->split;
+    const int cs = sc->cs;
+    for (int k = blockIdx.x * NT + threadIdx.x; k < n_items && k < max_items; k += gridDim.x * NT) {
+        const SubItem it = make_item(k, ncl, cl, cs, split, act_begin, act_n, ich_off, item_off);
+        items[k] = it;
+        if (it.split == 0) info[it.chunk] = it;
+    }
+}
+
+// The corrector as a pass over the active list: row = act[k] (FP64 path).
+__global__ void block_correct_kernel(const BlockCorrect c, const int32_t *__restrict__ act,
+                                     const double *__restrict__ a1, const double *__restrict__ j1,
+                                     const double *__restrict__ p1) {
+    const double tn = c.sc->t_next;
+    const long long tnq = c.sc->t_next_q;
+    const int n_active = c.sc->n_active;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_active; k += gridDim.x * blockDim.x) {
+        const int64_t i = act[k];
+        double A1[3], J1[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            A1[d] = a1[d * c.n + i];
+            J1[d] = j1[d * c.n + i];
+        }
+        correct_particle(c, i, A1, J1, p1[i], tn, tnq);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, double dt_max,
+                              double dt_min, double eta_s, double *t, double *dt, long long *tq,
+                              cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    block_init_kernel<<<grid_of(n, 256), 256, 0, s>>>(n, acc, jerk, dt_max, dt_min, eta_s, t, dt, tq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_shadow(int64_t n, const double *acc, const double *jerk, float *af, float *jf,
+                                cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    block_shadow_kernel<<<grid_of(3 * n, 256), 256, 0, s>>>(3 * n, acc, jerk, af, jf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_levels(int64_t n, const double *dt, double dt_max, double dt_min,
+                                const Chunk *chunks, int n_chunks, const long long *tq, double *part,
+                                BlockScalars *sc, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    block_levels_kernel<<<grid_of(n, 256), 256, 0, s>>>(n, dt, dt_max, sc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    block_min_kernel<<<n_chunks, kMinThreads, 0, s>>>(tq, chunks, reinterpret_cast<long long *>(part),
+                                                      n_chunks, dt_min, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kernels) {
+    cudaError_t e;
+#define NB_BL(x)                        \
+    do {                                \
+        x;                              \
+        e = cudaGetLastError();         \
+        if (e != cudaSuccess) return e; \
+        ++*kernels;                     \
+    } while (0)
+    if (!b.px)  // the F32C path has t_next from the previous step's last kernel
+        NB_BL((block_min_kernel<<<b.n_chunks, kMinThreads, 0, s>>>(
+            b.tq, b.chunks, reinterpret_cast<long long *>(b.part), b.n_chunks, b.dt_min, b.sc)));
+    if (b.px) {
+        if (b.tc <= 0 || b.tc % 128 != 0 || b.tc > kPackMaxPer * (b.tc % 256 == 0 ? 256 : 128))
+            return cudaErrorInvalidValue;
+        BlockPackParams q{};
+        q.perm = b.perm; q.cl = b.cl; q.tile_cluster = b.tile_cluster; q.tc = b.tc;
+        q.n_tiles = b.n_tiles; q.n = b.n; q.mass = b.mass; q.t = b.t; q.tq = b.tq; q.af = b.af; q.jf = b.jf;
+        q.pos = b.pos; q.vel = b.vel;
+        q.px = b.px; q.py = b.py; q.pz = b.pz; q.pm = b.pm;
+        q.pvx = b.pvx; q.pvy = b.pvy; q.pvz = b.pvz; q.chl = b.chl; q.vchl = b.vchl;
+        q.flag = b.flag; q.tile_cnt = b.cnt; q.tile_off = b.chunk_off; q.tile_first = b.tile_first;
+        q.ncl = b.ncl; q.cs = b.cs; q.workers = b.workers; q.max_split = b.max_split;
+        q.act_begin = b.act_begin; q.act_n = b.act_n; q.ich_off = b.ich_off; q.item_off = b.item_off;
+        q.sc = b.sc; q.queue_head = b.queue_head; q.few_max = b.few_max;
+        q.cs_large = b.cs_large; q.workers_large = b.workers_large; q.large_min = b.large_min;
+        q.partial_cap = b.partial_cap;
+        q.dt_max = b.dt_max;
+        q.dt_min = b.dt_min;
+        if (b.tc % 256 == 0) {
+            if (b.fresh) NB_BL((block_pack_kernel<256, true><<<b.n_tiles, 256, 0, s>>>(q)));
+            else NB_BL((block_pack_kernel<256, false><<<b.n_tiles, 256, 0, s>>>(q)));
+        } else {
+            if (b.fresh) NB_BL((block_pack_kernel<128, true><<<b.n_tiles, 128, 0, s>>>(q)));
+            else NB_BL((block_pack_kernel<128, false><<<b.n_tiles, 128, 0, s>>>(q)));
+        }
+    } else {
+        NB_BL((block_predict_kernel<<<grid_of(b.n, 256), 256, 0, s>>>(
+            b.n, b.sc, b.t, b.tq, b.pos, b.vel, b.acc, b.jerk, b.xp, b.vp, b.flag)));
+        NB_BL((block_count_kernel<<<b.n_chunks, 256, 0, s>>>(b.flag, b.chunks, b.cnt)));
+        NB_BL((block_plan_kernel<<<1, kScan, 0, s>>>(b.cnt, b.n_chunks, b.chunk_first, b.ncl, b.cl, b.cs,
+                                                      b.workers, b.max_split, b.chunk_off, b.act_begin,
+                                                      b.act_n, b.ich_off, b.item_off, b.sc)));
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_block_queue(const BlockLaunch &b, cudaStream_t s, int *kernels) {
+    cudaError_t e;
+    if (b.px) {
+        if (b.tc % 256 == 0)
+            NB_BL((block_queue_kernel<256><<<b.n_tiles, 256, 0, s>>>(
+                b.flag, b.tc, b.cnt, b.chunk_off, b.act, b.ncl, b.cl, b.act_begin, b.act_n, b.ich_off,
+                b.item_off, b.sc, b.max_items, b.items, b.info)));
+        else
+            NB_BL((block_queue_kernel<128><<<b.n_tiles, 128, 0, s>>>(
+                b.flag, b.tc, b.cnt, b.chunk_off, b.act, b.ncl, b.cl, b.act_begin, b.act_n, b.ich_off,
+                b.item_off, b.sc, b.max_items, b.items, b.info)));
+    } else {
+        NB_BL((block_scatter_kernel<<<b.n_chunks, 256, 0, s>>>(b.flag, b.chunks, b.chunk_off, b.act)));
+        NB_BL((block_items_kernel<<<grid_of(b.max_items, 256), 256, 0, s>>>(
+            b.ncl, b.cl, b.act_begin, b.act_n, b.ich_off, b.item_off, b.sc, b.max_items, b.items,
+            b.info)));
+    }
+    return cudaSuccess;
+}
+#undef NB_BL
+
+
+cudaError_t launch_block_correct(const BlockCorrect &c, const int32_t *act, const double *a1,
+                                 const double *j1, const double *p1, cudaStream_t s) {
+    if (c.n <= 0) return cudaSuccess;
+    // grid-stride over the active list: a few waves suffice for every particle
+    const int grid = std::min(grid_of(c.n, 256), 2 * 152);
+    block_correct_kernel<<<grid, 256, 0, s>>>(c, act, a1, j1, p1);
+    return cudaGetLastError();
+}
+
+}  // namespace nbody

@@ -928,7 +928,7 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
     return b;
 }
 
-// One block step (see block.cu): schedule, predict, pack the predicted j-set,
+// One block step (see block_sched.cu, block_force.cu): schedule, predict, pack the predicted j-set,
 // forces + jerks of the active subset, correct and re-step the active ones.
 int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, bool capturing,
                        cudaStream_t s, int *kernels) {

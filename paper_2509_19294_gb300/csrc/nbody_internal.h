@@ -121,7 +121,7 @@ struct Chunk {
     int64_t begin, end;  // caller rows [begin, end)
 };
 
-// Block time steps (block.cu).  One work item: an i-chunk of the active list
+// Block time steps (block_sched.cu, block_force.cu).  One work item: an i-chunk of the active list
 // (positions a0 .. a0 + na - 1, all in one cluster) against one j-range split.
 struct SubItem {
     int32_t a0, na, cluster, chunk;
@@ -157,7 +157,7 @@ struct BlockScalars {
 // Subset acceleration + jerk kernel: base carries the j-set (the jerk path's
 // packed predicted particles), perm (slot -> row) and the outputs (rows).
 // Hermite corrector + next-step choice of the block scheme, applied where an
-// active particle's acceleration and jerk become final (block.cu).
+// active particle's acceleration and jerk become final (block_common.cuh).
 struct BlockCorrect {
     const BlockScalars *sc;
     int *level;  // BlockScalars::level (the corrector moves particles between levels)
@@ -262,7 +262,7 @@ cudaError_t launch_block_shadow(int64_t n, const double *acc, const double *jerk
 cudaError_t launch_block_levels(int64_t n, const double *dt, double dt_max, double dt_min,
                                 const Chunk *chunks, int n_chunks, const long long *tq, double *part,
                                 BlockScalars *sc, cudaStream_t s);
-// block * groups threads per CTA (see SubsetKernel in block.cu).
+// block * groups threads per CTA (see SubsetKernel in block_force.cu).
 cudaError_t launch_subset_f32c(int block, int p, int tj, int groups, int minb, bool eps_zero,
                                int grid, const F32CSubsetParams &prm, cudaStream_t s);
 cudaError_t launch_subset_f64(int max_items, const double *xp, const double *vp, const double *mass,
