@@ -117,6 +117,28 @@ def time_oracle_rows(pos, mass, budget_s, seed):
     return len(rows) * n / (t1 - t0), len(rows), t1 - t0, oracle.num_threads()
 
 
+def time_oracle_configs():
+    """One full FP64 oracle evaluation at the smaller workloads (C1 N=1024,
+    C2 N=16384 uniform sphere with log-uniform masses, C3 N=131072), as
+    context for the sampled rate at N=1M."""
+    import oracle
+    from paper_2509_19294_gb300 import ic
+    out = {}
+    cases = [("C1 Plummer N=1024", lambda: (ic.plummer(1024, seed=1)[0], np.full(1024, 1.0 / 1024), 0.01)),
+             ("C2 uniform sphere N=16384, log-uniform masses",
+              lambda: (ic.uniform_sphere(16384, seed=2)[0], ic.log_uniform_masses(16384, seed=2), 0.005)),
+             ("C3 Plummer N=131072", lambda: (ic.plummer(131072, seed=3)[0], np.full(131072, 1.0 / 131072),
+                                               1e-3))]
+    for name, make in cases:
+        pos, mass, eps = make()
+        n = mass.shape[0]
+        t0 = time.perf_counter()
+        oracle.forces(pos, mass, eps)
+        sec = time.perf_counter() - t0
+        out[name] = {"seconds": sec, "interactions_per_s": float(n) * n / sec}
+    return out
+
+
 # ----------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -297,7 +319,8 @@ def run_ours(args):
             val, nrows, secs, thr = time_oracle_rows(ph, mh, args.cpu_seconds, 7)
             cpu = {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
                    "sample": f"{nrows} random rows x all {n} particles of the same state "
-                             f"(FP64, {secs:.1f} s on {thr} threads)"}
+                             f"(FP64, {secs:.1f} s on {thr} threads)",
+                   "full_evaluations": time_oracle_configs()}
 
     # plain FP64 GPU kernel on the same GPU: one evaluation of a bounded sample
     fp64 = None
