@@ -117,6 +117,27 @@ def time_oracle_rows(pos, mass, budget_s, seed):
     return len(rows) * n / (t1 - t0), len(rows), t1 - t0, oracle.num_threads()
 
 
+def host_cpu():
+    """CPU model and usable cores of this host (for the CPU-baseline record)."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count()
+    return {"model": model or platform.processor() or platform.machine(), "arch": platform.machine(),
+            "cores_usable": cores}
+
+
 def time_oracle_configs():
     """One full FP64 oracle evaluation at the smaller workloads (C1 N=1024,
     C2 N=16384 uniform sphere with log-uniform masses, C3 N=131072), as
@@ -320,7 +341,7 @@ def run_ours(args):
             cpu = {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
                    "sample": f"{nrows} random rows x all {n} particles of the same state "
                              f"(FP64, {secs:.1f} s on {thr} threads)",
-                   "full_evaluations": time_oracle_configs()}
+                   "full_evaluations": time_oracle_configs(), "host": host_cpu()}
 
     # plain FP64 GPU kernel on the same GPU: one evaluation of a bounded sample
     fp64 = None
