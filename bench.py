@@ -130,6 +130,15 @@ def host_cpu():
                     break
     except OSError:
         pass
+    if model is None:
+        try:  # Arm hosts: /proc/cpuinfo has no model name, lscpu does
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
     try:
         cores = len(os.sched_getaffinity(0))
     except AttributeError:
