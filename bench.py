@@ -636,7 +636,7 @@ def run_reference(args):
                                      "against all N particles (the full O(N^2) step would take "
                                      "~11 minutes on the host cores)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
