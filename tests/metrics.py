@@ -10,9 +10,9 @@ def rel_acc_errors(a, ref):
 
 
 def paper_metric(a, ref):
-    """The paper's bound (Sec. 3 validation paragraph): every acceleration
-    component within 0.05 % of "a typical force magnitude".  Read here as the
-    particle's own magnitude: max_i,k |a_ik - ref_ik| / |ref_i|."""
+    """The paper's validation bound (Sec. 3): each acceleration component
+    within 0.05 % of a force magnitude it calls typical without defining it.
+    Read here as the particle's own magnitude: max_i,k |a_ik - ref_ik| / |ref_i|."""
     a, ref = np.asarray(a), np.asarray(ref)
     den = np.linalg.norm(ref, axis=0)
     return float((np.abs(a - ref).max(axis=0) / np.where(den > 0, den, 1.0)).max())

@@ -5,8 +5,8 @@ Tolerances:
     <= 1e-12 (both are FP64 sums of the same terms in different orders).
   * NBODY_F32C against the oracle: median relative acceleration error <= 1e-6
     and max <= 1e-4, potential median <= 1e-6 and max <= 1e-4, and the paper's
-    own bound (each component within 0.05 % of a typical force magnitude,
-    Sec. 3 validation paragraph; "typical" read as the particle's own |a_i|).
+    own validation bound (Sec. 3: each component within 0.05 % of an undefined
+    typical force magnitude, read as the particle's own |a_i|).
 """
 import numpy as np
 import pytest
