@@ -36,8 +36,9 @@ __device__ __forceinline__ double recip_pow2(double h) {
 // (<= dt_max, <= the criterion, and t_next a multiple of the doubled step --
 // an integer test in units of dt_min).  Records the particle's new time, step
 // and level.
-__device__ __forceinline__ void choose_step(const BlockCorrect &c, int64_t i, double h, double na,
-                                            double nj, double n2, double n3, double tn, long long tnq) {
+__device__ __forceinline__ void choose_step(const BlockCorrect &c, int64_t i, int slot, double h,
+                                            double na, double nj, double n2, double n3, double tn,
+                                            long long tnq) {
     const double den = nj * n3 + n2 * n2;
     const double da = den > 0.0 ? sqrt(c.eta * (na * n2 + nj * nj) / den) : c.dt_max;
     const double inv_dt_min = recip_pow2(c.dt_min);
@@ -49,9 +50,14 @@ __device__ __forceinline__ void choose_step(const BlockCorrect &c, int64_t i, do
         atomicSub(&c.level[block_level(h, c.dt_max)], 1);
         atomicAdd(&c.level[block_level(nd, c.dt_max)], 1);
     }
+    const long long tq_next = tnq + (long long)(nd * inv_dt_min);
     c.t[i] = tn;
     c.dt[i] = nd;
-    c.tq[i] = tnq + (long long)(nd * inv_dt_min);
+    c.tq[i] = tq_next;
+    if (c.m.pos) {
+        c.m.t[slot] = tn;
+        c.m.tq[slot] = tq_next;
+    }
 }
 
 // Hermite corrector of active particle (row) i over its step h = dt_i with the
@@ -60,9 +66,9 @@ __device__ __forceinline__ void choose_step(const BlockCorrect &c, int64_t i, do
 // multiple of dt_min, so dividing by h, h^2, h^3 is the exact multiplication
 // by their reciprocals and "t_next is a multiple of 2h" is an integer test;
 // both give the oracle's results bit for bit.
-__device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t i, const double (&A1)[3],
-                                                 const double (&J1)[3], double p1, double tn,
-                                                 long long tnq) {
+__device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t i, int slot,
+                                                 const double (&A1)[3], const double (&J1)[3], double p1,
+                                                 double tn, long long tnq) {
     const double h = c.dt[i], h2 = h * h;
     const double ih = recip_pow2(h), ih2 = ih * ih, ih3 = ih2 * ih;
     double A2[3], A3[3];
@@ -71,15 +77,19 @@ __device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t 
         const int64_t q = d * c.n + i;
         const double a0 = c.acc[q], j0 = c.jerk[q], v0 = c.vel[q];
         const double v1 = v0 + (a0 + A1[d]) * h / 2.0 + (j0 - J1[d]) * h2 / 12.0;
-        c.pos[q] = c.pos[q] + (v0 + v1) * h / 2.0 + (a0 - A1[d]) * h2 / 12.0;
+        const double x1 = c.pos[q] + (v0 + v1) * h / 2.0 + (a0 - A1[d]) * h2 / 12.0;
+        c.pos[q] = x1;
         c.vel[q] = v1;
         A3[d] = (12.0 * (a0 - A1[d]) + 6.0 * h * (j0 + J1[d])) * ih3;
         A2[d] = (-6.0 * (a0 - A1[d]) - h * (4.0 * j0 + 2.0 * J1[d])) * ih2 + h * A3[d];
         c.acc[q] = A1[d];
         c.jerk[q] = J1[d];
-        if (c.af) {
-            c.af[q] = (float)A1[d];
-            c.jf[q] = (float)J1[d];
+        if (c.m.pos) {
+            const int64_t qs = d * c.m.n_pad + slot;
+            c.m.pos[qs] = x1;
+            c.m.vel[qs] = v1;
+            c.m.af[qs] = (float)A1[d];
+            c.m.jf[qs] = (float)J1[d];
         }
     }
     if (c.pot) c.pot[i] = p1;
@@ -87,15 +97,15 @@ __device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t 
     const double nj = sqrt(J1[0] * J1[0] + J1[1] * J1[1] + J1[2] * J1[2]);
     const double n2 = sqrt(A2[0] * A2[0] + A2[1] * A2[1] + A2[2] * A2[2]);
     const double n3 = sqrt(A3[0] * A3[0] + A3[1] * A3[1] + A3[2] * A3[2]);
-    choose_step(c, i, h, na, nj, n2, n3, tn, tnq);
+    choose_step(c, i, slot, h, na, nj, n2, n3, tn, tnq);
 }
 
 // correct_particle spread over four consecutive lanes of a warp: lane sub
 // (0..2) corrects component sub, the norms are summed across the three lanes
 // in component order, and lane 0 chooses the step.  Every lane of the warp
 // calls it (the shuffles need them); lanes with valid == false store nothing.
-__device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64_t i, bool valid, int sub,
-                                                    double a1, double j1, double p1, double tn,
+__device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64_t i, int slot, bool valid,
+                                                    int sub, double a1, double j1, double p1, double tn,
                                                     long long tnq) {
     const double h = c.dt[i], h2 = h * h;
     const double ih = recip_pow2(h), ih2 = ih * ih, ih3 = ih2 * ih;
@@ -112,9 +122,12 @@ __device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64
             c.vel[q] = v1;
             c.acc[q] = a1;
             c.jerk[q] = j1;
-            if (c.af) {
-                c.af[q] = (float)a1;
-                c.jf[q] = (float)j1;
+            if (c.m.pos) {
+                const int64_t qs = sub * c.m.n_pad + slot;
+                c.m.pos[qs] = x1;
+                c.m.vel[qs] = v1;
+                c.m.af[qs] = (float)a1;
+                c.m.jf[qs] = (float)j1;
             }
         }
         sq[0] = a1 * a1;
@@ -133,7 +146,7 @@ __device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64
     }
     if (sub != 0 || !valid) return;
     if (c.pot) c.pot[i] = p1;
-    choose_step(c, i, h, nrm[0], nrm[1], nrm[2], nrm[3], tn, tnq);
+    choose_step(c, i, slot, h, nrm[0], nrm[1], nrm[2], nrm[3], tn, tnq);
 }
 
 // FP64 epilogue of one active particle: scale by G, remove the self term of
@@ -147,7 +160,7 @@ __device__ __forceinline__ void subset_finalize(const F32CJerkParams &p, const B
     if (corr.sc) {
         const double A1[3] = {p.G * r[0], p.G * r[1], p.G * r[2]};
         const double J1[3] = {p.G * r[3], p.G * r[4], p.G * r[5]};
-        correct_particle(corr, u, A1, J1, -p.G * ph, corr.sc->t_next, corr.sc->t_next_q);
+        correct_particle(corr, u, slot, A1, J1, -p.G * ph, corr.sc->t_next, corr.sc->t_next_q);
         return;
     }
 #pragma unroll

@@ -421,7 +421,7 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
             const int slot = act[aa];
             double ph = csum[aa][6];
             if (cl.eps2f > 0.0f) ph -= (double)__fmul_rn(p.pm[slot], rsqrt_mufu(cl.eps2f));
-            correct_particle_x4(q.corr, p.perm[slot], valid, sub, p.G * csum[aa][sub < 3 ? sub : 0],
+            correct_particle_x4(q.corr, p.perm[slot], slot, valid, sub, p.G * csum[aa][sub < 3 ? sub : 0],
                                 p.G * csum[aa][sub < 3 ? 3 + sub : 3], -p.G * ph, sc->t_next,
                                 sc->t_next_q);
         }

@@ -53,13 +53,30 @@ __global__ void block_init_kernel(int64_t n, const double *acc, const double *je
     }
 }
 
-// FP32 copies of a and a' for the packing predictor (start of block stepping).
-__global__ void block_shadow_kernel(int64_t n3, const double *__restrict__ acc,
-                                    const double *__restrict__ jerk, float *af, float *jf) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        af[k] = (float)acc[k];
-        jf[k] = (float)jerk[k];
+// The packing predictor's state in j-set slot order (F32C): gathered from the
+// rows through perm at the start of block stepping, after every re-sort and at
+// the start of every advance call (the caller may have changed the rows).
+__global__ void block_mirror_kernel(const int32_t *__restrict__ perm, const ClusterDev *__restrict__ cl,
+                                    const int32_t *__restrict__ tile_cluster, int tc, int64_t n,
+                                    const double *__restrict__ pos, const double *__restrict__ vel,
+                                    const double *__restrict__ t, const long long *__restrict__ tq,
+                                    const double *__restrict__ acc, const double *__restrict__ jerk,
+                                    const SlotMirror m) {
+    for (int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; slot < m.n_pad;
+         slot += (int64_t)gridDim.x * blockDim.x) {
+        const ClusterDev c = cl[tile_cluster[slot / tc]];
+        if (slot - c.slot_begin >= c.n) continue;  // padding: never read
+        const int64_t u = perm[slot];
+        m.t[slot] = t[u];
+        m.tq[slot] = tq[u];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int64_t k = d * n + u, ks = d * m.n_pad + slot;
+            m.pos[ks] = pos[k];
+            m.vel[ks] = vel[k];
+            m.af[ks] = (float)acc[k];
+            m.jf[ks] = (float)jerk[k];
+        }
     }
 }
 
@@ -307,9 +324,8 @@ struct BlockPackParams {
     const int32_t *tile_cluster;
     int tc, n_tiles;
     int64_t n;
-    const double *mass, *t, *pos, *vel;
-    const float *af, *jf;  // FP32 copies of each particle's a, a' (kept by the corrector)
-    const long long *tq;
+    const double *mass;
+    SlotMirror m;  // slot-ordered pos, vel, t, tq and FP32 a, a' (kept by the corrector)
     float *px, *py, *pz, *pm, *pvx, *pvy, *pvz;
     float4 *chl, *vchl;
     uint8_t *flag;  // per slot
@@ -331,18 +347,18 @@ struct BlockPackParams {
 // their FP32 rounding stays far below that of the packed FP32 offsets; FP64
 // operations, scarce on this part, drop from 24 to 11 per particle (the
 // velocity change is returned apart, for the packed offset).
-__device__ __forceinline__ void predict_mixed(const BlockPackParams &q, int64_t u, double tn,
+__device__ __forceinline__ void predict_mixed(const SlotMirror &m, int64_t slot, double tn,
                                               double (&x)[6], float (&dv)[3]) {
-    const double h = tn - q.t[u];
+    const double h = tn - m.t[slot];
     const float hf = (float)h;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const int64_t k = d * q.n + u;
-        const float a = q.af[k], j = q.jf[k];
+        const int64_t k = d * m.n_pad + slot;
+        const float a = m.af[k], j = m.jf[k];
         const float dx = hf * hf * (0.5f * a + hf * (j * (1.0f / 6.0f)));
         dv[d] = hf * (a + hf * (0.5f * j));
-        const double v = q.vel[k];
-        x[d] = fma(h, v, q.pos[k]) + (double)dx;
+        const double v = m.vel[k];
+        x[d] = fma(h, v, m.pos[k]) + (double)dx;
         x[3 + d] = v;  // the velocity change dv is added in FP32 to the packed offset
     }
 }
@@ -382,8 +398,7 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
         act[r] = false;
         const int slot = base + threadIdx.x + NT * r;
         if (r < per && slot - cl.slot_begin < cl.n) {
-            const int64_t u = q.perm[slot];
-            predict_mixed(q, u, tn, x[r], dvel[r]);
+            predict_mixed(q.m, slot, tn, x[r], dvel[r]);
             if (FRESH) {
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
@@ -399,7 +414,7 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
                 sf[5] += q.pvz[slot];
             }
             sf[6] += 1.0f;
-            act[r] = live && q.tq[u] == tnq;
+            act[r] = live && q.m.tq[slot] == tnq;
             sf[7] += act[r] ? 1.0f : 0.0f;
         }
     }
@@ -604,7 +619,7 @@ __global__ void block_correct_kernel(const BlockCorrect c, const int32_t *__rest
             A1[d] = a1[d * c.n + i];
             J1[d] = j1[d * c.n + i];
         }
-        correct_particle(c, i, A1, J1, p1[i], tn, tnq);
+        correct_particle(c, i, -1, A1, J1, p1[i], tn, tnq);  // no mirror on this path
     }
 }
 
@@ -618,10 +633,13 @@ cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_shadow(int64_t n, const double *acc, const double *jerk, float *af, float *jf,
-                                cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    block_shadow_kernel<<<grid_of(3 * n, 256), 256, 0, s>>>(3 * n, acc, jerk, af, jf);
+cudaError_t launch_block_mirror(const int32_t *perm, const ClusterDev *cl, const int32_t *tile_cluster,
+                                int tc, int64_t n, const double *pos, const double *vel, const double *t,
+                                const long long *tq, const double *acc, const double *jerk,
+                                const SlotMirror &m, cudaStream_t s) {
+    if (n <= 0 || m.n_pad <= 0) return cudaSuccess;
+    block_mirror_kernel<<<grid_of(m.n_pad, 256), 256, 0, s>>>(perm, cl, tile_cluster, tc, n, pos, vel, t, tq,
+                                                              acc, jerk, m);
     return cudaGetLastError();
 }
 
@@ -654,8 +672,7 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
             return cudaErrorInvalidValue;
         BlockPackParams q{};
         q.perm = b.perm; q.cl = b.cl; q.tile_cluster = b.tile_cluster; q.tc = b.tc;
-        q.n_tiles = b.n_tiles; q.n = b.n; q.mass = b.mass; q.t = b.t; q.tq = b.tq; q.af = b.af; q.jf = b.jf;
-        q.pos = b.pos; q.vel = b.vel;
+        q.n_tiles = b.n_tiles; q.n = b.n; q.mass = b.mass; q.m = b.mirror;
         q.px = b.px; q.py = b.py; q.pz = b.pz; q.pm = b.pm;
         q.pvx = b.pvx; q.pvy = b.pvy; q.pvz = b.pvz; q.chl = b.chl; q.vchl = b.vchl;
         q.flag = b.flag; q.tile_cnt = b.cnt; q.tile_off = b.chunk_off; q.tile_first = b.tile_first;

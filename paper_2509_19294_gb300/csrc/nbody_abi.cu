@@ -81,7 +81,7 @@ struct BlockState {
     double *t = nullptr, *dt = nullptr, *part = nullptr, *partial = nullptr, *p1 = nullptr;
     double *few_part = nullptr;  // few-particle path: kFewCtas * kFewMax * 7
     long long *tq = nullptr;     // t_i + dt_i in units of dt_min
-    float *af = nullptr, *jf = nullptr;  // FP32 copies of a, a' (F32C packing predictor)
+    SlotMirror m{};  // F32C: the packing predictor's state in j-set slot order
     uint8_t *flag = nullptr;
     int *cnt = nullptr, *chunk_off = nullptr, *act_begin = nullptr, *act_n = nullptr;
     int *ich_off = nullptr, *item_off = nullptr;
@@ -784,8 +784,13 @@ void free_block(nbody_ctx *ctx) {
     BlockState &b = ctx->bs;
     for (double **q : {&b.t, &b.dt, &b.part, &b.partial, &b.p1, &b.few_part}) dev_free(q);
     dev_free(&b.tq);
-    dev_free(&b.af);
-    dev_free(&b.jf);
+    dev_free(&b.m.pos);
+    dev_free(&b.m.vel);
+    dev_free(&b.m.t);
+    dev_free(&b.m.tq);
+    dev_free(&b.m.af);
+    dev_free(&b.m.jf);
+    b.m.n_pad = 0;
     dev_free(&b.flag);
     for (int **q : {&b.cnt, &b.chunk_off, &b.act_begin, &b.act_n, &b.ich_off, &b.item_off}) dev_free(q);
     dev_free(&b.act);
@@ -852,9 +857,15 @@ int alloc_block(nbody_ctx *ctx) {
     for (double **q : {&b.t, &b.dt, &b.p1})
         if ((rc = dev_alloc(ctx, q, n))) return rc;
     if ((rc = dev_alloc(ctx, &b.tq, n))) return rc;
-    if (f32c)
-        for (float **q : {&b.af, &b.jf})
-            if ((rc = dev_alloc(ctx, q, 3 * n))) return rc;
+    if (f32c) {
+        const size_t np = (size_t)ctx->jp.n_pad;
+        b.m.n_pad = (int64_t)np;
+        for (double **q : {&b.m.pos, &b.m.vel})
+            if ((rc = dev_alloc(ctx, q, 3 * np))) return rc;
+        if ((rc = dev_alloc(ctx, &b.m.t, np)) || (rc = dev_alloc(ctx, &b.m.tq, np))) return rc;
+        for (float **q : {&b.m.af, &b.m.jf})
+            if ((rc = dev_alloc(ctx, q, 3 * np))) return rc;
+    }
     if ((rc = dev_alloc(ctx, &b.part, nc))) return rc;
     if ((rc = dev_alloc(ctx, &b.flag, nflag))) return rc;
     for (int **q : {&b.cnt, &b.chunk_off})
@@ -886,8 +897,7 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
     b.t = bs.t;
     b.dt = bs.dt;
     b.tq = bs.tq;
-    b.af = bs.af;
-    b.jf = bs.jf;
+    b.mirror = bs.m;
     b.dt_min = bs.dt_min;
     b.dt_max = bs.dt_max;
     b.part = bs.part;
@@ -928,6 +938,14 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
     return b;
 }
 
+cudaError_t launch_mirror(nbody_ctx *ctx, const double *pos, const double *vel, const double *acc,
+                          const double *jerk, cudaStream_t s) {
+    const JerkPath &j = ctx->jp;
+    const BlockState &bs = ctx->bs;
+    return launch_block_mirror(j.perm, j.dcl, j.tile_cluster, j.tc, ctx->n, pos, vel, bs.t, bs.tq, acc, jerk,
+                               bs.m, s);
+}
+
 // One block step (see block_sched.cu, block_force.cu): schedule, predict, pack the predicted j-set,
 // forces + jerks of the active subset, correct and re-step the active ones.
 int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, bool capturing,
@@ -938,17 +956,19 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
     BlockLaunch b = block_launch(ctx, a);
     b.fresh = reorder;
     int rc;
-    if (ctx->mode == NBODY_F32C && reorder)
+    if (ctx->mode == NBODY_F32C && reorder) {
         NB_CUDA(launch_reorder(a.pos, ctx->n, ctx->chunks, ctx->n_chunks, ctx->chunk_first, ctx->ncl, j.dcl,
                                ctx->bpart, ctx->bbox, ctx->keys, ctx->vals, ctx->sort_n, ctx->max_cluster,
                                j.perm, s, kernels));
+        NB_CUDA(launch_mirror(ctx, a.pos, a.vel, a.acc, a.jerk, s));
+        ++*kernels;
+    }
     NB_CUDA(launch_block_prepare(b, s, kernels));
     NB_CUDA(launch_block_queue(b, s, kernels));
     BlockCorrect corr{};
     corr.sc = bs.sc;
     corr.level = bs.sc->level;
-    corr.af = bs.af;  // null on the FP64 path
-    corr.jf = bs.jf;
+    corr.m = bs.m;  // empty on the FP64 path
     corr.t = bs.t;
     corr.dt = bs.dt;
     corr.tq = bs.tq;
@@ -1546,8 +1566,8 @@ int nbody_block_start(nbody_ctx *ctx, const double *pos, const double *vel, cons
     b.eta = eta;
     NB_CUDA(launch_block_init(ctx->n, acc, jerk, dt_max, dt_min, eta_s, b.t, b.dt, b.tq, s));
     NB_CUDA(cudaMemsetAsync(b.sc, 0, sizeof(BlockScalars), s));
-    if (b.af) {
-        NB_CUDA(launch_block_shadow(ctx->n, acc, jerk, b.af, b.jf, s));
+    if (b.m.pos) {
+        NB_CUDA(launch_mirror(ctx, pos, vel, acc, jerk, s));
         ctx->launches += 1;
     }
     // level counts and the first t_next (later steps set the next one themselves)
@@ -1578,6 +1598,10 @@ int nbody_block_advance(nbody_ctx *ctx, double *pos, double *vel, const double *
         if (!q || !is_device_ptr(q)) return fail(ctx, NBODY_EINVAL, "block steps need device arrays");
     if (pot && !is_device_ptr(pot)) return fail(ctx, NBODY_EINVAL, "block steps need device arrays");
     cudaStream_t s = (cudaStream_t)stream;
+    if (b.m.pos) {  // the rows are the caller's: take them as they are now
+        NB_CUDA(launch_mirror(ctx, pos, vel, acc, jerk, s));
+        ctx->launches += 1;
+    }
     NB_CUDA(cudaMemcpyAsync(&b.sc->t_end, &t_end, sizeof(double), cudaMemcpyHostToDevice, s));
     BlockScalars h{};
     NB_CUDA(cudaMemcpyAsync(&h, b.sc, sizeof h, cudaMemcpyDeviceToHost, s));

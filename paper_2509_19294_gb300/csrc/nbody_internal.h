@@ -158,10 +158,22 @@ struct BlockScalars {
 // packed predicted particles), perm (slot -> row) and the outputs (rows).
 // Hermite corrector + next-step choice of the block scheme, applied where an
 // active particle's acceleration and jerk become final (block_common.cuh).
+// F32C block steps: the state the packing predictor reads, kept in j-set slot
+// order so that its loads are contiguous (the caller's arrays stay in row
+// order).  Rebuilt from the rows after every re-sort; the corrector updates
+// both.  a and a' are kept as FP32 copies (the predictor's higher-order terms).
+struct SlotMirror {
+    double *pos, *vel;  // [3][n_pad]
+    double *t;          // [n_pad]
+    long long *tq;      // [n_pad]
+    float *af, *jf;     // [3][n_pad]
+    int64_t n_pad;
+};
+
 struct BlockCorrect {
     const BlockScalars *sc;
     int *level;  // BlockScalars::level (the corrector moves particles between levels)
-    float *af, *jf;  // FP32 copies of a, a' (F32C packing predictor), or null
+    SlotMirror m;  // m.pos == null: no mirror (FP64 path)
     double *t, *dt, *pos, *vel, *acc, *jerk, *pot;  // rows; acc, jerk: the particle's a0, j0
     long long *tq;
     int64_t n;
@@ -213,8 +225,8 @@ struct BlockLaunch {
     long long *tq;  // t_i + dt_i in units of dt_min (exact: steps are powers of two >= dt_min)
     double dt_min, dt_max;
     double *pos, *vel, *acc, *jerk, *xp, *vp;
-    const float *af, *jf;  // FP32 copies of a, a' (F32C)
-    bool fresh;            // the j-set was just re-sorted (tile centres from scratch)
+    SlotMirror mirror;  // F32C: the packing predictor's slot-ordered state
+    bool fresh;         // the j-set was just re-sorted (tile centres from scratch)
     const double *mass;
     uint8_t *flag;  // per row (FP64) or per j-set slot (F32C)
     // per row chunk (FP64) or per centre tile (F32C): active counts, offsets
@@ -255,9 +267,12 @@ int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap);
 cudaError_t launch_subset_tail(int max_chunks, int max_cs, int max_ctas, const F32CSubsetParams &prm,
                                const int32_t *act, BlockScalars *sc, double *few_part, const SubItem *info,
                                cudaStream_t s);
-// FP32 copies of a, a' (start of block stepping, F32C).
-cudaError_t launch_block_shadow(int64_t n, const double *acc, const double *jerk, float *af, float *jf,
-                                cudaStream_t s);
+// (Re)build the slot-ordered mirror from the rows through perm (F32C: start of
+// block stepping, every re-sort, every advance call).
+cudaError_t launch_block_mirror(const int32_t *perm, const ClusterDev *cl, const int32_t *tile_cluster,
+                                int tc, int64_t n, const double *pos, const double *vel, const double *t,
+                                const long long *tq, const double *acc, const double *jerk,
+                                const SlotMirror &m, cudaStream_t s);
 // Level counts of all particles and the first t_next (start of block stepping).
 cudaError_t launch_block_levels(int64_t n, const double *dt, double dt_max, double dt_min,
                                 const Chunk *chunks, int n_chunks, const long long *tq, double *part,
