@@ -104,17 +104,19 @@ __device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t 
 // (0..2) corrects component sub, the norms are summed across the three lanes
 // in component order, and lane 0 chooses the step.  Every lane of the warp
 // calls it (the shuffles need them); lanes with valid == false store nothing.
-__device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64_t i, int slot, bool valid,
-                                                    int sub, double a1, double j1, double p1, double tn,
-                                                    long long tnq) {
-    const double h = c.dt[i], h2 = h * h;
+// The particle's step h and its component sub of a0, j0, v0, x0 come in as
+// arguments (loaded ahead of time by the caller, or by correct_particle_x4).
+__device__ __forceinline__ void correct_particle_x4_pre(const BlockCorrect &c, int64_t i, int slot, bool valid,
+                                                        int sub, double h, double a0, double j0, double v0,
+                                                        double x0, double a1, double j1, double p1, double tn,
+                                                        long long tnq) {
+    const double h2 = h * h;
     const double ih = recip_pow2(h), ih2 = ih * ih, ih3 = ih2 * ih;
     double sq[4] = {0.0, 0.0, 0.0, 0.0};  // this component's a1^2, j1^2, a2^2, a3^2
     if (sub < 3) {
         const int64_t q = sub * c.n + i;
-        const double a0 = c.acc[q], j0 = c.jerk[q], v0 = c.vel[q];
         const double v1 = v0 + (a0 + a1) * h / 2.0 + (j0 - j1) * h2 / 12.0;
-        const double x1 = c.pos[q] + (v0 + v1) * h / 2.0 + (a0 - a1) * h2 / 12.0;
+        const double x1 = x0 + (v0 + v1) * h / 2.0 + (a0 - a1) * h2 / 12.0;
         const double a3 = (12.0 * (a0 - a1) + 6.0 * h * (j0 + j1)) * ih3;
         const double a2 = (-6.0 * (a0 - a1) - h * (4.0 * j0 + 2.0 * j1)) * ih2 + h * a3;
         if (valid) {
@@ -147,6 +149,21 @@ __device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64
     if (sub != 0 || !valid) return;
     if (c.pot) c.pot[i] = p1;
     choose_step(c, i, slot, h, nrm[0], nrm[1], nrm[2], nrm[3], tn, tnq);
+}
+
+__device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64_t i, int slot, bool valid,
+                                                    int sub, double a1, double j1, double p1, double tn,
+                                                    long long tnq) {
+    const double h = c.dt[i];
+    double a0 = 0.0, j0 = 0.0, v0 = 0.0, x0 = 0.0;
+    if (sub < 3) {
+        const int64_t q = sub * c.n + i;
+        a0 = c.acc[q];
+        j0 = c.jerk[q];
+        v0 = c.vel[q];
+        x0 = c.pos[q];
+    }
+    correct_particle_x4_pre(c, i, slot, valid, sub, h, a0, j0, v0, x0, a1, j1, p1, tn, tnq);
 }
 
 // FP64 epilogue of one active particle: scale by G, remove the self term of

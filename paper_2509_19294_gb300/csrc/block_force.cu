@@ -18,6 +18,19 @@
 
 namespace nbody {
 
+// Asynchronous global -> shared copies (no register staging); the caller
+// commits them and waits before reading the shared copy.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 namespace {
 
 // Subset kernel: persistent CTAs over the device-built queue of (i-chunk of the
@@ -235,6 +248,11 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
     __shared__ double fsum[kFewThreads];  // [group][output], ngrp * n_out <= kFewThreads
     __shared__ int fjb[kFewMax + 1], fcl[kFewMax], fab[kFewMax], fsb[kFewMax];
     __shared__ float fe2[kFewMax];
+    // the corrector's inputs, fetched by cp.async while the j-loop runs: per
+    // particle h, then a0, j0, v0, x0 of each component; its mass
+    __shared__ double pre[kFewMax][13];
+    __shared__ int64_t pre_u[kFewMax];
+    __shared__ float pre_m[kFewMax];
     __shared__ bool last;
     if (!sc->few) return;  // uniform: the plan chose the subset kernel
     const int na = sc->n_active;
@@ -266,7 +284,23 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
         int e = 0;
         while (e + 1 < nf && fab[e + 1] <= a) ++e;
         ocl[a] = e;  // index into the few-cluster list
+        if (q.corr.sc) {
+            const BlockCorrect &c = q.corr;
+            const int64_t u = p.perm[slot];
+            pre_u[a] = u;
+            cp_async8(&pre[a][0], c.dt + u);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int64_t k = d * c.n + u;
+                cp_async8(&pre[a][1 + 4 * d], c.acc + k);
+                cp_async8(&pre[a][2 + 4 * d], c.jerk + k);
+                cp_async8(&pre[a][3 + 4 * d], c.vel + k);
+                cp_async8(&pre[a][4 + 4 * d], c.pos + k);
+            }
+            cp_async4(&pre_m[a], p.pm + slot);
+        }
     }
+    cp_async_commit();
     __syncthreads();
     const int jtot = fjb[nf];
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
@@ -372,6 +406,7 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
         }
         __syncthreads();
     }
+    cp_async_wait_all();  // long done: the j-loop took longer (the smem is read after a barrier)
     double *mine = part + (size_t)blockIdx.x * kFewMax * 7;
     for (int t = threadIdx.x; t < na * 7; t += blockDim.x) mine[t] = csum[t / 7][t % 7];
     __threadfence();
@@ -417,13 +452,14 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
             const int a = threadIdx.x / 4, sub = threadIdx.x % 4;
             const bool valid = a < na;
             const int aa = valid ? a : 0;
-            const ClusterDev cl = p.cl[fcl[ocl[aa]]];
-            const int slot = act[aa];
+            const float e2 = fe2[ocl[aa]];
             double ph = csum[aa][6];
-            if (cl.eps2f > 0.0f) ph -= (double)__fmul_rn(p.pm[slot], rsqrt_mufu(cl.eps2f));
-            correct_particle_x4(q.corr, p.perm[slot], slot, valid, sub, p.G * csum[aa][sub < 3 ? sub : 0],
-                                p.G * csum[aa][sub < 3 ? 3 + sub : 3], -p.G * ph, sc->t_next,
-                                sc->t_next_q);
+            if (e2 > 0.0f) ph -= (double)__fmul_rn(pre_m[aa], rsqrt_mufu(e2));
+            const int cp = sub < 3 ? sub : 0;
+            correct_particle_x4_pre(q.corr, pre_u[aa], act[aa], valid, sub, pre[aa][0], pre[aa][1 + 4 * cp],
+                                    pre[aa][2 + 4 * cp], pre[aa][3 + 4 * cp], pre[aa][4 + 4 * cp],
+                                    p.G * csum[aa][cp], p.G * csum[aa][3 + cp], -p.G * ph, sc->t_next,
+                                    sc->t_next_q);
         }
     } else {
         for (int a = threadIdx.x; a < na; a += blockDim.x) {

@@ -374,7 +374,7 @@ constexpr int kPackMaxPer = 4;  // slots per thread in block_pack_kernel (tc <= 
 // are FP64 differences from it, rounded once to FP32.  It is stored as a
 // float (lo = 0).  One CTA per tile, so the previous offsets are all read
 // before the CTA overwrites them.
-template <int NT, bool FRESH>
+template <int NT, int PER, bool FRESH>
 __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q) {
     __shared__ float redf[NT / 32][8];
     __shared__ double cen[6];
@@ -387,17 +387,16 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
     const double tn = (double)tnq * q.dt_min;
     const bool live = tn <= q.sc->t_end;
     const ClusterDev cl = q.cl[q.tile_cluster[tile]];
-    const int base = tile * q.tc;
-    const int per = q.tc / NT;
+    const int base = tile * NT * PER;  // tc = NT * PER slots per tile
     float sf[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // position, velocity sums (6), count, active count
-    double x[kPackMaxPer][6];
-    float dvel[kPackMaxPer][3];
-    bool act[kPackMaxPer];
+    double x[PER][6];
+    float dvel[PER][3];
+    bool act[PER];
 #pragma unroll
-    for (int r = 0; r < kPackMaxPer; ++r) {
+    for (int r = 0; r < PER; ++r) {
         act[r] = false;
         const int slot = base + threadIdx.x + NT * r;
-        if (r < per && slot - cl.slot_begin < cl.n) {
+        if (slot - cl.slot_begin < cl.n) {
             predict_mixed(q.m, slot, tn, x[r], dvel[r]);
             if (FRESH) {
 #pragma unroll
@@ -458,9 +457,8 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
 #pragma unroll
     for (int d = 0; d < 6; ++d) c[d] = cen[d];
 #pragma unroll
-    for (int r = 0; r < kPackMaxPer; ++r) {
+    for (int r = 0; r < PER; ++r) {
         const int slot = base + threadIdx.x + NT * r;
-        if (r >= per) break;
         if (slot - cl.slot_begin < cl.n) {
             q.px[slot] = (float)(x[r][0] - c[0]);
             q.py[slot] = (float)(x[r][1] - c[1]);
@@ -683,13 +681,17 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         q.partial_cap = b.partial_cap;
         q.dt_max = b.dt_max;
         q.dt_min = b.dt_min;
-        if (b.tc % 256 == 0) {
-            if (b.fresh) NB_BL((block_pack_kernel<256, true><<<b.n_tiles, 256, 0, s>>>(q)));
-            else NB_BL((block_pack_kernel<256, false><<<b.n_tiles, 256, 0, s>>>(q)));
-        } else {
-            if (b.fresh) NB_BL((block_pack_kernel<128, true><<<b.n_tiles, 128, 0, s>>>(q)));
-            else NB_BL((block_pack_kernel<128, false><<<b.n_tiles, 128, 0, s>>>(q)));
-        }
+        // tc = NT * PER, NT = 256 where tc allows it (checked above: PER <= 4)
+#define NB_PACK(NT_, PER_)                                                                  \
+    if (b.tc == (NT_) * (PER_)) {                                                           \
+        if (b.fresh) NB_BL((block_pack_kernel<NT_, PER_, true><<<b.n_tiles, NT_, 0, s>>>(q))); \
+        else NB_BL((block_pack_kernel<NT_, PER_, false><<<b.n_tiles, NT_, 0, s>>>(q)));        \
+        return cudaSuccess;                                                                 \
+    }
+        NB_PACK(256, 1) NB_PACK(256, 2) NB_PACK(256, 3) NB_PACK(256, 4)
+        NB_PACK(128, 1) NB_PACK(128, 3)
+#undef NB_PACK
+        return cudaErrorInvalidValue;
     } else {
         NB_BL((block_predict_kernel<<<grid_of(b.n, 256), 256, 0, s>>>(
             b.n, b.sc, b.t, b.tq, b.pos, b.vel, b.acc, b.jerk, b.xp, b.vp, b.flag)));
