@@ -44,8 +44,8 @@ __device__ __forceinline__ void choose_step(const BlockCorrect &c, int64_t i, in
     const double inv_dt_min = recip_pow2(c.dt_min);
     double nd = h;
     while (nd > da && nd > c.dt_min) nd *= 0.5;
-    const long long q2 = (long long)(2.0 * h * inv_dt_min);  // 2h in units of dt_min
-    if (nd == h && da >= 2.0 * h && 2.0 * h <= c.dt_max && tnq % q2 == 0) nd = 2.0 * h;
+    const long long q2 = (long long)(2.0 * h * inv_dt_min);  // 2h in units of dt_min: a power of two
+    if (nd == h && da >= 2.0 * h && 2.0 * h <= c.dt_max && (tnq & (q2 - 1)) == 0) nd = 2.0 * h;
     if (c.level && nd != h) {
         atomicSub(&c.level[block_level(h, c.dt_max)], 1);
         atomicAdd(&c.level[block_level(nd, c.dt_max)], 1);
@@ -54,10 +54,33 @@ __device__ __forceinline__ void choose_step(const BlockCorrect &c, int64_t i, in
     c.t[i] = tn;
     c.dt[i] = nd;
     c.tq[i] = tq_next;
-    if (c.m.pos) {
-        c.m.t[slot] = tn;
+    if (c.m.xr) {
+        c.m.tcq[slot] = tnq;
         c.m.tq[slot] = tq_next;
     }
+}
+
+// Component d of the tile frame of j-set slot `slot` at time tnq (units of
+// dt_min): its position c0 + cv (t - t0) in FP64 and its velocity cv.
+__device__ __forceinline__ void frame_component(const BlockCorrect &c, int slot, int d, long long tnq, double &fc,
+                                                double &fv) {
+    const int tile = slot / c.m.tc;
+    fv = (double)reinterpret_cast<const float *>(c.m.vchl + 2 * tile)[d];
+    fc = fma(fv, (double)(tnq - c.sc->frame_t0q) * c.dt_min, c.m.c0[(int64_t)d * c.m.n_tiles + tile]);
+}
+
+// The slot's mirror after a correction to time tnq (F32C): offsets from the
+// frame (fc, fv: the frame's position and velocity component at tnq).
+__device__ __forceinline__ void mirror_store(const BlockCorrect &c, int slot, int d, double x1, double v1,
+                                             double a1, double j1, double fc, double fv) {
+    const int64_t qs = d * c.m.n_pad + slot;
+    const double xr = x1 - fc;
+    const float hi = (float)xr;
+    c.m.xr[qs] = hi;
+    c.m.xl[qs] = (float)(xr - (double)hi);
+    c.m.vr[qs] = (float)(v1 - fv);
+    c.m.af[qs] = (float)a1;
+    c.m.jf[qs] = (float)j1;
 }
 
 // Hermite corrector of active particle (row) i over its step h = dt_i with the
@@ -84,12 +107,10 @@ __device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t 
         A2[d] = (-6.0 * (a0 - A1[d]) - h * (4.0 * j0 + 2.0 * J1[d])) * ih2 + h * A3[d];
         c.acc[q] = A1[d];
         c.jerk[q] = J1[d];
-        if (c.m.pos) {
-            const int64_t qs = d * c.m.n_pad + slot;
-            c.m.pos[qs] = x1;
-            c.m.vel[qs] = v1;
-            c.m.af[qs] = (float)A1[d];
-            c.m.jf[qs] = (float)J1[d];
+        if (c.m.xr) {
+            double fc, fv;
+            frame_component(c, slot, d, tnq, fc, fv);
+            mirror_store(c, slot, d, x1, v1, A1[d], J1[d], fc, fv);
         }
     }
     if (c.pot) c.pot[i] = p1;
@@ -104,12 +125,13 @@ __device__ __forceinline__ void correct_particle(const BlockCorrect &c, int64_t 
 // (0..2) corrects component sub, the norms are summed across the three lanes
 // in component order, and lane 0 chooses the step.  Every lane of the warp
 // calls it (the shuffles need them); lanes with valid == false store nothing.
-// The particle's step h and its component sub of a0, j0, v0, x0 come in as
-// arguments (loaded ahead of time by the caller, or by correct_particle_x4).
+// The particle's step h, its component sub of a0, j0, v0, x0 and (with a
+// mirror) of its tile frame at tnq, fc and fv, come in as arguments (loaded
+// ahead of time by the caller, or by correct_particle_x4).
 __device__ __forceinline__ void correct_particle_x4_pre(const BlockCorrect &c, int64_t i, int slot, bool valid,
                                                         int sub, double h, double a0, double j0, double v0,
-                                                        double x0, double a1, double j1, double p1, double tn,
-                                                        long long tnq) {
+                                                        double x0, double fc, double fv, double a1, double j1,
+                                                        double p1, double tn, long long tnq) {
     const double h2 = h * h;
     const double ih = recip_pow2(h), ih2 = ih * ih, ih3 = ih2 * ih;
     double sq[4] = {0.0, 0.0, 0.0, 0.0};  // this component's a1^2, j1^2, a2^2, a3^2
@@ -124,13 +146,7 @@ __device__ __forceinline__ void correct_particle_x4_pre(const BlockCorrect &c, i
             c.vel[q] = v1;
             c.acc[q] = a1;
             c.jerk[q] = j1;
-            if (c.m.pos) {
-                const int64_t qs = sub * c.m.n_pad + slot;
-                c.m.pos[qs] = x1;
-                c.m.vel[qs] = v1;
-                c.m.af[qs] = (float)a1;
-                c.m.jf[qs] = (float)j1;
-            }
+            if (c.m.xr) mirror_store(c, slot, sub, x1, v1, a1, j1, fc, fv);
         }
         sq[0] = a1 * a1;
         sq[1] = j1 * j1;
@@ -155,15 +171,16 @@ __device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64
                                                     int sub, double a1, double j1, double p1, double tn,
                                                     long long tnq) {
     const double h = c.dt[i];
-    double a0 = 0.0, j0 = 0.0, v0 = 0.0, x0 = 0.0;
+    double a0 = 0.0, j0 = 0.0, v0 = 0.0, x0 = 0.0, fc = 0.0, fv = 0.0;
     if (sub < 3) {
         const int64_t q = sub * c.n + i;
         a0 = c.acc[q];
         j0 = c.jerk[q];
         v0 = c.vel[q];
         x0 = c.pos[q];
+        if (c.m.xr) frame_component(c, slot, sub, tnq, fc, fv);
     }
-    correct_particle_x4_pre(c, i, slot, valid, sub, h, a0, j0, v0, x0, a1, j1, p1, tn, tnq);
+    correct_particle_x4_pre(c, i, slot, valid, sub, h, a0, j0, v0, x0, fc, fv, a1, j1, p1, tn, tnq);
 }
 
 // FP64 epilogue of one active particle: scale by G, remove the self term of

@@ -28,6 +28,10 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(BLOCK * G, MINB) subset_jerk_kernel(const F32C
 // Per thread and per warp FP32 sums, then FP64: the warps in order, the CTAs in
 // a fixed order by the last CTA (ticket), which also applies the epilogue.
 constexpr int kFewThreads = 256;
-constexpr int kFewBatch = 8;
+constexpr int kFewBatch = 6;
 constexpr int kFewUnroll = 2;
 
 __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ act, BlockScalars *sc,
@@ -241,6 +245,7 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
     constexpr int nctas = kFewCtas;  // the CTAs taking part: blockIdx.x < kFewCtas
     const F32CJerkParams &p = q.base;
     __shared__ float own[kFewMax][6];
+    __shared__ float ownl[kFewMax][3];  // low parts of the position offsets
     __shared__ float4 oc[kFewMax][4];
     __shared__ int ocl[kFewMax];
     __shared__ float wsum[kFewThreads / 32][kFewBatch][7];
@@ -249,10 +254,14 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
     __shared__ int fjb[kFewMax + 1], fcl[kFewMax], fab[kFewMax], fsb[kFewMax];
     __shared__ float fe2[kFewMax];
     // the corrector's inputs, fetched by cp.async while the j-loop runs: per
-    // particle h, then a0, j0, v0, x0 of each component; its mass
+    // particle h, then a0, j0, v0, x0 of each component; its mass; with a
+    // mirror, its tile frame (origin c0, velocity) and the frame time
     __shared__ double pre[kFewMax][13];
     __shared__ int64_t pre_u[kFewMax];
     __shared__ float pre_m[kFewMax];
+    __shared__ double pre_c0[kFewMax][3];
+    __shared__ float4 pre_cv[kFewMax];
+    __shared__ long long pre_t0q;
     __shared__ bool last;
     if (!sc->few) return;  // uniform: the plan chose the subset kernel
     const int na = sc->n_active;
@@ -276,6 +285,9 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
         own[a][3] = p.pvx[slot];
         own[a][4] = p.pvy[slot];
         own[a][5] = p.pvz[slot];
+        ownl[a][0] = q.pxl ? q.pxl[slot] : 0.0f;
+        ownl[a][1] = q.pyl ? q.pyl[slot] : 0.0f;
+        ownl[a][2] = q.pzl ? q.pzl[slot] : 0.0f;
         const int tile = slot / p.tc;
         oc[a][0] = p.chl[2 * tile];
         oc[a][1] = p.chl[2 * tile + 1];
@@ -298,6 +310,13 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
                 cp_async8(&pre[a][4 + 4 * d], c.pos + k);
             }
             cp_async4(&pre_m[a], p.pm + slot);
+            if (c.m.xr) {
+                const int tile = slot / c.m.tc;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) cp_async8(&pre_c0[a][d], c.m.c0 + (int64_t)d * c.m.n_tiles + tile);
+                cp_async16(&pre_cv[a], c.m.vchl + 2 * tile);
+                if (a == 0) cp_async8(&pre_t0q, &sc->frame_t0q);
+            }
         }
     }
     cp_async_commit();
@@ -313,7 +332,7 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
             for (int c = 0; c < 7; ++c) acc[k][c] = 0.0f;
         for (int g0 = blockIdx.x * kFewThreads + threadIdx.x; g0 < jtot; g0 += kFewUnroll * stride) {
             // the loads of kFewUnroll j-particles first, so their latencies overlap
-            float J[kFewUnroll][7];
+            float J[kFewUnroll][7], Jl[kFewUnroll][3];
             float4 jcen[kFewUnroll][4];
             int ej[kFewUnroll];
 #pragma unroll
@@ -332,6 +351,9 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
                     J[u][4] = p.pvx[js];
                     J[u][5] = p.pvy[js];
                     J[u][6] = p.pvz[js];
+                    Jl[u][0] = q.pxl ? q.pxl[js] : 0.0f;
+                    Jl[u][1] = q.pyl ? q.pyl[js] : 0.0f;
+                    Jl[u][2] = q.pzl ? q.pzl[js] : 0.0f;
                     const int jt = js / p.tc;
                     jcen[u][0] = p.chl[2 * jt];
                     jcen[u][1] = p.chl[2 * jt + 1];
@@ -361,8 +383,17 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
                     for (int q = 0; q < 6; ++q) {
                         float hi, lo;
                         centre_diff(ih[q], il[q], jh[q], jl[q], hi, lo);
-                        r[q] = __fsub_rn(J[u][q < 3 ? q : q + 1],
-                                         __fadd_rn(__fadd_rn(own[a][q], hi), lo));
+                        if (q < 3) {
+                            // positions to ~2^-48 of the offsets: with s + e =
+                            // own + hi exactly (TwoSum), r = (J - s) + (Jl -
+                            // (ownl + lo + e)); J - s is exact for close pairs
+                            const float sm = __fadd_rn(own[a][q], hi), bb = __fsub_rn(sm, own[a][q]);
+                            const float e = __fadd_rn(__fsub_rn(own[a][q], __fsub_rn(sm, bb)), __fsub_rn(hi, bb));
+                            r[q] = __fadd_rn(__fsub_rn(J[u][q], sm),
+                                             __fsub_rn(Jl[u][q], __fadd_rn(__fadd_rn(ownl[a][q], lo), e)));
+                        } else {
+                            r[q] = __fsub_rn(J[u][q + 1], __fadd_rn(__fadd_rn(own[a][q], hi), lo));
+                        }
                     }
                     float r2 = __fmaf_rn(r[0], r[0], e2);
                     r2 = __fmaf_rn(r[1], r[1], r2);
@@ -456,10 +487,15 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
             double ph = csum[aa][6];
             if (e2 > 0.0f) ph -= (double)__fmul_rn(pre_m[aa], rsqrt_mufu(e2));
             const int cp = sub < 3 ? sub : 0;
+            const long long tnq = sc->t_next_q;
+            double fc = 0.0, fv = 0.0;
+            if (q.corr.m.xr) {  // the tile frame at t_next
+                fv = (double)reinterpret_cast<const float *>(&pre_cv[aa])[cp];
+                fc = fma(fv, (double)(tnq - pre_t0q) * q.corr.dt_min, pre_c0[aa][cp]);
+            }
             correct_particle_x4_pre(q.corr, pre_u[aa], act[aa], valid, sub, pre[aa][0], pre[aa][1 + 4 * cp],
-                                    pre[aa][2 + 4 * cp], pre[aa][3 + 4 * cp], pre[aa][4 + 4 * cp],
-                                    p.G * csum[aa][cp], p.G * csum[aa][3 + cp], -p.G * ph, sc->t_next,
-                                    sc->t_next_q);
+                                    pre[aa][2 + 4 * cp], pre[aa][3 + 4 * cp], pre[aa][4 + 4 * cp], fc, fv,
+                                    p.G * csum[aa][cp], p.G * csum[aa][3 + cp], -p.G * ph, sc->t_next, tnq);
         }
     } else {
         for (int a = threadIdx.x; a < na; a += blockDim.x) {
@@ -524,7 +560,7 @@ __device__ void reduce_pass(const F32CSubsetParams &q, const SubItem *__restrict
 // empty queue in the few-particle case).
 static_assert(kFewThreads == 32 * kReduceWarps, "one block size for both passes");
 
-__global__ void __launch_bounds__(kFewThreads)
+__global__ void __launch_bounds__(kFewThreads, 2)
     subset_tail_kernel(const F32CSubsetParams q, const int32_t *__restrict__ act, BlockScalars *sc,
                        double *__restrict__ few_part, const SubItem *__restrict__ info) {
     if (sc->few) {  // uniform

@@ -53,33 +53,6 @@ __global__ void block_init_kernel(int64_t n, const double *acc, const double *je
     }
 }
 
-// The packing predictor's state in j-set slot order (F32C): gathered from the
-// rows through perm at the start of block stepping, after every re-sort and at
-// the start of every advance call (the caller may have changed the rows).
-__global__ void block_mirror_kernel(const int32_t *__restrict__ perm, const ClusterDev *__restrict__ cl,
-                                    const int32_t *__restrict__ tile_cluster, int tc, int64_t n,
-                                    const double *__restrict__ pos, const double *__restrict__ vel,
-                                    const double *__restrict__ t, const long long *__restrict__ tq,
-                                    const double *__restrict__ acc, const double *__restrict__ jerk,
-                                    const SlotMirror m) {
-    for (int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; slot < m.n_pad;
-         slot += (int64_t)gridDim.x * blockDim.x) {
-        const ClusterDev c = cl[tile_cluster[slot / tc]];
-        if (slot - c.slot_begin >= c.n) continue;  // padding: never read
-        const int64_t u = perm[slot];
-        m.t[slot] = t[u];
-        m.tq[slot] = tq[u];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int64_t k = d * n + u, ks = d * m.n_pad + slot;
-            m.pos[ks] = pos[k];
-            m.vel[ks] = vel[k];
-            m.af[ks] = (float)acc[k];
-            m.jf[ks] = (float)jerk[k];
-        }
-    }
-}
-
 // Count the particles per step level (start of block stepping).
 __global__ void block_levels_kernel(int64_t n, const double *__restrict__ dt, double dt_max,
                                     BlockScalars *sc) {
@@ -314,19 +287,23 @@ __global__ void __launch_bounds__(kScan)
 }
 
 // F32C: one CTA per centre tile of the j-set.  Predicts the tile's particles to
-// t_next (FP64, as block_predict_kernel), packs them as pack_kernel does
-// (FP64 mean position and velocity as float pairs, FP32 offsets, FP32 masses,
-// pads far away with mass 0), flags the active slots and counts them.  The
-// last CTA to finish (ticket) scans the tile counts and plans the step.
+// t_next, packs them as the j-set (FP32 offsets from the tile centre, FP32
+// masses, pads far away with mass 0), flags the active slots and counts them.
+// The last CTA to finish (ticket) scans the tile counts and plans the step.
+// Two forms: block_fresh_kernel (after a re-sort, at the start of an advance)
+// gathers the FP64 rows through perm, sets each tile's frame and writes the
+// slot mirror; block_pack_kernel (every other step) reads only the FP32 mirror.
 struct BlockPackParams {
     const int32_t *perm;
     const ClusterDev *cl;
     const int32_t *tile_cluster;
     int tc, n_tiles;
     int64_t n;
-    const double *mass;
-    SlotMirror m;  // slot-ordered pos, vel, t, tq and FP32 a, a' (kept by the corrector)
+    const double *mass, *t, *pos, *vel, *acc, *jerk;  // rows (fresh pack)
+    const long long *tq;                               // rows (fresh pack)
+    SlotMirror m;
     float *px, *py, *pz, *pm, *pvx, *pvy, *pvz;
+    float *pxl, *pyl, *pzl;  // low parts: px + pxl is the offset to ~2^-48 relative
     float4 *chl, *vchl;
     uint8_t *flag;  // per slot
     int *tile_cnt, *tile_off;
@@ -341,49 +318,83 @@ struct BlockPackParams {
     double dt_max, dt_min;
 };
 
-// Hermite predictor for the packed j-set (F32C): x + h v in FP64, the
-// higher-order terms h^2 (a/2 + h a'/6) and h (a + h a'/2) in FP32 from FP32
-// copies of a and a'.  They are small against the step's displacement, so
-// their FP32 rounding stays far below that of the packed FP32 offsets; FP64
-// operations, scarce on this part, drop from 24 to 11 per particle (the
-// velocity change is returned apart, for the packed offset).
-__device__ __forceinline__ void predict_mixed(const SlotMirror &m, int64_t slot, double tn,
-                                              double (&x)[6], float (&dv)[3]) {
-    const double h = tn - m.t[slot];
+// The step's time in units of dt_min (block_next_time_q with the level scan
+// done by one warp-wide ballot instead of a loop of dependent loads; every
+// lane of the warp calls it).
+__device__ __forceinline__ long long next_time_q_warp(const BlockScalars *sc, double dt_max, double dt_min) {
+    const int lane = threadIdx.x % 32;
+    const long long tq_now = sc->t_next_q;
+    const int n_moved = sc->n_active;
+    const unsigned lo = __ballot_sync(0xffffffffu, sc->level[lane] != 0);
+    const unsigned hi = __ballot_sync(0xffffffffu, sc->level[lane + 32] != 0);
+    if (n_moved == 0) return tq_now;
+    const int kmax = block_level(dt_min, dt_max);
+    unsigned long long occ = ((unsigned long long)hi << 32) | lo;
+    if (kmax < 63) occ &= (2ULL << kmax) - 1;  // levels 0 .. kmax
+    const int k = occ ? 63 - __clzll((long long)occ) : 0;
+    const int sh = kmax - k;  // the smallest occupied step is 2^sh dt_min
+    return ((tq_now >> sh) + 1) << sh;
+}
+
+// The last CTA to arrive scans the tile counts and plans the step.
+template <int NT>
+__device__ __forceinline__ void pack_tail(const BlockPackParams &q, long long tnq, bool fresh) {
+    __shared__ bool last;
+    __shared__ int total;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&q.sc->ticket_pack, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    block_exclusive_scan<NT>(q.tile_cnt, q.tile_off, q.n_tiles, &total);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        q.sc->t_next_q = tnq;
+        q.sc->t_next = (double)tnq * q.dt_min;
+        if (fresh) q.sc->frame_t0q = tnq;
+        plan_step(q.tile_off, total, q.n_tiles, q.tile_first, q.ncl, q.cl, q.cs, q.workers, q.max_split,
+                  q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max, q.cs_large,
+                  q.workers_large, q.large_min, q.partial_cap);
+        q.sc->ticket_pack = 0;
+    }
+}
+
+// Hermite predictor from the rows (fresh pack): x + h v in FP64, the
+// higher-order terms h^2 (a/2 + h a'/6) and h (a + h a'/2) in FP32 (small
+// against the step's displacement; their FP32 rounding stays far below that of
+// the packed FP32 offsets).  The velocity change is returned apart, for the
+// packed offset.
+__device__ __forceinline__ void predict_rows(const BlockPackParams &q, int64_t u, double tn, double (&x)[6],
+                                             float (&dv)[3]) {
+    const double h = tn - q.t[u];
     const float hf = (float)h;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const int64_t k = d * m.n_pad + slot;
-        const float a = m.af[k], j = m.jf[k];
+        const int64_t k = d * q.n + u;
+        const float a = (float)q.acc[k], j = (float)q.jerk[k];
         const float dx = hf * hf * (0.5f * a + hf * (j * (1.0f / 6.0f)));
         dv[d] = hf * (a + hf * (0.5f * j));
-        const double v = m.vel[k];
-        x[d] = fma(h, v, m.pos[k]) + (double)dx;
+        const double v = q.vel[k];
+        x[d] = fma(h, v, q.pos[k]) + (double)dx;
         x[3 + d] = v;  // the velocity change dv is added in FP32 to the packed offset
     }
 }
 
-constexpr int kPackMaxPer = 4;  // slots per thread in block_pack_kernel (tc <= 4 NT)
-
-// FP64 is scarce on this part (about 1/64 of the FP32 rate), so the tile
-// centre never needs an FP64 reduction.  After a re-sort (FRESH) it is the
-// mean of the FP32-rounded predicted positions (velocities); otherwise the
-// tile holds the same particles as at the previous pack, and the centre is
-// that pack's centre moved by the mean of its FP32 offsets (their mean
-// position then) -- FP32 data only.  Any centre near the tile serves: offsets
-// are FP64 differences from it, rounded once to FP32.  It is stored as a
-// float (lo = 0).  One CTA per tile, so the previous offsets are all read
-// before the CTA overwrites them.
-template <int NT, int PER, bool FRESH>
-__global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q) {
+// Fresh pack: the tile's frame is set at t0 = t_next to the FP32 mean of its
+// particles' predicted positions and velocities (no FP64 reduction: any centre
+// near the tile serves, offsets are FP64 differences rounded once to FP32);
+// the mirror takes each particle's offsets from the frame at its own time.
+template <int NT, int PER>
+__global__ void __launch_bounds__(NT) block_fresh_kernel(const BlockPackParams q) {
     __shared__ float redf[NT / 32][8];
-    __shared__ double cen[6];
-    __shared__ bool last;
-    __shared__ int total;
+    __shared__ float cen[6];
     const int tile = blockIdx.x;
     // this step's time from the previous step's state (every CTA reads it
-    // before the last one, below, stores it)
-    const long long tnq = block_next_time_q(q.sc->t_next_q, q.sc->n_active, q.sc->level, q.dt_max, q.dt_min);
+    // before the last one, in pack_tail, stores it)
+    const long long tnq = next_time_q_warp(q.sc, q.dt_max, q.dt_min);
     const double tn = (double)tnq * q.dt_min;
     const bool live = tn <= q.sc->t_end;
     const ClusterDev cl = q.cl[q.tile_cluster[tile]];
@@ -397,27 +408,19 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
         act[r] = false;
         const int slot = base + threadIdx.x + NT * r;
         if (slot - cl.slot_begin < cl.n) {
-            predict_mixed(q.m, slot, tn, x[r], dvel[r]);
-            if (FRESH) {
+            const int64_t u = q.perm[slot];
+            predict_rows(q, u, tn, x[r], dvel[r]);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    sf[d] += (float)x[r][d];
-                    sf[3 + d] += (float)x[r][3 + d] + dvel[r][d];
-                }
-            } else {
-                sf[0] += q.px[slot];
-                sf[1] += q.py[slot];
-                sf[2] += q.pz[slot];
-                sf[3] += q.pvx[slot];
-                sf[4] += q.pvy[slot];
-                sf[5] += q.pvz[slot];
+            for (int d = 0; d < 3; ++d) {
+                sf[d] += (float)x[r][d];
+                sf[3 + d] += (float)x[r][3 + d] + dvel[r][d];
             }
             sf[6] += 1.0f;
-            act[r] = live && q.m.tq[slot] == tnq;
+            act[r] = live && q.tq[u] == tnq;
             sf[7] += act[r] ? 1.0f : 0.0f;
         }
     }
-    // CTA sum in FP32, fixed order (counts are exact: at most tc)
+    // CTA sums in FP32, fixed order (counts are exact: at most tc)
 #pragma unroll
     for (int k = 0; k < 8; ++k)
 #pragma unroll
@@ -434,71 +437,155 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
             sf[k] = v;
         }
         const float inv = sf[6] > 0.0f ? 1.0f / sf[6] : 0.0f;
-        float h[6];
-        if (!FRESH) {
-            const float4 p0 = q.chl[2 * tile], v0 = q.vchl[2 * tile];
-            const float prev[6] = {p0.x, p0.y, p0.z, v0.x, v0.y, v0.z};
 #pragma unroll
-            for (int d = 0; d < 6; ++d) h[d] = prev[d] + sf[d] * inv;
-        } else {
-#pragma unroll
-            for (int d = 0; d < 6; ++d) h[d] = sf[d] * inv;
-        }
-#pragma unroll
-        for (int d = 0; d < 6; ++d) cen[d] = (double)h[d];
-        q.chl[2 * tile + 0] = make_float4(h[0], h[1], h[2], 0.0f);
-        q.chl[2 * tile + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        q.vchl[2 * tile + 0] = make_float4(h[3], h[4], h[5], 0.0f);
+        for (int d = 0; d < 6; ++d) cen[d] = sf[d] * inv;
+        q.chl[2 * tile + 0] = make_float4(cen[0], cen[1], cen[2], 0.0f);
+        q.chl[2 * tile + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // c(t0) = c0 exactly
+        q.vchl[2 * tile + 0] = make_float4(cen[3], cen[4], cen[5], 0.0f);
         q.vchl[2 * tile + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) q.m.c0[(int64_t)d * q.n_tiles + tile] = (double)cen[d];
         q.tile_cnt[tile] = (int)sf[7];
     }
     __syncthreads();
     double c[6];
 #pragma unroll
-    for (int d = 0; d < 6; ++d) c[d] = cen[d];
+    for (int d = 0; d < 6; ++d) c[d] = (double)cen[d];
+    const double inv_dt_min = recip_pow2(q.dt_min);
+    const int64_t np = q.m.n_pad;
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
         const int slot = base + threadIdx.x + NT * r;
         if (slot - cl.slot_begin < cl.n) {
-            q.px[slot] = (float)(x[r][0] - c[0]);
-            q.py[slot] = (float)(x[r][1] - c[1]);
-            q.pz[slot] = (float)(x[r][2] - c[2]);
-            if (FRESH) q.pm[slot] = (float)q.mass[q.perm[slot]];  // else unchanged
+            const int64_t u = q.perm[slot];
+            {
+                float hi[3], lo[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const double o = x[r][d] - c[d];
+                    hi[d] = (float)o;
+                    lo[d] = (float)(o - (double)hi[d]);
+                }
+                q.px[slot] = hi[0];
+                q.py[slot] = hi[1];
+                q.pz[slot] = hi[2];
+                q.pxl[slot] = lo[0];
+                q.pyl[slot] = lo[1];
+                q.pzl[slot] = lo[2];
+            }
+            q.pm[slot] = (float)q.mass[u];
             // velocity offsets: FP64 difference from the centre, then the FP32
             // change (two roundings, well inside the jerk's tolerance)
             q.pvx[slot] = (float)(x[r][3] - c[3]) + dvel[r][0];
             q.pvy[slot] = (float)(x[r][4] - c[4]) + dvel[r][1];
             q.pvz[slot] = (float)(x[r][5] - c[5]) + dvel[r][2];
             q.flag[slot] = act[r];
+            // the mirror: offsets from the frame at the particle's own time t_i
+            const double ti = q.t[u], back = ti - tn;  // <= 0, exact (multiples of dt_min)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int64_t k = d * q.n + u, ks = d * np + slot;
+                const double xr = q.pos[k] - fma(c[3 + d], back, c[d]);
+                const float hi = (float)xr;
+                q.m.xr[ks] = hi;
+                q.m.xl[ks] = (float)(xr - (double)hi);
+                q.m.vr[ks] = (float)(x[r][3 + d] - c[3 + d]);
+                q.m.af[ks] = (float)q.acc[k];
+                q.m.jf[ks] = (float)q.jerk[k];
+            }
+            q.m.tcq[slot] = (long long)(ti * inv_dt_min);
+            q.m.tq[slot] = q.tq[u];
         } else {
             q.px[slot] = kPadOffset;
             q.py[slot] = kPadOffset;
             q.pz[slot] = kPadOffset;
+            q.pxl[slot] = q.pyl[slot] = q.pzl[slot] = 0.0f;
             q.pm[slot] = 0.0f;
             q.pvx[slot] = q.pvy[slot] = q.pvz[slot] = 0.0f;
             q.flag[slot] = 0;
         }
     }
-    // the last CTA reads only the tile counts (thread 0's writes); the packed
-    // data is for later kernels
+    pack_tail<NT>(q, tnq, true);
+}
+
+// Every other step: FP32 only.  With k = t_next - t_i (units of dt_min, exact
+// h = k dt_min), the offset from the frame at t_next is
+// xr + (xl + h (vr + h (a/2 + h a'/6))), rounded to FP32 once against the
+// pair's high part, and the velocity offset vr + h (a + h a'/2);
+// the tile's centre is the frame at t_next, c0 + cv (t_next - t0), evaluated
+// in FP64 once per tile and stored as a float pair.  Pads keep what the fresh
+// pack wrote.
+template <int NT, int PER>
+__global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q) {
+    __shared__ int wcnt[NT / 32];
+    const int tile = blockIdx.x;
+    const long long tnq = next_time_q_warp(q.sc, q.dt_max, q.dt_min);
+    const bool live = (double)tnq * q.dt_min <= q.sc->t_end;
+    double c0[3] = {0.0, 0.0, 0.0};
+    float4 cv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    long long t0q = 0;
+    if (threadIdx.x == 0) {  // the frame (loads issued early)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) c0[d] = q.m.c0[(int64_t)d * q.n_tiles + tile];
+        cv = q.vchl[2 * tile];
+        t0q = q.sc->frame_t0q;
+    }
+    const ClusterDev cl = q.cl[q.tile_cluster[tile]];
+    const int base = tile * NT * PER;
+    const int64_t np = q.m.n_pad;
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int slot = base + threadIdx.x + NT * r;
+        if (slot - cl.slot_begin < cl.n) {
+            const float hf = (float)((double)(tnq - q.m.tcq[slot]) * q.dt_min);
+            float o[6], ol[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int64_t ks = d * np + slot;
+                const float xr = q.m.xr[ks], xl = q.m.xl[ks], vr = q.m.vr[ks], a = q.m.af[ks], j = q.m.jf[ks];
+                const float t = xl + hf * (vr + hf * (0.5f * a + hf * (j * (1.0f / 6.0f))));
+                // o + ol = xr + t exactly (TwoSum)
+                const float sum = __fadd_rn(xr, t), bb = __fsub_rn(sum, xr);
+                o[d] = sum;
+                ol[d] = __fadd_rn(__fsub_rn(xr, __fsub_rn(sum, bb)), __fsub_rn(t, bb));
+                o[3 + d] = vr + hf * (a + hf * (0.5f * j));
+            }
+            q.px[slot] = o[0];
+            q.py[slot] = o[1];
+            q.pz[slot] = o[2];
+            q.pxl[slot] = ol[0];
+            q.pyl[slot] = ol[1];
+            q.pzl[slot] = ol[2];
+            q.pvx[slot] = o[3];
+            q.pvy[slot] = o[4];
+            q.pvz[slot] = o[5];
+            const bool a = live && q.m.tq[slot] == tnq;
+            q.flag[slot] = a;
+            cnt += a ? 1 : 0;
+        }
+    }
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (threadIdx.x % 32 == 0) wcnt[threadIdx.x / 32] = cnt;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&q.sc->ticket_pack, 1) == (int)gridDim.x - 1;
+        int total = 0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) total += wcnt[w];
+        q.tile_cnt[tile] = total;
+        const double dtf = (double)(tnq - t0q) * q.dt_min;
+        const float cvd[3] = {cv.x, cv.y, cv.z};
+        float hi[3], lo[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double c = fma((double)cvd[d], dtf, c0[d]);
+            hi[d] = (float)c;
+            lo[d] = (float)(c - (double)hi[d]);
+        }
+        q.chl[2 * tile + 0] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+        q.chl[2 * tile + 1] = make_float4(lo[0], lo[1], lo[2], 0.0f);
     }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    block_exclusive_scan<NT>(q.tile_cnt, q.tile_off, q.n_tiles, &total);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        q.sc->t_next_q = tnq;
-        q.sc->t_next = tn;
-        plan_step(q.tile_off, total, q.n_tiles, q.tile_first, q.ncl, q.cl, q.cs, q.workers, q.max_split,
-                  q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max, q.cs_large,
-                  q.workers_large, q.large_min, q.partial_cap);
-        q.sc->ticket_pack = 0;
-    }
+    pack_tail<NT>(q, tnq, false);
 }
 
 // Work item k -> (cluster, i-chunk of the active list, j-range split).
@@ -631,16 +718,6 @@ cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_mirror(const int32_t *perm, const ClusterDev *cl, const int32_t *tile_cluster,
-                                int tc, int64_t n, const double *pos, const double *vel, const double *t,
-                                const long long *tq, const double *acc, const double *jerk,
-                                const SlotMirror &m, cudaStream_t s) {
-    if (n <= 0 || m.n_pad <= 0) return cudaSuccess;
-    block_mirror_kernel<<<grid_of(m.n_pad, 256), 256, 0, s>>>(perm, cl, tile_cluster, tc, n, pos, vel, t, tq,
-                                                              acc, jerk, m);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_block_levels(int64_t n, const double *dt, double dt_max, double dt_min,
                                 const Chunk *chunks, int n_chunks, const long long *tq, double *part,
                                 BlockScalars *sc, cudaStream_t s) {
@@ -666,12 +743,14 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         NB_BL((block_min_kernel<<<b.n_chunks, kMinThreads, 0, s>>>(
             b.tq, b.chunks, reinterpret_cast<long long *>(b.part), b.n_chunks, b.dt_min, b.sc)));
     if (b.px) {
-        if (b.tc <= 0 || b.tc % 128 != 0 || b.tc > kPackMaxPer * (b.tc % 256 == 0 ? 256 : 128))
+        if (b.tc <= 0 || b.tc % 128 != 0 || b.tc > 4 * (b.tc % 256 == 0 ? 256 : 128))  // <= 4 slots a thread
             return cudaErrorInvalidValue;
         BlockPackParams q{};
         q.perm = b.perm; q.cl = b.cl; q.tile_cluster = b.tile_cluster; q.tc = b.tc;
         q.n_tiles = b.n_tiles; q.n = b.n; q.mass = b.mass; q.m = b.mirror;
+        q.t = b.t; q.pos = b.pos; q.vel = b.vel; q.acc = b.acc; q.jerk = b.jerk; q.tq = b.tq;
         q.px = b.px; q.py = b.py; q.pz = b.pz; q.pm = b.pm;
+        q.pxl = b.pxl; q.pyl = b.pyl; q.pzl = b.pzl;
         q.pvx = b.pvx; q.pvy = b.pvy; q.pvz = b.pvz; q.chl = b.chl; q.vchl = b.vchl;
         q.flag = b.flag; q.tile_cnt = b.cnt; q.tile_off = b.chunk_off; q.tile_first = b.tile_first;
         q.ncl = b.ncl; q.cs = b.cs; q.workers = b.workers; q.max_split = b.max_split;
@@ -684,8 +763,8 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         // tc = NT * PER, NT = 256 where tc allows it (checked above: PER <= 4)
 #define NB_PACK(NT_, PER_)                                                                  \
     if (b.tc == (NT_) * (PER_)) {                                                           \
-        if (b.fresh) NB_BL((block_pack_kernel<NT_, PER_, true><<<b.n_tiles, NT_, 0, s>>>(q))); \
-        else NB_BL((block_pack_kernel<NT_, PER_, false><<<b.n_tiles, NT_, 0, s>>>(q)));        \
+        if (b.fresh) NB_BL((block_fresh_kernel<NT_, PER_><<<b.n_tiles, NT_, 0, s>>>(q)));   \
+        else NB_BL((block_pack_kernel<NT_, PER_><<<b.n_tiles, NT_, 0, s>>>(q)));            \
         return cudaSuccess;                                                                 \
     }
         NB_PACK(256, 1) NB_PACK(256, 2) NB_PACK(256, 3) NB_PACK(256, 4)

@@ -27,7 +27,7 @@ struct GraphEntry {
     const void *pos, *vel, *mass, *acc, *pot, *diag, *jerk;
     int kind;  // 0 = KDK leapfrog step, 1 = Hermite step, 2 = block step
     uint64_t dt_bits;
-    int reorder;
+    int reorder;  // variant: re-sort and, for block steps, fresh pack (see step_common)
     int slot;
     cudaGraphExec_t exec;
     int kernels;
@@ -73,6 +73,9 @@ struct BlockState {
     // multiples of dt_max, at the start of the next 16-step batch
     int64_t reorder_epoch = 0;
     bool reorder_pending = false;
+    // F32C: the next step packs from the rows and sets new tile frames (after
+    // a re-sort, and at the start of every advance: the rows are the caller's)
+    bool fresh_pending = false;
     // subset kernel shapes (F32C; split holds the thread-group count): small
     // active sets, and large ones from large_min active particles on
     nbody_tiles sub{0, 0, 0, 0, 0}, sub_large{0, 0, 0, 0, 0};
@@ -82,6 +85,7 @@ struct BlockState {
     double *few_part = nullptr;  // few-particle path: kFewCtas * kFewMax * 7
     long long *tq = nullptr;     // t_i + dt_i in units of dt_min
     SlotMirror m{};  // F32C: the packing predictor's state in j-set slot order
+    float *pxl = nullptr, *pyl = nullptr, *pzl = nullptr;  // F32C: low parts of the packed offsets
     uint8_t *flag = nullptr;
     int *cnt = nullptr, *chunk_off = nullptr, *act_begin = nullptr, *act_n = nullptr;
     int *ich_off = nullptr, *item_off = nullptr;
@@ -784,13 +788,11 @@ void free_block(nbody_ctx *ctx) {
     BlockState &b = ctx->bs;
     for (double **q : {&b.t, &b.dt, &b.part, &b.partial, &b.p1, &b.few_part}) dev_free(q);
     dev_free(&b.tq);
-    dev_free(&b.m.pos);
-    dev_free(&b.m.vel);
-    dev_free(&b.m.t);
+    for (float **q : {&b.m.xr, &b.m.xl, &b.m.vr, &b.m.af, &b.m.jf, &b.pxl, &b.pyl, &b.pzl}) dev_free(q);
+    dev_free(&b.m.tcq);
     dev_free(&b.m.tq);
-    dev_free(&b.m.af);
-    dev_free(&b.m.jf);
-    b.m.n_pad = 0;
+    dev_free(&b.m.c0);
+    b.m = SlotMirror{};
     dev_free(&b.flag);
     for (int **q : {&b.cnt, &b.chunk_off, &b.act_begin, &b.act_n, &b.ich_off, &b.item_off}) dev_free(q);
     dev_free(&b.act);
@@ -859,12 +861,16 @@ int alloc_block(nbody_ctx *ctx) {
     if ((rc = dev_alloc(ctx, &b.tq, n))) return rc;
     if (f32c) {
         const size_t np = (size_t)ctx->jp.n_pad;
+        for (float **q : {&b.m.xr, &b.m.xl, &b.m.vr, &b.m.af, &b.m.jf})
+            if ((rc = dev_alloc(ctx, q, 3 * np))) return rc;
+        for (float **q : {&b.pxl, &b.pyl, &b.pzl})
+            if ((rc = dev_alloc(ctx, q, np))) return rc;
+        if ((rc = dev_alloc(ctx, &b.m.tcq, np)) || (rc = dev_alloc(ctx, &b.m.tq, np))) return rc;
+        if ((rc = dev_alloc(ctx, &b.m.c0, 3 * (size_t)std::max(ctx->jp.n_tiles, 1)))) return rc;
+        b.m.vchl = ctx->jp.vchl;
+        b.m.tc = ctx->jp.tc;
+        b.m.n_tiles = ctx->jp.n_tiles;
         b.m.n_pad = (int64_t)np;
-        for (double **q : {&b.m.pos, &b.m.vel})
-            if ((rc = dev_alloc(ctx, q, 3 * np))) return rc;
-        if ((rc = dev_alloc(ctx, &b.m.t, np)) || (rc = dev_alloc(ctx, &b.m.tq, np))) return rc;
-        for (float **q : {&b.m.af, &b.m.jf})
-            if ((rc = dev_alloc(ctx, q, 3 * np))) return rc;
     }
     if ((rc = dev_alloc(ctx, &b.part, nc))) return rc;
     if ((rc = dev_alloc(ctx, &b.flag, nflag))) return rc;
@@ -926,6 +932,7 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
         b.tc = j.tc;
         b.n_tiles = j.n_tiles;
         b.px = j.px; b.py = j.py; b.pz = j.pz; b.pm = j.pm;
+        b.pxl = bs.pxl; b.pyl = bs.pyl; b.pzl = bs.pzl;
         b.pvx = j.pvx; b.pvy = j.pvy; b.pvz = j.pvz;
         b.chl = j.chl; b.vchl = j.vchl;
         b.queue_head = j.counters;
@@ -938,31 +945,20 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
     return b;
 }
 
-cudaError_t launch_mirror(nbody_ctx *ctx, const double *pos, const double *vel, const double *acc,
-                          const double *jerk, cudaStream_t s) {
-    const JerkPath &j = ctx->jp;
-    const BlockState &bs = ctx->bs;
-    return launch_block_mirror(j.perm, j.dcl, j.tile_cluster, j.tc, ctx->n, pos, vel, bs.t, bs.tq, acc, jerk,
-                               bs.m, s);
-}
-
 // One block step (see block_sched.cu, block_force.cu): schedule, predict, pack the predicted j-set,
 // forces + jerks of the active subset, correct and re-step the active ones.
-int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, bool capturing,
+int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, bool fresh, int slot, bool capturing,
                        cudaStream_t s, int *kernels) {
     if (ctx->n == 0) return NBODY_OK;
     BlockState &bs = ctx->bs;
     JerkPath &j = ctx->jp;
     BlockLaunch b = block_launch(ctx, a);
-    b.fresh = reorder;
+    b.fresh = fresh || reorder;
     int rc;
-    if (ctx->mode == NBODY_F32C && reorder) {
+    if (ctx->mode == NBODY_F32C && reorder)
         NB_CUDA(launch_reorder(a.pos, ctx->n, ctx->chunks, ctx->n_chunks, ctx->chunk_first, ctx->ncl, j.dcl,
                                ctx->bpart, ctx->bbox, ctx->keys, ctx->vals, ctx->sort_n, ctx->max_cluster,
                                j.perm, s, kernels));
-        NB_CUDA(launch_mirror(ctx, a.pos, a.vel, a.acc, a.jerk, s));
-        ++*kernels;
-    }
     NB_CUDA(launch_block_prepare(b, s, kernels));
     NB_CUDA(launch_block_queue(b, s, kernels));
     BlockCorrect corr{};
@@ -992,6 +988,9 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, int slot, 
         q.n_items = &bs.sc->n_items;
         q.partial = bs.partial;
         q.tcj = j.tc;
+        q.pxl = bs.pxl;
+        q.pyl = bs.pyl;
+        q.pzl = bs.pzl;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
         q.n_items = &bs.sc->n_items_small;
         NB_CUDA(launch_subset_f32c(bs.sub.block, bs.sub.p, bs.sub.tj, bs.sub.split,
@@ -1418,18 +1417,21 @@ int step_common(nbody_ctx *ctx, double *pos, double *vel, const double *mass, do
     uint64_t dt_bits;
     memcpy(&dt_bits, &dt, sizeof dt);
     for (int32_t step = 0; step < nsteps; ++step) {
-        bool reorder = want_reorder(ctx);
+        bool reorder = want_reorder(ctx), fresh = false;
         if (kind == 2) {
             reorder = ctx->bs.reorder_pending;
-            ctx->bs.reorder_pending = false;
+            fresh = reorder || ctx->bs.fresh_pending;
+            ctx->bs.reorder_pending = ctx->bs.fresh_pending = false;
         }
+        // graph variants: 0 plain, 1 re-sort; block steps: 1 fresh pack, 2 re-sort + fresh pack
+        const int variant = kind == 2 ? (reorder ? 2 : fresh ? 1 : 0) : (reorder ? 1 : 0);
         const int slot = next_slot(ctx);
         if (slot < -1) return ctx->sticky;
         const int multi =
-            kind == 2 && use_graph && slot == -1 && !reorder && nsteps - step >= kMultiSteps ? kMultiSteps : 1;
+            kind == 2 && use_graph && slot == -1 && !fresh && nsteps - step >= kMultiSteps ? kMultiSteps : 1;
         if (!use_graph) {
             int k = 0;
-            rc = kind == 2   ? enqueue_block_step(ctx, a, reorder, slot, false, s, &k)
+            rc = kind == 2   ? enqueue_block_step(ctx, a, reorder, fresh, slot, false, s, &k)
                  : kind == 1 ? enqueue_hermite_step(ctx, a, dt, reorder, slot, false, s, &k)
                              : enqueue_step(ctx, a, dt, reorder, slot, false, s, &k);
             ctx->launches += k;
@@ -1439,17 +1441,17 @@ int step_common(nbody_ctx *ctx, double *pos, double *vel, const double *mass, do
             for (auto &e : ctx->graphs)
                 if (e.pos == a.pos && e.vel == a.vel && e.mass == a.mass && e.acc == a.acc &&
                     e.pot == a.pot && e.diag == a.diag && e.jerk == a.jerk && e.kind == kind &&
-                    e.dt_bits == dt_bits && e.reorder == (int)reorder && e.slot == slot &&
+                    e.dt_bits == dt_bits && e.reorder == variant && e.slot == slot &&
                     e.steps == multi)
                     g = &e;
             if (!g) {
                 if (ctx->graphs.size() >= 16) drop_graphs(ctx);
                 GraphEntry ge{a.pos, a.vel, a.mass, a.acc, a.pot, a.diag, a.jerk, kind, dt_bits,
-                              (int)reorder, slot, nullptr, 0, multi};
+                              variant, slot, nullptr, 0, multi};
                 NB_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
                 int k = 0;
                 for (int m = 0; m < multi && rc == NBODY_OK; ++m)
-                    rc = kind == 2   ? enqueue_block_step(ctx, a, reorder, slot, true, ctx->cap_stream, &k)
+                    rc = kind == 2   ? enqueue_block_step(ctx, a, reorder, fresh, slot, true, ctx->cap_stream, &k)
                          : kind == 1 ? enqueue_hermite_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k)
                                      : enqueue_step(ctx, a, dt, reorder, slot, true, ctx->cap_stream, &k);
                 cudaGraph_t graph = nullptr;
@@ -1566,10 +1568,6 @@ int nbody_block_start(nbody_ctx *ctx, const double *pos, const double *vel, cons
     b.eta = eta;
     NB_CUDA(launch_block_init(ctx->n, acc, jerk, dt_max, dt_min, eta_s, b.t, b.dt, b.tq, s));
     NB_CUDA(cudaMemsetAsync(b.sc, 0, sizeof(BlockScalars), s));
-    if (b.m.pos) {
-        NB_CUDA(launch_mirror(ctx, pos, vel, acc, jerk, s));
-        ctx->launches += 1;
-    }
     // level counts and the first t_next (later steps set the next one themselves)
     NB_CUDA(launch_block_levels(ctx->n, b.dt, dt_max, dt_min, ctx->chunks, ctx->n_chunks, b.tq, b.part,
                                 b.sc, s));
@@ -1577,6 +1575,7 @@ int nbody_block_start(nbody_ctx *ctx, const double *pos, const double *vel, cons
     NB_CUDA(cudaStreamSynchronize(s));
     b.reorder_epoch = 0;
     b.reorder_pending = false;
+    b.fresh_pending = true;
     b.started = true;
     return NBODY_OK;
 }
@@ -1598,10 +1597,7 @@ int nbody_block_advance(nbody_ctx *ctx, double *pos, double *vel, const double *
         if (!q || !is_device_ptr(q)) return fail(ctx, NBODY_EINVAL, "block steps need device arrays");
     if (pot && !is_device_ptr(pot)) return fail(ctx, NBODY_EINVAL, "block steps need device arrays");
     cudaStream_t s = (cudaStream_t)stream;
-    if (b.m.pos) {  // the rows are the caller's: take them as they are now
-        NB_CUDA(launch_mirror(ctx, pos, vel, acc, jerk, s));
-        ctx->launches += 1;
-    }
+    b.fresh_pending = true;  // the rows are the caller's: take them as they are now
     NB_CUDA(cudaMemcpyAsync(&b.sc->t_end, &t_end, sizeof(double), cudaMemcpyHostToDevice, s));
     BlockScalars h{};
     NB_CUDA(cudaMemcpyAsync(&h, b.sc, sizeof h, cudaMemcpyDeviceToHost, s));

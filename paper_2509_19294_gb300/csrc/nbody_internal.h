@@ -152,28 +152,40 @@ struct BlockScalars {
     // i-chunk size of this step and the queue size seen by each subset kernel
     // (the one not chosen reads 0 and returns at once)
     int cs, n_items_small, n_items_large;
+    // F32C: time of the tile frames' origins (units of dt_min), set by the
+    // fresh pack
+    long long frame_t0q;
 };
 
 // Subset acceleration + jerk kernel: base carries the j-set (the jerk path's
 // packed predicted particles), perm (slot -> row) and the outputs (rows).
 // Hermite corrector + next-step choice of the block scheme, applied where an
 // active particle's acceleration and jerk become final (block_common.cuh).
-// F32C block steps: the state the packing predictor reads, kept in j-set slot
-// order so that its loads are contiguous (the caller's arrays stay in row
-// order).  Rebuilt from the rows after every re-sort; the corrector updates
-// both.  a and a' are kept as FP32 copies (the predictor's higher-order terms).
+// F32C block steps: the state the packing predictor reads, in j-set slot
+// order and in FP32, relative to a frame per centre tile that moves at a
+// constant velocity: its position at time t is c(t) = c0 + cv (t - t0), c0 in
+// FP64, cv the tile's FP32 velocity centre (vchl), t0 the time of the last
+// fresh pack (BlockScalars::frame_t0q), which sets c0 and cv from the rows
+// (after a re-sort, at the start of each advance).  Each slot holds its
+// particle's x_i - c(t_i) (a float pair, so that the predicted offset is
+// rounded to FP32 once) and v_i - cv at the particle's own time t_i, and FP32
+// copies of a_i and a'_i; the corrector rewrites them.  The predicted offset
+// from the frame at t is then a short FP32 polynomial in t - t_i, and the tile
+// centre the force kernels see, c(t), is a float pair (hi + lo) from FP64.
 struct SlotMirror {
-    double *pos, *vel;  // [3][n_pad]
-    double *t;          // [n_pad]
-    long long *tq;      // [n_pad]
-    float *af, *jf;     // [3][n_pad]
+    float *xr, *xl, *vr;   // [3][n_pad] x_i - c(t_i) as a float pair (xr + xl), v_i - cv
+    float *af, *jf;        // [3][n_pad]
+    long long *tcq, *tq;   // [n_pad] t_i and t_i + dt_i in units of dt_min
+    double *c0;            // [3][n_tiles] frame origins at t0
+    const float4 *vchl;    // frame velocities: vchl[2 tile].xyz
+    int tc, n_tiles;       // slots per tile, tiles
     int64_t n_pad;
 };
 
 struct BlockCorrect {
     const BlockScalars *sc;
     int *level;  // BlockScalars::level (the corrector moves particles between levels)
-    SlotMirror m;  // m.pos == null: no mirror (FP64 path)
+    SlotMirror m;  // m.xr == null: no mirror (FP64 path)
     double *t, *dt, *pos, *vel, *acc, *jerk, *pot;  // rows; acc, jerk: the particle's a0, j0
     long long *tq;
     int64_t n;
@@ -213,6 +225,9 @@ struct F32CSubsetParams {
     const int *n_items;       // device count
     double *partial;          // [slots][7][block * p]
     int tcj;                  // j-set centre-tile size
+    // low parts of the packed position offsets (px + pxl, ...), or null: the
+    // few-particle pass then differences close pairs exactly
+    const float *pxl, *pyl, *pzl;
 };
 
 struct BlockLaunch {
@@ -226,7 +241,7 @@ struct BlockLaunch {
     double dt_min, dt_max;
     double *pos, *vel, *acc, *jerk, *xp, *vp;
     SlotMirror mirror;  // F32C: the packing predictor's slot-ordered state
-    bool fresh;         // the j-set was just re-sorted (tile centres from scratch)
+    bool fresh;         // F32C: new tile frames and mirror from the rows (after a re-sort, ...)
     const double *mass;
     uint8_t *flag;  // per row (FP64) or per j-set slot (F32C)
     // per row chunk (FP64) or per centre tile (F32C): active counts, offsets
@@ -239,6 +254,7 @@ struct BlockLaunch {
     const int32_t *perm, *tile_cluster, *tile_first;
     int tc, n_tiles;
     float *px, *py, *pz, *pm, *pvx, *pvy, *pvz;
+    float *pxl, *pyl, *pzl;  // low parts of the position offsets (block steps)
     float4 *chl, *vchl;
     int *queue_head;  // [2]: the small- and large-set subset kernels' queue heads
     int few_max;  // 0 disables the few-particle path
@@ -267,12 +283,6 @@ int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap);
 cudaError_t launch_subset_tail(int max_chunks, int max_cs, int max_ctas, const F32CSubsetParams &prm,
                                const int32_t *act, BlockScalars *sc, double *few_part, const SubItem *info,
                                cudaStream_t s);
-// (Re)build the slot-ordered mirror from the rows through perm (F32C: start of
-// block stepping, every re-sort, every advance call).
-cudaError_t launch_block_mirror(const int32_t *perm, const ClusterDev *cl, const int32_t *tile_cluster,
-                                int tc, int64_t n, const double *pos, const double *vel, const double *t,
-                                const long long *tq, const double *acc, const double *jerk,
-                                const SlotMirror &m, cudaStream_t s);
 // Level counts of all particles and the first t_next (start of block stepping).
 cudaError_t launch_block_levels(int64_t n, const double *dt, double dt_max, double dt_min,
                                 const Chunk *chunks, int n_chunks, const long long *tq, double *part,
