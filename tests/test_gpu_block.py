@@ -182,6 +182,44 @@ def test_block_steps_without_softening(oracle, mode):
         assert metrics.summary(ga, ra)["median"] <= 1e-6
 
 
+def wide_tile_binary(n_field=30, seed=61, sep=1e-3, where=8.0):
+    """A loose field of n_field stars (one centre tile of extent ~10) and a
+    circular binary of separation sep placed `where` from the centre: its
+    members' FP32 offsets from the tile centre are ~where, so rounding them
+    once (u * where ~ 5e-7) would be a relative error ~5e-4 of their
+    separation."""
+    pos, vel, _ = ic.plummer(n_field, seed=seed)
+    pos, vel = pos * 5.0, vel / np.sqrt(5.0)
+    n = n_field + 2
+    mass = np.full(n, 1.0 / n)
+    v = np.sqrt(2.0 * mass[0] / sep) / 2.0  # each member's speed on the circular orbit
+    bp = np.array([[where - sep / 2, where + sep / 2], [0.0, 0.0], [0.0, 0.0]])
+    bv = np.array([[0.0, 0.0], [-v, v], [0.0, 0.0]])
+    return np.hstack([pos, bp]), np.hstack([vel, bv]), mass
+
+
+def test_f32c_few_particle_pass_differences_close_pairs_exactly(oracle):
+    # <= 32 particles: every block step runs the few-particle pass.  The
+    # binary takes the smallest steps; its orbit (~20 periods) and its members'
+    # accelerations follow the oracle to the FP32 accuracy of the pair terms,
+    # not to that of the offsets' magnitude.
+    pos, vel, mass = wide_tile_binary()
+    t_end = DT_MAX
+    gp, gv, ga, gj, gdt, gt, gb, ge = block_run(pos, vel, mass, 1e-4, nb.NBODY_F32C, t_end=t_end)
+    rp, rv, ra, rj, _, rdt, rb, re = oracle.block_hermite(pos, vel, mass, 1e-4, t_end, DT_MAX, DT_MIN,
+                                                         0.02, 0.01)
+    assert rdt[-1] <= 2.0 ** -14 and rdt[-1] < rdt[:-2].min()  # the binary takes the smallest steps
+    # offsets rounded to FP32 once (error ~5e-4 of the separation) make the
+    # binary's forces noisy enough for the step criterion (its third
+    # derivative estimate scales as da / h^3) to shrink the step towards
+    # dt_min, multiplying the block steps; differenced exactly, the binary
+    # keeps the oracle's step and the run its schedule
+    assert np.array_equal(gdt[-2:], rdt[-2:]) and abs(gb - rb) <= 0.05 * rb, (gb, rb)
+    assert np.abs(gp[:, :-2] - rp[:, :-2]).max() <= 1e-10
+    assert np.abs(gp[:, -2:] - rp[:, -2:]).max() <= 5e-7  # ~20 orbits of FP32 pair arithmetic
+    assert metrics.rel_acc_errors(ga[:, -2:], ra[:, -2:]).max() <= 2e-4
+
+
 def test_block_steps_save_evaluations():
     pos, vel, mass = cluster_system(3000, 56)
     *_, gb, ge = block_run(pos, vel, mass, 0.002, nb.NBODY_F32C)
