@@ -196,15 +196,24 @@ int nbody_step_hermite(nbody_ctx *ctx, double *pos, double *vel, const double *m
  * compaction of the active set, work queue) runs on the device, so block steps
  * are replayed CUDA graphs (eight steps to a graph unless NBODY_FLAG_PROFILE
  * records per-step events); the host checks progress every 16-256 steps.
- * With NBODY_F32C the predicted j-set is packed as FP32 offsets (position and
- * velocity corrections over the prediction interval in FP32); with NBODY_F64
- * every pair is FP64 and the step decisions equal the FP64 oracle's.
+ * With NBODY_F32C the predicted j-set is packed as FP32 offsets from a frame
+ * per centre tile that moves at the tile's mean velocity: each particle's
+ * offset from its frame is kept between steps as a float pair and predicted
+ * by a short FP32 polynomial; the frames are set again from the FP64 state
+ * after every re-sort and at the start of every nbody_block_advance call (the
+ * arrays are the caller's and may have changed).  Steps with at most 32 active
+ * particles difference close pairs exactly (position offsets as float pairs):
+ * FP32-rounded offsets would make a close pair's forces noisy enough for the
+ * criterion (its third-derivative term scales as 1/h^3) to shrink its step
+ * towards dt_min.  With NBODY_F64 every pair is FP64 and the step decisions
+ * equal the FP64 oracle's.
  *
  * nbody_block_start: computes a, jerk, pot at the current state (t = 0) and the
  *   initial steps, the largest power of two <= min(dt_max, eta_s |a|/|a'|),
  *   not below dt_min.  dt_max and dt_min are powers of two with
  *   dt_max / dt_min <= 2^40, and t_end / dt_min <= 2^60 (times are counted in
- *   units of dt_min; NBODY_EINVAL otherwise).  Unless jerk tiles
+ *   units of dt_min), and with NBODY_F32C dt_min >= 2^-126 (NBODY_EINVAL
+ *   otherwise).  Unless jerk tiles
  *   were set (nbody_set_jerk_tiles) or built by an earlier jerk call, it picks
  *   a tile shape suited to block steps (narrower j-tiles for large N).
  * nbody_block_advance: block steps until every particle reaches t_end (a

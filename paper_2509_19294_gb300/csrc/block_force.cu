@@ -540,7 +540,29 @@ __device__ void reduce_pass(const F32CSubsetParams &q, const SubItem *__restrict
 #pragma unroll
         for (int c = 0; c < 7; ++c) part[g][c][lane] = tot[c];
         __syncthreads();
-        if (g == 0 && l < it.na) {
+        if (q.corr.sc) {
+            // the unit's 32 particles corrected four lanes each (one per
+            // component): the FP64 chain of one particle is what a step of a
+            // few chunks waits for
+            if (threadIdx.x < 4 * 32) {
+                const int a = threadIdx.x / 4, sub = threadIdx.x % 4, cp = sub < 3 ? sub : 0;
+                const int la = (u % subs) * 32 + a;
+                const bool valid = la < it.na;
+                double ra = part[0][cp][a], rj = part[0][3 + cp][a], rp = part[0][6][a];
+#pragma unroll
+                for (int h = 1; h < kReduceWarps; ++h) {
+                    ra += part[h][cp][a];
+                    rj += part[h][3 + cp][a];
+                    rp += part[h][6][a];
+                }
+                const int slot = q.act_slot[it.a0 + (valid ? la : (u % subs) * 32)];
+                const float e2 = q.base.cl[it.cluster].eps2f;
+                if (e2 > 0.0f) rp -= (double)__fmul_rn(q.base.pm[slot], rsqrt_mufu(e2));
+                const double G = q.base.G;
+                correct_particle_x4(q.corr, q.base.perm[slot], slot, valid, sub, G * ra, G * rj, -G * rp,
+                                    sc->t_next, sc->t_next_q);
+            }
+        } else if (g == 0 && l < it.na) {
             double r[7];
 #pragma unroll
             for (int c = 0; c < 7; ++c) {

@@ -316,6 +316,7 @@ struct BlockPackParams {
     int cs_large, workers_large, large_min;
     long long partial_cap;  // doubles in the split-partial buffer
     double dt_max, dt_min;
+    float dt_min_f;  // dt_min as a float (exact: a power of two >= 2^-126)
 };
 
 // The step's time in units of dt_min (block_next_time_q with the level scan
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
     __shared__ int wcnt[NT / 32];
     const int tile = blockIdx.x;
     const long long tnq = next_time_q_warp(q.sc, q.dt_max, q.dt_min);
-    const bool live = (double)tnq * q.dt_min <= q.sc->t_end;
+    const bool live = tnq <= q.sc->t_end_q;
     double c0[3] = {0.0, 0.0, 0.0};
     float4 cv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     long long t0q = 0;
@@ -538,7 +539,9 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
     for (int r = 0; r < PER; ++r) {
         const int slot = base + threadIdx.x + NT * r;
         if (slot - cl.slot_begin < cl.n) {
-            const float hf = (float)((double)(tnq - q.m.tcq[slot]) * q.dt_min);
+            // h = k dt_min, k < 2^31 in practice (a conversion off the FP64 pipe)
+            const long long k = tnq - q.m.tcq[slot];
+            const float hf = (k < (1LL << 31) ? (float)(int)k : (float)k) * q.dt_min_f;
             float o[6], ol[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -760,6 +763,7 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         q.partial_cap = b.partial_cap;
         q.dt_max = b.dt_max;
         q.dt_min = b.dt_min;
+        q.dt_min_f = (float)b.dt_min;
         // tc = NT * PER, NT = 256 where tc allows it (checked above: PER <= 4)
 #define NB_PACK(NT_, PER_)                                                                  \
     if (b.tc == (NT_) * (PER_)) {                                                           \

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -1553,6 +1554,8 @@ int nbody_block_start(nbody_ctx *ctx, const double *pos, const double *vel, cons
         return fail(ctx, NBODY_EINVAL, "block steps: dt_max, dt_min must be powers of two, eta > 0");
     if (dt_max / dt_min > 0x1p40)
         return fail(ctx, NBODY_EINVAL, "block steps: dt_max / dt_min must be at most 2^40");
+    if (ctx->mode == NBODY_F32C && dt_min < 0x1p-126)
+        return fail(ctx, NBODY_EINVAL, "F32C block steps: dt_min must be at least 2^-126 (a normal float)");
     if (ctx->n == 0) return NBODY_OK;
     for (const void *q : {(const void *)pos, (const void *)vel, (const void *)mass, (const void *)acc,
                           (const void *)jerk})
@@ -1598,7 +1601,13 @@ int nbody_block_advance(nbody_ctx *ctx, double *pos, double *vel, const double *
     if (pot && !is_device_ptr(pot)) return fail(ctx, NBODY_EINVAL, "block steps need device arrays");
     cudaStream_t s = (cudaStream_t)stream;
     b.fresh_pending = true;  // the rows are the caller's: take them as they are now
-    NB_CUDA(cudaMemcpyAsync(&b.sc->t_end, &t_end, sizeof(double), cudaMemcpyHostToDevice, s));
+    struct {
+        double t;
+        long long q;
+    } end{t_end, (long long)(t_end / b.dt_min)};  // exact: t_end a multiple of dt_max
+    static_assert(offsetof(BlockScalars, t_end_q) == offsetof(BlockScalars, t_end) + sizeof(double),
+                  "t_end, t_end_q adjacent");
+    NB_CUDA(cudaMemcpyAsync(&b.sc->t_end, &end, sizeof end, cudaMemcpyHostToDevice, s));
     BlockScalars h{};
     NB_CUDA(cudaMemcpyAsync(&h, b.sc, sizeof h, cudaMemcpyDeviceToHost, s));
     NB_CUDA(cudaStreamSynchronize(s));

@@ -139,6 +139,7 @@ struct BlockScalars {
     double t_next;   // time of the current block step
     long long t_next_q;  // the same in units of dt_min
     double t_end;    // stop time (set by the host before each batch)
+    long long t_end_q;  // the same in units of dt_min (follows t_end in memory: set together)
     int n_active, n_chunks, split, n_items;
     long long blocks, evals;  // block steps taken, single-particle evaluations
     int ticket_min, ticket_pack, ticket_few;  // last-CTA tickets (each reset by its last CTA)
