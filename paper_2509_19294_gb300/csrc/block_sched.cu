@@ -11,9 +11,14 @@
 //      smallest occupied step (per-level counts kept by the corrector), taken
 //      by every CTA of block_pack_kernel (block_min_kernel, an integer min in
 //      units of dt_min, runs at the start and on the FP64 path)
-//   2. block_pack_kernel: predict every particle to t_next, pack it as the
-//      j-set (the jerk path's geometry), flag and count the active slots per
-//      tile; the last CTA plans the step (offsets, regime, split, queue size)
+//   2. block_pack_kernel: predict every particle to t_next in FP32 from the
+//      slot-ordered mirror (offsets from per-tile frames moving at constant
+//      velocity), pack it as the j-set (the jerk path's geometry) with the
+//      low parts of the position offsets, flag and count the active slots per
+//      tile; the last CTA plans the step (offsets, regime, split, queue
+//      size).  block_fresh_kernel replaces it after a re-sort and at the start
+//      of an advance: it predicts from the FP64 rows, sets the frames and
+//      writes the mirror.
 //   3. block_queue_kernel: ordered compaction of the active slots, work items
 //   4. the force pass (block_force.cu): the small-set and the large-set subset
 //      kernels, then subset_tail_kernel, which either runs the few-particle
