@@ -40,12 +40,24 @@ __device__ __forceinline__ void choose_step(const BlockCorrect &c, int64_t i, in
                                             double na, double nj, double n2, double n3, double tn,
                                             long long tnq) {
     const double den = nj * n3 + n2 * n2;
-    const double da = den > 0.0 ? sqrt(c.eta * (na * n2 + nj * nj) / den) : c.dt_max;
     const double inv_dt_min = recip_pow2(c.dt_min);
     double nd = h;
-    while (nd > da && nd > c.dt_min) nd *= 0.5;
+    bool grow;
+    if (den > 0.0 && c.dt_min >= 0x1p-500 && c.dt_max <= 0x1p500) {  // every p^2 below is exact
+        // y = da^2 before its square root.  The criterion is only compared
+        // with powers of two p, and for those p > sqrt_rn(y) <=> y < p^2
+        // exactly (p^2 is exact, and no double lies within the half ulp below
+        // p^2 that rounds up to p), so the square root is never taken
+        const double y = c.eta * (na * n2 + nj * nj) / den;
+        while (y < nd * nd && nd > c.dt_min) nd *= 0.5;
+        grow = y >= 4.0 * h * h;
+    } else {
+        const double da = den > 0.0 ? sqrt(c.eta * (na * n2 + nj * nj) / den) : c.dt_max;
+        while (nd > da && nd > c.dt_min) nd *= 0.5;
+        grow = da >= 2.0 * h;
+    }
     const long long q2 = (long long)(2.0 * h * inv_dt_min);  // 2h in units of dt_min: a power of two
-    if (nd == h && da >= 2.0 * h && 2.0 * h <= c.dt_max && (tnq & (q2 - 1)) == 0) nd = 2.0 * h;
+    if (nd == h && grow && 2.0 * h <= c.dt_max && (tnq & (q2 - 1)) == 0) nd = 2.0 * h;
     if (c.level && nd != h) {
         atomicSub(&c.level[block_level(h, c.dt_max)], 1);
         atomicAdd(&c.level[block_level(nd, c.dt_max)], 1);
