@@ -220,6 +220,62 @@ def test_f32c_few_particle_pass_differences_close_pairs_exactly(oracle):
     assert metrics.rel_acc_errors(ga[:, -2:], ra[:, -2:]).max() <= 2e-4
 
 
+def block_run_chunked(pos, vel, mass, eps, mode, t_ends, shift=None, **kw):
+    """block_run advancing through t_ends in turn; shift (a 3-vector) is added
+    to every position on the device after the first advance call."""
+    n = mass.shape[0]
+    with nb.nbody_init(n, eps, mode=mode, **kw) as ctx:
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        a = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        j = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        ph = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_block_start(ctx, p, v, m, a, j, ph, DT_MAX, DT_MIN, 0.02, 0.01)
+        for k, te in enumerate(t_ends):
+            blocks, evals = nb.nbody_block_advance(ctx, p, v, m, a, j, ph, te)
+            if k == 0 and shift is not None:
+                p += torch.tensor(shift, dtype=torch.float64, device="cuda").reshape(3, 1)
+        t, dt = nb.nbody_block_state(ctx)
+        return host(p), host(v), host(a), host(j), dt, t, blocks, evals
+
+
+@pytest.mark.parametrize("mode", [nb.NBODY_F64, nb.NBODY_F32C])
+def test_block_steps_in_chunks_with_resorts_track_oracle(oracle, mode):
+    # four advance calls (each F32C one starts from the rows again) and a
+    # Morton re-sort at every dt_max (a fresh F32C pack of new tile frames)
+    pos, vel, mass = cluster_system(1500, 62)
+    t_ends = [DT_MAX * k for k in (1, 2, 3, 4)]
+    gp, gv, ga, gj, gdt, gt, gb, ge = block_run_chunked(pos, vel, mass, 0.005, mode, t_ends,
+                                                        reorder_every=1)
+    rp, rv, ra, rj, _, rdt, rb, re = oracle.block_hermite(pos, vel, mass, 0.005, T_END, DT_MAX, DT_MIN,
+                                                         0.02, 0.01)
+    assert np.all(gt == T_END)
+    if mode == nb.NBODY_F64:
+        assert np.array_equal(gdt, rdt) and gb == rb and ge == re
+        np.testing.assert_allclose(gp, rp, rtol=0, atol=1e-12)
+    else:
+        assert np.mean(gdt == rdt) >= 0.99 and abs(ge - re) <= 0.01 * re
+        dx = np.abs(gp - rp).max(axis=0)
+        assert np.median(dx) <= 1e-10 and dx.max() <= 1e-7, (np.median(dx), dx.max())
+
+
+@pytest.mark.parametrize("mode", [nb.NBODY_F64, nb.NBODY_F32C])
+def test_block_advance_reads_the_callers_arrays_again(mode):
+    # the caller translates every particle between two advance calls; forces
+    # are translation invariant, so the run is the untranslated one moved by
+    # the same vector (state kept from the previous call would ignore it)
+    pos, vel, mass = cluster_system(800, 63)
+    d = np.array([0.25, -0.5, 0.125])
+    t_ends = [DT_MAX * 2, T_END]
+    gp0, *_, gb0, ge0 = block_run_chunked(pos, vel, mass, 0.01, mode, t_ends)
+    gp1, *_, gb1, ge1 = block_run_chunked(pos, vel, mass, 0.01, mode, t_ends, shift=d)
+    dx = np.abs(gp1 - d[:, None] - gp0).max(axis=0)
+    if mode == nb.NBODY_F64:
+        assert dx.max() <= 1e-10, dx.max()
+    else:  # different tile centres round the offsets differently
+        assert np.median(dx) <= 1e-9 and dx.max() <= 1e-6, (np.median(dx), dx.max())
+    assert abs(gb1 - gb0) <= 0.01 * gb0 and abs(ge1 - ge0) <= 0.01 * ge0
+
+
 def test_block_steps_save_evaluations():
     pos, vel, mass = cluster_system(3000, 56)
     *_, gb, ge = block_run(pos, vel, mass, 0.002, nb.NBODY_F32C)
