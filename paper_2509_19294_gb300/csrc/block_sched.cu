@@ -242,15 +242,19 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
     // split counts that fit the partial buffer, take the one whose last round
     // is fullest (the smaller on ties)
     if (chunks > 0) {
+        // fullness of the last round, items / (workers * rounds), compared
+        // exactly as fractions in integers (no FP64 division on this thread,
+        // which every step waits for)
         const long long max_slots = partial_cap / (7LL * cs);
-        double best = -1.0;
+        long long best_items = 0, best_rounds = 1;
         int pick = split;
         for (int sp = split; sp <= split + 3 && sp <= max_split; ++sp) {
-            if (sp > 1 && (long long)chunks * sp > max_slots) break;
-            const double r = (double)chunks * sp / workers;
-            const double eff = r / ceil(r);
-            if (eff > best + 1e-9) {
-                best = eff;
+            const long long items = (long long)chunks * sp;
+            if (sp > 1 && items > max_slots) break;
+            const long long rounds = (items + workers - 1) / workers;
+            if (items * best_rounds > best_items * rounds) {
+                best_items = items;
+                best_rounds = rounds;
                 pick = sp;
             }
         }
@@ -544,9 +548,12 @@ __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q)
     for (int r = 0; r < PER; ++r) {
         const int slot = base + threadIdx.x + NT * r;
         if (slot - cl.slot_begin < cl.n) {
-            // h = k dt_min, k < 2^31 in practice (a conversion off the FP64 pipe)
+            // h = k dt_min, 0 <= k <= dt_max / dt_min <= 2^40: two exact 32-bit
+            // conversions and one rounding (no 64-bit conversion, which runs
+            // on the FP64 pipe)
             const long long k = tnq - q.m.tcq[slot];
-            const float hf = (k < (1LL << 31) ? (float)(int)k : (float)k) * q.dt_min_f;
+            const float kf = fmaf((float)(int)(k >> 24), 16777216.0f, (float)(int)(k & 0xFFFFFF));
+            const float hf = kf * q.dt_min_f;
             float o[6], ol[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
