@@ -233,7 +233,10 @@ __global__ void __launch_bounds__(BLOCK * G, MINB) subset_jerk_kernel(const F32C
 // takes j-particles of the active clusters (grid-stride over their real
 // particles) and evaluates them against the active particles of the same
 // cluster, kFewBatch at a time; pair terms as in the subset kernel (FP32
-// offsets from float-pair centres, exact centre differences, MUFU rsqrt).
+// offsets from float-pair centres, exact centre differences, MUFU rsqrt),
+// except that position differences use the offsets' low parts when given
+// (q.pxl ...), so that close pairs are differenced exactly: a particle that
+// steps alone is the one whose step choice the force noise would drive.
 // Per thread and per warp FP32 sums, then FP64: the warps in order, the CTAs in
 // a fixed order by the last CTA (ticket), which also applies the epilogue.
 constexpr int kFewThreads = 256;
