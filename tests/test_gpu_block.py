@@ -276,6 +276,36 @@ def test_block_advance_reads_the_callers_arrays_again(mode):
     assert abs(gb1 - gb0) <= 0.01 * gb0 and abs(ge1 - ge0) <= 0.01 * ge0
 
 
+def tiny_system(n, seed=64):
+    if n == 1:
+        return np.zeros((3, 1)), np.array([[0.1], [-0.2], [0.05]]), np.ones(1)
+    if n == 2:  # a circular binary
+        pos = np.array([[-0.5, 0.5], [0.0, 0.0], [0.0, 0.0]])
+        vel = np.array([[0.0, 0.0], [-0.5, 0.5], [0.0, 0.0]])
+        return pos, vel, np.full(2, 0.5)
+    return ic.plummer(n, seed=seed)
+
+
+@pytest.mark.parametrize("mode", [nb.NBODY_F64, nb.NBODY_F32C])
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 129])
+def test_block_steps_tiny_systems(oracle, mode, n):
+    # one particle (no force: every step dt_max), a binary, and active sets on
+    # both sides of the few-particle limit (32) and of one 128-slot tile
+    pos, vel, mass = tiny_system(n)
+    gp, gv, ga, gj, gdt, gt, gb, ge = block_run(pos, vel, mass, 0.01, mode)
+    rp, rv, ra, rj, _, rdt, rb, re = oracle.block_hermite(pos, vel, mass, 0.01, T_END, DT_MAX, DT_MIN,
+                                                         0.02, 0.01)
+    assert np.all(gt == T_END)
+    if n == 1:
+        assert np.all(gdt == DT_MAX) and np.all(ga == 0.0) and np.all(gj == 0.0)
+    if mode == nb.NBODY_F64:
+        assert np.array_equal(gdt, rdt) and gb == rb and ge == re
+        np.testing.assert_allclose(gp, rp, rtol=0, atol=1e-12)
+    else:
+        assert np.mean(gdt == rdt) >= 0.95
+        assert np.abs(gp - rp).max() <= 1e-7
+
+
 def test_block_steps_save_evaluations():
     pos, vel, mass = cluster_system(3000, 56)
     *_, gb, ge = block_run(pos, vel, mass, 0.002, nb.NBODY_F32C)
