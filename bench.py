@@ -642,6 +642,46 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_block_drift(n, t_end):
+    """Energy drift of block steps, F32C against the FP64 path: a Plummer sphere
+    of n (seed 8), eps 1e-3, dt_max 2^-7, advanced dt_max per call to t_end,
+    E from nbody_energy after every call.  Prints one JSON line."""
+    import torch
+    import paper_2509_19294_gb300 as nb
+    from paper_2509_19294_gb300 import build as nbuild
+    from paper_2509_19294_gb300 import ic
+    if not nbuild.up_to_date():
+        nbuild.build()
+    pos, vel, mass = ic.plummer(n, seed=8)
+    dt_max = 2.0 ** -7
+    res = {}
+    for name, mode in (("f32c", nb.NBODY_F32C), ("f64", nb.NBODY_F64)):
+        with nb.nbody_init(n, 1e-3, mode=mode, reorder_every=4) as cb:
+            p_, v_, m_ = (torch.from_numpy(x.copy()).cuda() for x in (pos, vel, mass))
+            a_ = torch.empty((3, n), dtype=torch.float64, device="cuda")
+            j_ = torch.empty((3, n), dtype=torch.float64, device="cuda")
+            po_ = torch.empty(n, dtype=torch.float64, device="cuda")
+            nb.nbody_block_start(cb, p_, v_, m_, a_, j_, po_, dt_max, 2.0 ** -22, 0.02, 0.01)
+            e0 = nb.nbody_energy(cb, p_, v_, m_, po_)[0][2]
+            worst, k, blocks, evals = 0.0, 0, 0, 0
+            t0 = time.perf_counter()
+            while (k + 1) * dt_max <= t_end:
+                k += 1
+                blocks, evals = nb.nbody_block_advance(cb, p_, v_, m_, a_, j_, po_, k * dt_max)
+                e = nb.nbody_energy(cb, p_, v_, m_, po_)[0][2]
+                worst = max(worst, abs(e - e0) / abs(e0))
+            sec = time.perf_counter() - t0
+            res[name] = {"block_steps": int(blocks), "particle_evaluations": int(evals),
+                         "max_abs_dE_over_E": worst, "seconds": sec, "pos": p_.cpu().numpy()}
+    dx = np.abs(res["f32c"].pop("pos") - res["f64"].pop("pos")).max(axis=0)
+    print(json.dumps({"block_drift": {
+        "workload": f"Plummer sphere N={n} (seed 8), eps=1e-3, block steps dt_max 2^-7 (eta 0.02), "
+                    f"t=0..{t_end}, one advance call per dt_max, re-sort every 4 dt_max",
+        "f32c": res["f32c"], "f64": res["f64"],
+        "drift_ratio_f32c_over_f64": res["f32c"]["max_abs_dE_over_E"] / res["f64"]["max_abs_dE_over_E"],
+        "final_position_difference": {"median": float(np.median(dx)), "max": float(dx.max())}}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -660,7 +700,14 @@ def main():
                     help="particles per sphere (default 524288: the N=1M workload)")
     ap.add_argument("--tiles", default=None,
                     help="force the tile shape block,p,tj,split instead of autotuning")
+    ap.add_argument("--block-drift", default=None, metavar="N,T",
+                    help="only the block-step energy drift, F32C vs FP64 path (e.g. 16384,0.5; "
+                         "the FP64 path takes minutes)")
     args = ap.parse_args()
+    if args.block_drift:
+        n, t = args.block_drift.split(",")
+        run_block_drift(int(n), float(t))
+        return
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
