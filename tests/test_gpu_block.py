@@ -339,3 +339,14 @@ def test_block_api_errors():
         nb.nbody_block_start(ctx, p, v, m, a, j, None, DT_MAX, DT_MIN, 0.02, 0.01)
         with pytest.raises(nb.NBodyError):
             nb.nbody_block_advance(ctx, p, v, m, a, j, None, DT_MAX * 1.5)
+    for mode, ok in ((nb.NBODY_F32C, False), (nb.NBODY_F64, True)):
+        # F32C block steps keep step lengths as floats: dt_min >= 2^-126
+        with nb.nbody_init(n, 0.01, mode=mode) as ctx:
+            p, v, m = dev(pos), dev(vel), dev(mass)
+            a = torch.empty((3, n), dtype=torch.float64, device="cuda")
+            j = torch.empty((3, n), dtype=torch.float64, device="cuda")
+            if ok:
+                nb.nbody_block_start(ctx, p, v, m, a, j, None, 2.0 ** -100, 2.0 ** -130, 0.02, 0.01)
+            else:
+                with pytest.raises(nb.NBodyError):
+                    nb.nbody_block_start(ctx, p, v, m, a, j, None, 2.0 ** -100, 2.0 ** -130, 0.02, 0.01)
