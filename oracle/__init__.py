@@ -19,7 +19,8 @@ no fast-math).  This module only builds it and marshals numpy arrays:
 * ``hermite``      -- the fourth-order Hermite predictor-corrector integrator
   that uses the jerk (shared time step).
 * ``block_hermite`` -- the same scheme with individual power-of-two block time
-  steps chosen by Aarseth's criterion.
+  steps chosen by Aarseth's criterion; ``aarseth_step`` evaluates that criterion
+  alone from the acceleration and jerk at both ends of one step.
 
 Layouts follow the C ABI: positions/velocities/accelerations are ``[3, n]``
 float64 arrays, masses and potentials ``[n]``.
@@ -93,6 +94,8 @@ class Oracle:
         lib.oracle_block_hermite.argtypes = [i64, vp, vp, vp, d, d, d, d, d, d, d, vp, vp, vp, vp,
                                              ctypes.POINTER(i64)]
         lib.oracle_block_hermite.restype = i64
+        lib.oracle_aarseth_step.argtypes = [vp, vp, vp, vp, d, d, d]
+        lib.oracle_aarseth_step.restype = d
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
         self.lib = lib
@@ -227,6 +230,16 @@ def _block_hermite(self, pos, vel, mass, eps: float, t_end: float, dt_max: float
     return pos, vel, acc, jerk, pot, dt, int(blocks), int(ev.value)
 
 
+def _aarseth_step(self, a0, j0, a1, j1, h: float, eta: float, dt_max: float = float("inf")):
+    """Aarseth's step criterion from the acceleration and jerk at both ends of a
+    step of length h (the block integrator's next-step rule, before rounding to
+    a power of two)."""
+    v = [_c(x, (3,)) for x in (a0, j0, a1, j1)]
+    return float(self.lib.oracle_aarseth_step(*[_p(x) for x in v], float(h), float(eta),
+                                              float(dt_max)))
+
+
+Oracle.aarseth_step = _aarseth_step
 Oracle.block_hermite = _block_hermite
 Oracle.forces_jerk = _forces_jerk
 Oracle.forces_jerk_rows = _forces_jerk_rows

@@ -309,6 +309,33 @@ static double norm3(const double *q, int64_t n, int64_t i) {
 static double pow2_floor(double x) { return exp2(floor(log2(x))); }
 
 /*
+ * Aarseth's step criterion at the end of a Hermite step of length h (Makino &
+ * Aarseth 1992): with a0, j0 the acceleration and jerk at the step start and
+ * a1, j1 at its end, the cubic Hermite interpolant of a(t) gives the third
+ * derivative a3 (constant over the step) and the second derivative at the step
+ * start, which a3 carries to the step end:
+ *   a3 = (12 (a0 - a1) + 6 h (j0 + j1)) / h^3
+ *   a2 = (-6 (a0 - a1) - h (4 j0 + 2 j1)) / h^2 + h a3
+ * and the criterion is sqrt(eta (|a1| |a2| + |j1|^2) / (|j1| |a3| + |a2|^2)),
+ * or dt_max when the denominator vanishes.
+ */
+double oracle_aarseth_step(const double a0[3], const double j0[3], const double a1[3],
+                           const double j1[3], double h, double eta, double dt_max) {
+    double h2 = h * h, h3 = h2 * h;
+    double a2[3], a3[3];
+    for (int d = 0; d < 3; ++d) {
+        a3[d] = (12.0 * (a0[d] - a1[d]) + 6.0 * h * (j0[d] + j1[d])) / h3;
+        a2[d] = (-6.0 * (a0[d] - a1[d]) - h * (4.0 * j0[d] + 2.0 * j1[d])) / h2 + h * a3[d];
+    }
+    double na = sqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
+    double nj = sqrt(j1[0] * j1[0] + j1[1] * j1[1] + j1[2] * j1[2]);
+    double n2 = sqrt(a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2]);
+    double n3 = sqrt(a3[0] * a3[0] + a3[1] * a3[1] + a3[2] * a3[2]);
+    double den = nj * n3 + n2 * n2;
+    return den > 0.0 ? sqrt(eta * (na * n2 + nj * nj) / den) : dt_max;
+}
+
+/*
  * Block-step Hermite until every particle reaches t_end (a multiple of dt_max).
  * pos, vel in/out [3][n]; acc, jerk out [3][n] at t_end; pot out [n] at the
  * final predicted state of each particle's last step; dt_out [n] final steps;
@@ -350,27 +377,24 @@ int64_t oracle_block_hermite(int64_t n, double *pos, double *vel, const double *
             if (t[i] + dt[i] != tn) continue;
             double o[7];
             oracle_one_jerk_at(n, xp, vp, mass, eps, G, i, o);
-            double h = dt[i], h2 = h * h, h3 = h2 * h;
-            double a1[3], j1[3], a2[3], a3[3];
-            for (int d = 0; d < 3; ++d) {
+            double h = dt[i], h2 = h * h;
+            double a0[3], j0[3], a1[3], j1[3];
+            for (int d = 0; d < 3; ++d) { /* corrector */
                 int64_t q = d * n + i;
+                a0[d] = acc[q];
+                j0[d] = jerk[q];
                 a1[d] = o[d];
                 j1[d] = o[3 + d];
                 double v1 = vel[q] + (acc[q] + a1[d]) * h / 2.0 + (jerk[q] - j1[d]) * h2 / 12.0;
                 pos[q] = pos[q] + (vel[q] + v1) * h / 2.0 + (acc[q] - a1[d]) * h2 / 12.0;
                 vel[q] = v1;
-                a3[d] = (12.0 * (acc[q] - a1[d]) + 6.0 * h * (jerk[q] + j1[d])) / h3;
-                a2[d] = (-6.0 * (acc[q] - a1[d]) - h * (4.0 * jerk[q] + 2.0 * j1[d])) / h2 + h * a3[d];
                 acc[q] = a1[d];
                 jerk[q] = j1[d];
             }
             pot[i] = o[6];
-            double na = sqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
-            double nj = sqrt(j1[0] * j1[0] + j1[1] * j1[1] + j1[2] * j1[2]);
-            double n2 = sqrt(a2[0] * a2[0] + a2[1] * a2[1] + a2[2] * a2[2]);
-            double n3 = sqrt(a3[0] * a3[0] + a3[1] * a3[1] + a3[2] * a3[2]);
-            double den = nj * n3 + n2 * n2;
-            double da = den > 0.0 ? sqrt(eta * (na * n2 + nj * nj) / den) : dt_max;
+            /* next step: halve while above the criterion (not below dt_min),
+             * or double once when the doubled step is allowed */
+            double da = oracle_aarseth_step(a0, j0, a1, j1, h, eta, dt_max);
             double nd = h;
             while (nd > da && nd > dt_min) nd /= 2.0;
             if (nd == h && da >= 2.0 * h && 2.0 * h <= dt_max && fmod(tn, 2.0 * h) == 0.0) nd = 2.0 * h;

@@ -5,8 +5,16 @@ integrator; the paper computes the jerk (Sec. 3) but does not describe its
 stepping, so the scheme is written from Makino & Aarseth (1992).  Pinned by:
 reduction to the (pinned) shared-step Hermite bit for bit when every step is
 forced to dt_max; the block-time invariants (powers of two, commensurate
-times, synchronisation at t_end); and convergence of a hierarchical triple,
-whose members take different steps, towards an accurate shared-step reference.
+times, synchronisation at t_end); convergence of a hierarchical triple, whose
+members take different steps, towards an accurate shared-step reference; and
+the step rules themselves:
+* Aarseth's criterion from the Hermite interpolation is exact when the
+  acceleration history is a cubic in time (the interpolant then reproduces
+  the second derivative at the step end and the third derivative exactly);
+* on a circular binary every derivative has a closed-form magnitude,
+  |a^(k)| = omega^(k+2) r, so the first step rule eta_s |a| / |a'| is
+  eta_s / omega and the criterion is sqrt(eta) / omega: the oracle's steps
+  must be the powers of two just below those values.
 """
 import numpy as np
 import pytest
@@ -72,3 +80,61 @@ def test_block_steps_converge_to_accurate_reference(oracle):
     assert steps[1] == steps[0] / 4, steps
     assert errs[1] < errs[0] / 100, errs
     assert errs[1] < 1e-6
+
+
+def test_criterion_is_exact_for_a_cubic_acceleration_history(oracle):
+    # a(t) = c0 + c1 t + c2 t^2 + c3 t^3: a'(h), a''(h) = 2 c2 + 6 c3 h and
+    # a'''(h) = 6 c3 are exact, and the criterion takes a'' at the step END
+    rng = np.random.default_rng(41)
+    nrm = np.linalg.norm
+    eta = 0.02
+    for h in (0.5, 2.0 ** -3, 2.0 ** -6):
+        for _ in range(4):
+            c0, c1, c2, c3 = rng.normal(size=(4, 3))
+            a0, j0 = c0, c1
+            a1 = c0 + c1 * h + c2 * h ** 2 + c3 * h ** 3
+            j1 = c1 + 2 * c2 * h + 3 * c3 * h ** 2
+            s2, s3 = 2 * c2 + 6 * c3 * h, 6 * c3
+            want = np.sqrt(eta * (nrm(a1) * nrm(s2) + nrm(j1) ** 2) / (nrm(j1) * nrm(s3) + nrm(s2) ** 2))
+            got = oracle.aarseth_step(a0, j0, a1, j1, h, eta)
+            assert got == pytest.approx(want, rel=1e-9), (h, got, want)
+
+
+def _circular_binary(omega):
+    # equal masses 1/2 (G = 1, total mass 1) at separation d with
+    # omega^2 = 1 / d^3: each body moves on a circle of radius d/2
+    d = omega ** (-2.0 / 3.0)
+    v = omega * d / 2
+    pos = np.array([[d / 2, -d / 2], [0.0, 0.0], [0.0, 0.0]])
+    vel = np.array([[0.0, 0.0], [v, -v], [0.0, 0.0]])
+    return pos, vel, np.array([0.5, 0.5])
+
+
+def test_first_steps_on_a_circular_binary(oracle):
+    # |a| / |a'| = 1 / omega for each body: the first step is the largest
+    # power of two <= eta_s / omega (here 2^-9.5, so 2^-10); t_end = 0 stops
+    # before the first block step
+    omega = 8.0
+    pos, vel, mass = _circular_binary(omega)
+    eta_s = omega * 2.0 ** -9.5
+    *_, dt, blocks, _ = oracle.block_hermite(pos, vel, mass, 0.0, 0.0, 2.0 ** -3, 2.0 ** -30, 0.02,
+                                             eta_s)
+    assert blocks == 0 and np.all(dt == 2.0 ** -10), dt
+
+
+def test_circular_binary_settles_on_the_closed_form_step(oracle):
+    # sqrt(eta) / omega = 2^-7.5: from first steps of 2^-10 the doubling rule
+    # climbs one level per allowed step to 2^-8 and stays there (2^-7 is above
+    # the criterion); two orbits (t_end = 1.5, omega t = 12)
+    omega = 8.0
+    pos, vel, mass = _circular_binary(omega)
+    eta = (omega * 2.0 ** -7.5) ** 2
+    eta_s = omega * 2.0 ** -9.5
+    bp, bv, *_, dt, blocks, evals = oracle.block_hermite(pos, vel, mass, 0.0, 1.5, 2.0 ** -3,
+                                                         2.0 ** -30, eta, eta_s)
+    assert np.all(dt == 2.0 ** -8), dt
+    # every step after the climb is 2^-8: a few climbing steps plus 1.5 / 2^-8
+    assert 1.5 * 2 ** 8 <= blocks <= 1.5 * 2 ** 8 + 4, blocks
+    # and the orbit stays circular to the fourth-order scheme's accuracy
+    r = np.linalg.norm(bp[:, 0] - bp[:, 1])
+    assert abs(r - omega ** (-2.0 / 3.0)) < 1e-7, r

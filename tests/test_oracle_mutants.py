@@ -46,8 +46,11 @@ MUTANTS = {
     "jerk_velocity_order": ("double ux = vx[j] - vx[i], uy = vy[j] - vy[i], uz = vz[j] - vz[i];",
                             "double ux = vx[i] - vx[j], uy = vy[i] - vy[j], uz = vz[i] - vz[j];"),
     "jerk_self_term_kept": ("        if (j == i) continue;\n        double rx", "        double rx"),
-    "block_criterion": ("double da = den > 0.0 ? sqrt(eta * (na * n2 + nj * nj) / den) : dt_max;",
-                        "double da = den > 0.0 ? sqrt(eta * (na * n2 + nj * nj) / den) * 8.0 : dt_max;"),
+    "block_criterion": ("return den > 0.0 ? sqrt(eta * (na * n2 + nj * nj) / den) : dt_max;",
+                        "return den > 0.0 ? sqrt(eta * (na * n2 + nj * nj) / den) * 8.0 : dt_max;"),
+    "block_criterion_a2_at_step_start": (" / h2 + h * a3[d];", " / h2;"),
+    "block_first_step_inverted": ("double d = jn > 0.0 ? eta_s * an / jn : dt_max;",
+                                  "double d = jn > 0.0 ? eta_s * jn / an : dt_max;"),
     "block_prediction": ("xp[q] = pos[q] + vel[q] * h + acc[q] * h2 / 2.0 + jerk[q] * h3 / 6.0;",
                          "xp[q] = pos[q] + vel[q] * h + acc[q] * h2 / 2.0;"),
     "hermite_corrector": ("(jerk[q] - j1[q]) * dt2 / 12.0;", "(jerk[q] - j1[q]) * dt2 / 6.0;"),
@@ -85,6 +88,9 @@ def _pin_calls(orc):
         lambda: bpins.test_equal_steps_reduce_to_shared_hermite(orc),
         lambda: bpins.test_block_invariants_and_synchronisation(orc),
         lambda: bpins.test_block_steps_converge_to_accurate_reference(orc),
+        lambda: bpins.test_criterion_is_exact_for_a_cubic_acceleration_history(orc),
+        lambda: bpins.test_first_steps_on_a_circular_binary(orc),
+        lambda: bpins.test_circular_binary_settles_on_the_closed_form_step(orc),
     ]
     return calls
 
