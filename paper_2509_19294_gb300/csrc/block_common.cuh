@@ -195,14 +195,12 @@ __device__ __forceinline__ void correct_particle_x4(const BlockCorrect &c, int64
     correct_particle_x4_pre(c, i, slot, valid, sub, h, a0, j0, v0, x0, fc, fv, a1, j1, p1, tn, tnq);
 }
 
-// FP64 epilogue of one active particle: scale by G, remove the self term of
-// phi (its own j-tile contributed m_i rsqrt(eps^2) exactly), then correct the
-// particle (corr.sc set) or store a1, j1, p1 at its row.
+// FP64 epilogue of one active particle: scale by G, then correct the particle
+// (corr.sc set) or store a1, j1, p1 at its row.
 __device__ __forceinline__ void subset_finalize(const F32CJerkParams &p, const BlockCorrect &corr,
-                                                const ClusterDev &cl, int slot, const double (&r)[7]) {
+                                                int slot, const double (&r)[7]) {
     const int64_t u = p.perm[slot];
-    double ph = r[6];
-    if (cl.eps2f > 0.0f) ph -= (double)__fmul_rn(p.pm[slot], rsqrt_mufu(cl.eps2f));
+    const double ph = r[6];
     if (corr.sc) {
         const double A1[3] = {p.G * r[0], p.G * r[1], p.G * r[2]};
         const double J1[3] = {p.G * r[3], p.G * r[4], p.G * r[5]};

@@ -4,8 +4,9 @@
 // cluster; the tail kernel runs either the few-particle pass or the ordered sum
 // of the subset kernels' split partials.  An active particle is evaluated with
 // its own j-set offset and its own tile centre: per j-tile each thread forms
-// the exact centre difference for each of its particles, so the self pair is
-// exactly zero, as in the full kernels.  The corrector runs in the epilogue.
+// the exact centre difference for each of its particles, so the self pair's
+// separation is exactly zero, as in the full kernels, and its potential term is
+// masked before it enters the FP32 sums.  The corrector runs in the epilogue.
 #include <algorithm>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -23,10 +24,6 @@ namespace nbody {
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -159,19 +156,21 @@ struct SubsetKernel {
                 for (int k = 0; k < P; ++k)
 #pragma unroll
                     for (int c = 0; c < NC; ++c) acc[k][c] = make_float2(0.0f, 0.0f);
-#pragma unroll 1
-                for (int v = g * COLS; v < (g + 1) * COLS; ++v) {
-                    float4 Q[NA];
+                // a j-tile holding one of the warp's own slots masks the self
+                // pairs' potential terms (warp-uniform branch; the active
+                // list is in slot order, so few tiles take it)
+                const int gs = cl.slot_begin + (it.jt0 + t) * TJ;
+                int d[P];
+                bool own_here = false;
 #pragma unroll
-                    for (int a = 0; a < NA; ++a) Q[a] = sm.j[b][a][v];
-                    float2 J[NA];
-#pragma unroll
-                    for (int a = 0; a < NA; ++a) J[a] = make_float2(Q[a].x, Q[a].y);
-                    JK::body(J, e2, ni, acc);
-#pragma unroll
-                    for (int a = 0; a < NA; ++a) J[a] = make_float2(Q[a].z, Q[a].w);
-                    JK::body(J, e2, ni, acc);
+                for (int k = 0; k < P; ++k) {
+                    d[k] = slot[k] - gs;
+                    own_here |= d[k] >= 0 && d[k] < TJ;
                 }
+                if (!EPS_ZERO && __any_sync(0xffffffffu, own_here))
+                    JK::template tile_pass<true>(sm, b, g * COLS, (g + 1) * COLS, e2, ni, acc, d);
+                else
+                    JK::template tile_pass<false>(sm, b, g * COLS, (g + 1) * COLS, e2, ni, acc, d);
 #pragma unroll
                 for (int k = 0; k < P; ++k)
 #pragma unroll
@@ -210,7 +209,7 @@ struct SubsetKernel {
             if (it.nsplit <= 1) {
 #pragma unroll
                 for (int k = 0; k < P; ++k)
-                    if (valid[k]) subset_finalize(p, q.corr, cl, slot[k], res[k]);
+                    if (valid[k]) subset_finalize(p, q.corr, slot[k], res[k]);
                 continue;
             }
             double *mine = q.partial + (size_t)(it.pbase + it.split) * NC * CS;
@@ -251,17 +250,17 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
     __shared__ float ownl[kFewMax][3];  // low parts of the position offsets
     __shared__ float4 oc[kFewMax][4];
     __shared__ int ocl[kFewMax];
+    __shared__ int oslot[kFewMax];  // j-set slot of each active particle (its self pair)
     __shared__ float wsum[kFewThreads / 32][kFewBatch][7];
     __shared__ double csum[kFewMax][7];
     __shared__ double fsum[kFewThreads];  // [group][output], ngrp * n_out <= kFewThreads
     __shared__ int fjb[kFewMax + 1], fcl[kFewMax], fab[kFewMax], fsb[kFewMax];
     __shared__ float fe2[kFewMax];
     // the corrector's inputs, fetched by cp.async while the j-loop runs: per
-    // particle h, then a0, j0, v0, x0 of each component; its mass; with a
-    // mirror, its tile frame (origin c0, velocity) and the frame time
+    // particle h, then a0, j0, v0, x0 of each component; with a mirror, its
+    // tile frame (origin c0, velocity) and the frame time
     __shared__ double pre[kFewMax][13];
     __shared__ int64_t pre_u[kFewMax];
-    __shared__ float pre_m[kFewMax];
     __shared__ double pre_c0[kFewMax][3];
     __shared__ float4 pre_cv[kFewMax];
     __shared__ long long pre_t0q;
@@ -282,6 +281,7 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
     __syncthreads();
     for (int a = threadIdx.x; a < na; a += blockDim.x) {
         const int slot = act[a];
+        oslot[a] = slot;
         own[a][0] = p.px[slot];
         own[a][1] = p.py[slot];
         own[a][2] = p.pz[slot];
@@ -312,7 +312,6 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
                 cp_async8(&pre[a][3 + 4 * d], c.vel + k);
                 cp_async8(&pre[a][4 + 4 * d], c.pos + k);
             }
-            cp_async4(&pre_m[a], p.pm + slot);
             if (c.m.xr) {
                 const int tile = slot / c.m.tc;
 #pragma unroll
@@ -337,7 +336,7 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
             // the loads of kFewUnroll j-particles first, so their latencies overlap
             float J[kFewUnroll][7], Jl[kFewUnroll][3];
             float4 jcen[kFewUnroll][4];
-            int ej[kFewUnroll];
+            int ej[kFewUnroll], jslot[kFewUnroll];
 #pragma unroll
             for (int u = 0; u < kFewUnroll; ++u) {
                 const int g = g0 + u * stride;
@@ -347,6 +346,7 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
                     while (e + 1 < nf && fjb[e + 1] <= g) ++e;
                     ej[u] = e;
                     const int js = fsb[e] + (g - fjb[e]);
+                    jslot[u] = js;
                     J[u][0] = p.px[js];
                     J[u][1] = p.py[js];
                     J[u][2] = p.pz[js];
@@ -408,7 +408,8 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
                     const float ms = __fmul_rn(J[u][3], s), s2 = __fmul_rn(s, s);
                     const float w3 = __fmul_rn(ms, s2);
                     const float beta = __fmul_rn(rv, __fmul_rn(s2, -3.0f));
-                    acc[k][6] = __fadd_rn(acc[k][6], ms);
+                    // the self pair (r = 0 exactly) adds nothing; its potential term is masked
+                    acc[k][6] = __fadd_rn(acc[k][6], jslot[u] == oslot[a] ? 0.0f : ms);
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         acc[k][q] = __fmaf_rn(w3, r[q], acc[k][q]);
@@ -486,9 +487,7 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
             const int a = threadIdx.x / 4, sub = threadIdx.x % 4;
             const bool valid = a < na;
             const int aa = valid ? a : 0;
-            const float e2 = fe2[ocl[aa]];
-            double ph = csum[aa][6];
-            if (e2 > 0.0f) ph -= (double)__fmul_rn(pre_m[aa], rsqrt_mufu(e2));
+            const double ph = csum[aa][6];
             const int cp = sub < 3 ? sub : 0;
             const long long tnq = sc->t_next_q;
             double fc = 0.0, fv = 0.0;
@@ -505,7 +504,7 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
             double r[7];
 #pragma unroll
             for (int c = 0; c < 7; ++c) r[c] = csum[a][c];
-            subset_finalize(p, q.corr, p.cl[fcl[ocl[a]]], act[a], r);
+            subset_finalize(p, q.corr, act[a], r);
         }
     }
     if (threadIdx.x == 0) sc->ticket_few = 0;
@@ -559,8 +558,6 @@ __device__ void reduce_pass(const F32CSubsetParams &q, const SubItem *__restrict
                     rp += part[h][6][a];
                 }
                 const int slot = q.act_slot[it.a0 + (valid ? la : (u % subs) * 32)];
-                const float e2 = q.base.cl[it.cluster].eps2f;
-                if (e2 > 0.0f) rp -= (double)__fmul_rn(q.base.pm[slot], rsqrt_mufu(e2));
                 const double G = q.base.G;
                 correct_particle_x4(q.corr, q.base.perm[slot], slot, valid, sub, G * ra, G * rj, -G * rp,
                                     sc->t_next, sc->t_next_q);
@@ -573,7 +570,7 @@ __device__ void reduce_pass(const F32CSubsetParams &q, const SubItem *__restrict
 #pragma unroll
                 for (int h = 1; h < kReduceWarps; ++h) r[c] += part[h][c][lane];
             }
-            subset_finalize(q.base, q.corr, q.base.cl[it.cluster], q.act_slot[it.a0 + l], r);
+            subset_finalize(q.base, q.corr, q.act_slot[it.a0 + l], r);
         }
         __syncthreads();
     }

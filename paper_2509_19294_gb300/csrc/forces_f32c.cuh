@@ -33,9 +33,13 @@
 //   * Split j-ranges (small N or load balance): each split writes its FP64
 //     partials; the CTA that finishes last (atomic ticket, no waiting) adds
 //     them in split order, so the result is bitwise deterministic.
-//   * Epilogue in FP64: scale by G, remove the self term of phi that the
-//     unmasked diagonal added (exactly the FP32 value it added), scatter to the
-//     caller's row through perm, and optionally apply the closing half-kick.
+//   * Self pair: on the diagonal j-tiles (those of the CTA's own centre tile)
+//     each thread drops the potential term of its own slot before it enters
+//     the FP32 tile sum (its acceleration term is exactly 0: the separation is
+//     0); every other j-tile runs the unmasked loop.  With eps = 0 the r^2 > 0
+//     guard already gives the self pair (and coincident pairs) zero.
+//   * Epilogue in FP64: scale by G, scatter to the caller's row through perm,
+//     and optionally apply the closing half-kick.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -64,11 +68,22 @@ __device__ __forceinline__ void centre_diff(float ih, float il, float jh, float 
     lo = __fadd_rn(e, __fsub_rn(il, jl));
 }
 
+// Folds one tile's FP32 sum x into the running sum s with Kahan compensation c.
+// NBODY_TILE_SUM_COMPENSATION=0 (an accuracy ablation: build.py builds it only
+// on request, as libnbody_ablate_tile_sums.so) folds with a plain FP32 add.
+#ifndef NBODY_TILE_SUM_COMPENSATION
+#define NBODY_TILE_SUM_COMPENSATION 1
+#endif
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+#if NBODY_TILE_SUM_COMPENSATION
     const float y = __fsub_rn(x, c);
     const float t = __fadd_rn(s, y);
     c = __fsub_rn(__fsub_rn(t, s), y);
     s = t;
+#else
+    c = 0.0f;
+    s = __fadd_rn(s, x);
+#endif
 }
 
 template <int BLOCK, int P, int TJ, bool EPS_ZERO>
@@ -116,11 +131,16 @@ struct F32CKernel {
         centre_diff(ih.z, il.z, jh.z, jl.z, sm.shift[b][2], sm.shift[b][6]);
     }
 
+    // One pair of j's (the halves of each float2, tile positions j0 and j0 + 1)
+    // against the thread's P i-particles.  MASK: d[k] is the tile position of
+    // i-particle k's own slot (or outside the tile), whose potential term is
+    // dropped.
+    template <bool MASK>
     __device__ static __forceinline__ void body(float2 xj, float2 yj, float2 zj, float2 mj,
                                                 const float2 e2, const float2 (&nx)[P],
                                                 const float2 (&ny)[P], const float2 (&nz)[P],
                                                 float2 (&ax)[P], float2 (&ay)[P], float2 (&az)[P],
-                                                float2 (&ph)[P]) {
+                                                float2 (&ph)[P], const int (&d)[P], int j0) {
 #pragma unroll
         for (int k = 0; k < P; ++k) {
             const float2 dx = __fadd2_rn(xj, nx[k]);
@@ -140,24 +160,47 @@ struct F32CKernel {
             const float2 ms = __fmul2_rn(mj, s);
             const float2 s2 = __fmul2_rn(s, s);
             const float2 w3 = __fmul2_rn(ms, s2);
-            ph[k] = __fadd2_rn(ph[k], ms);
+            float2 mp = ms;
+            if (MASK) {
+                mp.x = d[k] == j0 ? 0.0f : ms.x;
+                mp.y = d[k] == j0 + 1 ? 0.0f : ms.y;
+            }
+            ph[k] = __fadd2_rn(ph[k], mp);
             ax[k] = __ffma2_rn(w3, dx, ax[k]);
             ay[k] = __ffma2_rn(w3, dy, ay[k]);
             az[k] = __ffma2_rn(w3, dz, az[k]);
         }
     }
 
-    // FP64 epilogue for one i-slot: scale, self-term removal, scatter, kick.
+    // All pairs of one shared-memory j-tile (buffer b) against the thread's P
+    // i-particles, summed in FP32.
+    template <bool MASK>
+    __device__ static __forceinline__ void tile_pass(const Smem &sm, int b, const float2 e2,
+                                                     const float2 (&nx)[P], const float2 (&ny)[P],
+                                                     const float2 (&nz)[P], float2 (&ax)[P],
+                                                     float2 (&ay)[P], float2 (&az)[P],
+                                                     float2 (&ph)[P], const int (&d)[P]) {
+        const float4 *jx = sm.j[b][0];
+        const float4 *jy = sm.j[b][1];
+        const float4 *jz = sm.j[b][2];
+        const float4 *jm = sm.j[b][3];
+#pragma unroll 2
+        for (int v = 0; v < TJ / 4; ++v) {
+            const float4 X = jx[v], Y = jy[v], Z = jz[v], M = jm[v];
+            body<MASK>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+                       make_float2(M.x, M.y), e2, nx, ny, nz, ax, ay, az, ph, d, 4 * v);
+            body<MASK>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+                       make_float2(M.z, M.w), e2, nx, ny, nz, ax, ay, az, ph, d, 4 * v + 2);
+        }
+    }
+
+    // FP64 epilogue for one i-slot: scale, scatter, kick.
     __device__ static __forceinline__ void finalize(const F32CParams &p, const ClusterDev &cl,
                                                     int slot, double sx, double sy, double sz,
-                                                    double sp, float mi) {
+                                                    double sp) {
         const int local = slot - cl.slot_begin;
         if (local >= cl.n) return;
         const int64_t u = p.perm[slot];
-        if (cl.eps2f > 0.0f) {
-            // the diagonal pair (dx = dy = dz = 0 exactly) added m_i * rsqrt(eps^2) to phi
-            sp -= (double)__fmul_rn(mi, rsqrt_mufu(cl.eps2f));
-        }
         const double a0 = p.G * sx, a1 = p.G * sy, a2 = p.G * sz;
         p.acc[u] = a0;
         p.acc[p.n + u] = a1;
@@ -241,18 +284,16 @@ struct F32CKernel {
 #pragma unroll
                 for (int k = 0; k < P; ++k) ax[k] = ay[k] = az[k] = ph[k] = zero2;
 
-                const float4 *jx = sm.j[b][0];
-                const float4 *jy = sm.j[b][1];
-                const float4 *jz = sm.j[b][2];
-                const float4 *jm = sm.j[b][3];
-#pragma unroll 2
-                for (int v = 0; v < TJ / 4; ++v) {
-                    const float4 X = jx[v], Y = jy[v], Z = jz[v], M = jm[v];
-                    body(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
-                         make_float2(M.x, M.y), e2, nx, ny, nz, ax, ay, az, ph);
-                    body(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
-                         make_float2(M.z, M.w), e2, nx, ny, nz, ax, ay, az, ph);
-                }
+                // diagonal j-tile (inside the CTA's own centre tile): mask the
+                // self pair's potential term (CTA-uniform branch)
+                const int gs = cl.slot_begin + (it.jt0 + t) * TJ;
+                int d[P];
+#pragma unroll
+                for (int k = 0; k < P; ++k) d[k] = ibase + threadIdx.x + k * BLOCK - gs;
+                if (!EPS_ZERO && gs / TC == it.tile)
+                    tile_pass<true>(sm, b, e2, nx, ny, nz, ax, ay, az, ph, d);
+                else
+                    tile_pass<false>(sm, b, e2, nx, ny, nz, ax, ay, az, ph, d);
 #pragma unroll
                 for (int k = 0; k < P; ++k) {
                     kahan_add(ksum[k][0], kcmp[k][0], __fadd_rn(ax[k].x, ax[k].y));
@@ -278,7 +319,7 @@ struct F32CKernel {
 #pragma unroll
                 for (int k = 0; k < P; ++k) {
                     const int slot = ibase + threadIdx.x + k * BLOCK;
-                    finalize(p, cl, slot, res[k][0], res[k][1], res[k][2], res[k][3], p.pm[slot]);
+                    finalize(p, cl, slot, res[k][0], res[k][1], res[k][2], res[k][3]);
                 }
                 continue;  // the loop head's __syncthreads orders sm.item reuse
             }
@@ -309,7 +350,7 @@ struct F32CKernel {
                     for (int c = 0; c < 4; ++c) acc4[c] += __ldcg(ps + c * TC + l);
                 }
                 const int slot = ibase + l;
-                finalize(p, cl, slot, acc4[0], acc4[1], acc4[2], acc4[3], p.pm[slot]);
+                finalize(p, cl, slot, acc4[0], acc4[1], acc4[2], acc4[3]);
             }
         }
     }

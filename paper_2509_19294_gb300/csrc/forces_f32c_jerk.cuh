@@ -13,7 +13,8 @@
 // double-buffered shared memory, two j-particles per f32x2 instruction, FP32
 // offsets from float-pair tile centres for positions AND velocities, Kahan-
 // compensated per-tile sums, FP64 split reduction and epilogue; centre
-// differences as float pairs added per particle (see forces_f32c.cuh).  Per pair:
+// differences as float pairs added per particle, the self pair's potential term
+// masked on the diagonal j-tiles (see forces_f32c.cuh).  Per pair:
 // 3 add (r), 3 add (u), 3 fma (r^2), 3 (r.u), 1 rsqrt, 3 mul (m s, s^2, m s^3),
 // 2 mul (beta = -3 (r.u) s^2), 1 add (phi), 3 fma (a), 6 fma (jerk) =
 // 27 FP32 operations + 1 MUFU.
@@ -88,9 +89,14 @@ struct F32CJerkKernel {
         c[3] = p.vchl[2 * tile + 1];
     }
 
-    // One j-pair (two consecutive j's in the halves of each float2) against P i's.
+    // One j-pair (two consecutive j's in the halves of each float2, at tile
+    // positions j0 and j0 + 1) against P i's.  MASK: d[k] is the tile position
+    // of i-particle k's own slot (or outside the tile), whose potential term is
+    // dropped; its acceleration and jerk terms are exactly 0 (r = u = 0).
+    template <bool MASK>
     __device__ static __forceinline__ void body(const float2 (&J)[NA], const float2 e2,
-                                                const float2 (&ni)[P][6], float2 (&acc)[P][NC]) {
+                                                const float2 (&ni)[P][6], float2 (&acc)[P][NC],
+                                                const int (&d)[P], int j0) {
         const float2 m3 = make_float2(-3.0f, -3.0f);
 #pragma unroll
         for (int k = 0; k < P; ++k) {
@@ -118,7 +124,12 @@ struct F32CJerkKernel {
             const float2 s2 = __fmul2_rn(s, s);
             const float2 w3 = __fmul2_rn(ms, s2);
             const float2 beta = __fmul2_rn(rv, __fmul2_rn(s2, m3));  // -3 (r.u) s^2
-            acc[k][6] = __fadd2_rn(acc[k][6], ms);
+            float2 mp = ms;
+            if (MASK) {
+                mp.x = d[k] == j0 ? 0.0f : ms.x;
+                mp.y = d[k] == j0 + 1 ? 0.0f : ms.y;
+            }
+            acc[k][6] = __fadd2_rn(acc[k][6], mp);
             acc[k][0] = __ffma2_rn(w3, dx, acc[k][0]);
             acc[k][1] = __ffma2_rn(w3, dy, acc[k][1]);
             acc[k][2] = __ffma2_rn(w3, dz, acc[k][2]);
@@ -128,13 +139,33 @@ struct F32CJerkKernel {
         }
     }
 
+    // All pairs of columns [v0, v1) of the shared-memory j-tile in buffer b
+    // (four j's per column) against the thread's P i-particles, in FP32.
+    template <bool MASK, class SM>
+    __device__ static __forceinline__ void tile_pass(const SM &sm, int b, int v0, int v1,
+                                                     const float2 e2, const float2 (&ni)[P][6],
+                                                     float2 (&acc)[P][NC], const int (&d)[P]) {
+#pragma unroll 1
+        for (int v = v0; v < v1; ++v) {
+            float4 Q[NA];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) Q[a] = sm.j[b][a][v];
+            float2 J[NA];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) J[a] = make_float2(Q[a].x, Q[a].y);
+            body<MASK>(J, e2, ni, acc, d, 4 * v);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) J[a] = make_float2(Q[a].z, Q[a].w);
+            body<MASK>(J, e2, ni, acc, d, 4 * v + 2);
+        }
+    }
+
     __device__ static __forceinline__ void finalize(const F32CJerkParams &p, const ClusterDev &cl,
-                                                    int slot, const double (&r)[NC], float mi) {
+                                                    int slot, const double (&r)[NC]) {
         const int local = slot - cl.slot_begin;
         if (local >= cl.n) return;
         const int64_t u = p.perm[slot];
-        double ph = r[6];
-        if (cl.eps2f > 0.0f) ph -= (double)__fmul_rn(mi, rsqrt_mufu(cl.eps2f));
+        const double ph = r[6];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             p.acc[d * p.n + u] = p.G * r[d];
@@ -210,19 +241,16 @@ struct F32CJerkKernel {
                 for (int k = 0; k < P; ++k)
 #pragma unroll
                     for (int c = 0; c < NC; ++c) acc[k][c] = make_float2(0.0f, 0.0f);
-#pragma unroll 1
-                for (int v = 0; v < TJ / 4; ++v) {
-                    float4 Q[NA];
+                // diagonal j-tile (inside the CTA's own centre tile): mask the
+                // self pair's potential term (CTA-uniform branch)
+                const int gs = cl.slot_begin + (it.jt0 + t) * TJ;
+                int d[P];
 #pragma unroll
-                    for (int a = 0; a < NA; ++a) Q[a] = sm.j[b][a][v];
-                    float2 J[NA];
-#pragma unroll
-                    for (int a = 0; a < NA; ++a) J[a] = make_float2(Q[a].x, Q[a].y);
-                    body(J, e2, ni, acc);
-#pragma unroll
-                    for (int a = 0; a < NA; ++a) J[a] = make_float2(Q[a].z, Q[a].w);
-                    body(J, e2, ni, acc);
-                }
+                for (int k = 0; k < P; ++k) d[k] = ibase + threadIdx.x + k * BLOCK - gs;
+                if (!EPS_ZERO && gs / TC == it.tile)
+                    tile_pass<true>(sm, b, 0, TJ / 4, e2, ni, acc, d);
+                else
+                    tile_pass<false>(sm, b, 0, TJ / 4, e2, ni, acc, d);
 #pragma unroll
                 for (int k = 0; k < P; ++k)
 #pragma unroll
@@ -245,7 +273,7 @@ struct F32CJerkKernel {
 #pragma unroll
                 for (int k = 0; k < P; ++k) {
                     const int slot = ibase + threadIdx.x + k * BLOCK;
-                    finalize(p, cl, slot, res[k], p.pm[slot]);
+                    finalize(p, cl, slot, res[k]);
                 }
                 continue;
             }
@@ -277,7 +305,7 @@ struct F32CJerkKernel {
                     for (int c = 0; c < NC; ++c) tot[c] += __ldcg(ps + c * TC + l);
                 }
                 const int slot = ibase + l;
-                finalize(p, cl, slot, tot, p.pm[slot]);
+                finalize(p, cl, slot, tot);
             }
         }
     }

@@ -7,8 +7,10 @@
 //   * px/py/pz/pm: float[n_pad] SoA, the FP32 offset of each particle from its
 //     tile's centre, and its mass rounded to FP32.
 //   * chl: float4[n_tiles][2], each tile's centre as an unevaluated float pair
-//     (hi.x + lo.x, ...): the FP64 mean of the tile's positions split into
-//     hi = fl32(c) and lo = fl32(c - hi).
+//     (hi.x + lo.x, ...): the pack kernels store the FP32 mean of the tile's
+//     FP32-rounded positions as hi and lo = 0 (offsets are FP64 differences
+//     from that centre, rounded once); the block-step pack stores its tile
+//     frame's position, an FP64 value, as hi + lo.
 //   * perm: int32[n_pad], the caller's row of each packed slot (-1 for pads).
 //     Identity within each cluster unless Morton reordering is on.
 //   * items: the work queue of the force kernel, one entry per
@@ -18,7 +20,6 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
-#include <string.h>
 #include <string.h>
 
 namespace nbody {

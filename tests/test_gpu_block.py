@@ -350,3 +350,33 @@ def test_block_api_errors():
             else:
                 with pytest.raises(nb.NBodyError):
                     nb.nbody_block_start(ctx, p, v, m, a, j, None, 2.0 ** -100, 2.0 ** -130, 0.02, 0.01)
+
+
+@pytest.mark.parametrize("n", [24, 200])
+def test_f32c_block_potential_has_no_self_term(oracle, n):
+    # a heavy particle (m = 1) among light ones with eps = 1e-6: its self term
+    # m / eps is ~1e10 times its potential.  One block step with every particle
+    # active (the few-particle pass for n = 24, the subset kernel for n = 200):
+    # the stored potential equals the oracle's block scheme to the FP32C bound
+    rng = np.random.default_rng(71 + n)
+    pos = rng.uniform(-0.5, 0.5, size=(3, n))
+    vel = np.zeros((3, n))
+    mass = np.full(n, 1e-6)
+    h = n // 3
+    mass[h] = 1.0
+    with nb.nbody_init(n, 1e-6, mode=nb.NBODY_F32C) as ctx:
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        a = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        j = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        ph = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_block_start(ctx, p, v, m, a, j, ph, 2.0 ** -10, 2.0 ** -30, 0.02, 0.01)
+        _, rj, rp0 = oracle.forces_jerk(pos, vel, mass, 1e-6)
+        ep = metrics.rel_pot_errors(host(ph), rp0)
+        assert ep[h] <= 1e-5 and ep.max() <= 1e-4, (ep[h], ep.max())
+        blocks, evals = nb.nbody_block_advance(ctx, p, v, m, a, j, ph, 2.0 ** -10)
+        gpot = host(ph)
+    *_, rpot, rdt, rb, re = oracle.block_hermite(pos, vel, mass, 1e-6, 2.0 ** -10, 2.0 ** -10,
+                                                 2.0 ** -30, 0.02, 0.01)
+    assert (blocks, evals) == (rb, re) == (1, n)
+    ep = metrics.rel_pot_errors(gpot, rpot)
+    assert ep[h] <= 1e-5 and ep.max() <= 1e-4, (ep[h], ep.max())
