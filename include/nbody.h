@@ -16,13 +16,17 @@
  * Two arithmetic modes (chosen per context):
  *   NBODY_F64  -- every pairwise operation in IEEE double.
  *   NBODY_F32C -- positions stay FP64; each tile of particles is re-expressed
- *                 as FP32 offsets from its own centre (the FP64 mean of its
- *                 positions, kept as a float pair), pairwise terms run
- *                 in FP32 (hardware rsqrt), each particle's per-tile partial
- *                 sum is folded into a Kahan-compensated FP32 accumulator, and
- *                 the cross-CTA reduction, the final scaling by G and the
- *                 leapfrog run in FP64.  This is the paper's mixed-precision
- *                 split (FP32 forces, FP64 everything else, Sec. 3).
+ *                 as FP32 offsets from its own centre (the FP32 mean of its
+ *                 FP32-rounded positions, held as a float pair whose low part
+ *                 is 0: each offset is the FP64 difference from that centre,
+ *                 rounded once), pairwise terms run in FP32 (hardware rsqrt)
+ *                 with tile-centre differences formed exactly as float pairs,
+ *                 the self pair (j == i) is left out before any FP32 sum, each
+ *                 particle's per-tile partial sum is folded into a
+ *                 Kahan-compensated FP32 accumulator, and the cross-CTA
+ *                 reduction, the final scaling by G and the leapfrog run in
+ *                 FP64.  This is the paper's mixed-precision split (FP32
+ *                 forces, FP64 everything else, Sec. 3).
  *
  * Conventions for every entry point:
  *   * Array layout: positions, velocities and accelerations are
@@ -113,6 +117,12 @@ typedef struct nbody_config {
                                         block steps every k * dt_max of simulated time */
     int32_t flags;                   /* NBODY_FLAG_* */
     nbody_tiles tiles;               /* F32C tile shape; zeros = default or autotuned */
+    int64_t max_device_bytes;        /* cap on the device memory the context may hold (its
+                                        scratch, staging buffers, tuner and jerk/block-step
+                                        state); 0 = no cap.  An allocation that would pass
+                                        it is refused before cudaMalloc is called and fails
+                                        the call with NBODY_ENOMEM, exactly like a failed
+                                        cudaMalloc (sticky in the context) */
 } nbody_config;
 
 typedef struct nbody_ctx nbody_ctx;
@@ -159,9 +169,10 @@ int nbody_step(nbody_ctx *ctx, double *pos, double *vel, const double *mass, dou
  *     jerk_i = G sum_{j != i} m_j [ u / d2^(3/2) - 3 (r . u) r / d2^(5/2) ]
  *   pos, vel in : double[3][n]     mass in : double[n]
  *   acc, jerk out: double[3][n]    pot  out: double[n], or NULL
- * In NBODY_F32C mode velocities, like positions, are FP32 offsets from FP64
- * tile means; the call uses its own tile geometry (built on first use, shape
- * set by nbody_set_jerk_tiles or chosen from n).
+ * In NBODY_F32C mode velocities, like positions, are FP32 offsets from a
+ * per-tile centre (the FP32 mean of the tile's FP32-rounded values, low part
+ * 0); the call uses its own tile geometry (built on first use, shape set by
+ * nbody_set_jerk_tiles or chosen from n).
  */
 int nbody_forces_jerk(nbody_ctx *ctx, const double *pos, const double *vel, const double *mass,
                       double *acc, double *jerk, double *pot, void *stream);
@@ -267,19 +278,6 @@ int nbody_tiles_supported(nbody_tiles *out, int cap);
  * reset != 0 clears the totals afterwards.
  */
 int nbody_profile_read(nbody_ctx *ctx, double *ms_total, int64_t *launches, int reset);
-
-/*
- * Per-SM issue rates of this GPU behind the force kernel's roofline, measured
- * with one CTA of 1024 threads per SM and clock64() cycles (so they do not
- * depend on the clock frequency).  out (host, n_out >= 4):
- *   out[0] FP32 lane-operations per clock per SM with paired (f32x2) FMA
- *   out[1] MUFU rsqrt results per clock per SM
- *   out[2] pairwise interactions per clock per SM of the F32C kernel's per-pair
- *          arithmetic alone (register-resident operands, no shared-memory loads)
- *   out[3] FP64 FMA per clock per SM
- * Allocates and frees a small device buffer and synchronises the device.
- */
-int nbody_measure_pipes(double *out, int n_out);
 
 /* Number of kernels the library has launched on this context (eager and graph nodes). */
 int64_t nbody_kernel_launches(const nbody_ctx *ctx);

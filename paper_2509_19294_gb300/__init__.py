@@ -45,7 +45,7 @@ NBODY_FLAG_NO_GRAPH = 8
 EXPORTED = ("nbody_init", "nbody_destroy", "nbody_forces", "nbody_step", "nbody_energy",
             "nbody_tune", "nbody_get_tiles", "nbody_tiles_supported", "nbody_profile_read",
             "nbody_kernel_launches", "nbody_strerror", "nbody_last_error_message",
-            "nbody_forces_noalloc", "nbody_measure_pipes", "nbody_forces_jerk",
+            "nbody_forces_noalloc", "nbody_forces_jerk",
             "nbody_step_hermite", "nbody_get_jerk_tiles", "nbody_set_jerk_tiles",
             "nbody_block_start", "nbody_block_advance", "nbody_block_state")
 
@@ -60,7 +60,7 @@ class NBodyConfig(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("cluster_offsets", ctypes.POINTER(ctypes.c_int64)),
                 ("eps", ctypes.POINTER(ctypes.c_double)), ("G", ctypes.c_double),
                 ("reorder_every", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("tiles", NBodyTiles)]
+                ("tiles", NBodyTiles), ("max_device_bytes", ctypes.c_int64)]
 
 
 class NBodyError(RuntimeError):
@@ -127,8 +127,6 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.nbody_block_advance.restype = ctypes.c_int
         lib.nbody_block_state.argtypes = [vp, vp, vp, vp]
         lib.nbody_block_state.restype = ctypes.c_int
-        lib.nbody_measure_pipes.argtypes = [ctypes.POINTER(d), ctypes.c_int]
-        lib.nbody_measure_pipes.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -208,8 +206,10 @@ def _check(ctx, rc, where):
 
 
 def nbody_init(n_total: int, eps, mode: int = NBODY_F32C, G: float = 1.0, cluster_offsets=None,
-               reorder_every: int = 0, flags: int = 0, tiles=None, stream=None) -> Context:
-    """Create a context (see nbody_init in nbody.h).  eps: scalar or one per cluster."""
+               reorder_every: int = 0, flags: int = 0, tiles=None, max_device_bytes: int = 0,
+               stream=None) -> Context:
+    """Create a context (see nbody_init in nbody.h).  eps: scalar or one per cluster;
+    max_device_bytes: cap on the context's device memory (0 = none)."""
     lib = load()
     if cluster_offsets is None:
         offsets = np.array([0, n_total], np.int64)
@@ -226,6 +226,7 @@ def nbody_init(n_total: int, eps, mode: int = NBODY_F32C, G: float = 1.0, cluste
     cfg.G = float(G)
     cfg.reorder_every = int(reorder_every)
     cfg.flags = int(flags)
+    cfg.max_device_bytes = int(max_device_bytes)
     if tiles is not None:
         t = tuple(tiles) + (0,) * (5 - len(tiles))
         cfg.tiles = NBodyTiles(*[int(x) for x in t])
@@ -377,15 +378,6 @@ def nbody_profile_read(ctx: Context, reset: bool = False):
     rc = load().nbody_profile_read(ctx.handle, ctypes.byref(ms), ctypes.byref(cnt), int(reset))
     _check(ctx, rc, "nbody_profile_read")
     return ms.value, cnt.value
-
-
-def nbody_measure_pipes() -> dict:
-    """Measured per-SM-per-clock rates: FP32 f32x2 lanes, MUFU rsqrt, force-kernel
-    pair arithmetic (pairs), FP64 FMA (see nbody_measure_pipes in nbody.h)."""
-    out = (ctypes.c_double * 4)()
-    _check(None, load().nbody_measure_pipes(out, 4), "nbody_measure_pipes")
-    return {"fp32_lanes_per_clk_sm": out[0], "mufu_rsqrt_per_clk_sm": out[1],
-            "pair_arith_pairs_per_clk_sm": out[2], "fp64_fma_per_clk_sm": out[3]}
 
 
 def nbody_kernel_launches(ctx: Context) -> int:

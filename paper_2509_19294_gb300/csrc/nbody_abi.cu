@@ -11,8 +11,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <queue>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "nbody.h"
@@ -174,6 +176,10 @@ struct nbody_ctx {
     int64_t launches = 0;
     int sticky = NBODY_OK;
     std::string msg;
+
+    // device bytes held by the context and the cap on them (0 = none)
+    int64_t dev_bytes = 0;
+    int64_t cap_bytes = 0;
 };
 
 namespace {
@@ -197,25 +203,61 @@ int cuda_fail(nbody_ctx *c, cudaError_t e, const char *where) {
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);      \
     } while (0)
 
-template <class T>
-int dev_alloc(nbody_ctx *ctx, T **p, size_t count) {
-    if (*p) {
-        cudaFree(*p);
-        *p = nullptr;
-    }
-    size_t bytes = std::max<size_t>(count * sizeof(T), 256);
-    cudaError_t e = cudaMalloc((void **)p, bytes);
+// Ledger of the device allocations of every context (pointer -> owner, bytes),
+// so that frees made without the context at hand still update its total.
+std::mutex g_ledger_mutex;
+std::unordered_map<void *, std::pair<nbody_ctx *, size_t>> g_ledger;
+
+// cudaMalloc of `bytes` for ctx, refused with NBODY_ENOMEM (before any CUDA
+// call) when it would take the context past its allocation cap.
+int ctx_malloc(nbody_ctx *ctx, void **p, size_t bytes) {
+    *p = nullptr;
+    if (ctx && ctx->cap_bytes > 0 && ctx->dev_bytes + (int64_t)bytes > ctx->cap_bytes)
+        return fail(ctx, NBODY_ENOMEM,
+                    "allocation cap: " + std::to_string(bytes) + " more bytes would exceed the cap of " +
+                        std::to_string(ctx->cap_bytes) + " (" + std::to_string(ctx->dev_bytes) + " held)");
+    cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return fail(ctx, NBODY_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
     }
+    if (ctx) {
+        std::lock_guard<std::mutex> lock(g_ledger_mutex);
+        g_ledger[*p] = {ctx, bytes};
+        ctx->dev_bytes += (int64_t)bytes;
+    }
     return NBODY_OK;
+}
+
+void ctx_free(void *p) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lock(g_ledger_mutex);
+        auto it = g_ledger.find(p);
+        if (it != g_ledger.end()) {
+            it->second.first->dev_bytes -= (int64_t)it->second.second;
+            g_ledger.erase(it);
+        }
+    }
+    cudaFree(p);
+}
+
+template <class T>
+int dev_alloc(nbody_ctx *ctx, T **p, size_t count) {
+    if (*p) {
+        ctx_free(*p);
+        *p = nullptr;
+    }
+    void *q = nullptr;
+    const int rc = ctx_malloc(ctx, &q, std::max<size_t>(count * sizeof(T), 256));
+    *p = static_cast<T *>(q);
+    return rc;
 }
 
 template <class T>
 void dev_free(T **p) {
-    if (*p) cudaFree(*p);
+    ctx_free(*p);
     *p = nullptr;
 }
 
@@ -480,13 +522,10 @@ int resolve(nbody_ctx *ctx, const void *user, size_t bytes, DevBuf &st, bool cop
         return NBODY_OK;
     }
     if (st.bytes < bytes) {
-        if (st.p) cudaFree(st.p);
+        ctx_free(st.p);
         st.p = nullptr;
         st.bytes = 0;
-        if (cudaMalloc(&st.p, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ctx, NBODY_ENOMEM, "staging allocation failed");
-        }
+        if (int rc = ctx_malloc(ctx, &st.p, bytes)) return rc;
         st.bytes = bytes;
         drop_graphs(ctx);
     }
@@ -1122,7 +1161,7 @@ int run_tuner(nbody_ctx *ctx, cudaStream_t s) {
     for (int k = 0; k < ctx->ncl; ++k) total_pairs += (double)cluster_n(ctx, k) * cluster_n(ctx, k);
     const double jfrac = std::min(1.0, 1.0e11 / std::max(total_pairs, 1.0));
     double *acc = nullptr;
-    NB_CUDA(cudaMalloc(&acc, (size_t)ctx->n * 4 * sizeof(double)));
+    if (int rc0 = dev_alloc(ctx, &acc, (size_t)ctx->n * 4)) return rc0;
     cudaEvent_t e0, e1;
     NB_CUDA(cudaEventCreate(&e0));
     NB_CUDA(cudaEventCreate(&e1));
@@ -1162,7 +1201,7 @@ int run_tuner(nbody_ctx *ctx, cudaStream_t s) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(acc);
+    dev_free(&acc);
     if (rc) return rc;
     if (best.block == 0) return fail(ctx, NBODY_EUNSUPPORTED, "autotuner found no usable shape");
     if ((rc = build_f32c(ctx, best))) return rc;
@@ -1221,7 +1260,7 @@ void nbody_destroy(nbody_ctx *ctx) {
     dev_free(&ctx->vals);
     for (DevBuf *b : {&ctx->st_pos, &ctx->st_vel, &ctx->st_mass, &ctx->st_acc, &ctx->st_pot,
                       &ctx->st_diag, &ctx->st_jerk})
-        if (b->p) cudaFree(b->p);
+        ctx_free(b->p);
     for (int s = 0; s < kProfSlots; ++s)
         for (int k = 0; k < 2; ++k)
             if (ctx->ev[s][k]) cudaEventDestroy(ctx->ev[s][k]);
@@ -1237,6 +1276,7 @@ int nbody_init(nbody_ctx **out, const nbody_config *cfg, void *stream) {
     if (cfg->n_clusters < 1 || cfg->n_clusters > (1 << 24)) return NBODY_EINVAL;
     if (cfg->mode != NBODY_F64 && cfg->mode != NBODY_F32C) return NBODY_EINVAL;
     if (!cfg->eps || !std::isfinite(cfg->G) || cfg->reorder_every < 0) return NBODY_EINVAL;
+    if (cfg->max_device_bytes < 0) return NBODY_EINVAL;
     if (cfg->n_clusters > 1 && !cfg->cluster_offsets) return NBODY_EINVAL;
     nbody_ctx *ctx = new nbody_ctx();
     ctx->n = cfg->n_total;
@@ -1245,6 +1285,7 @@ int nbody_init(nbody_ctx **out, const nbody_config *cfg, void *stream) {
     ctx->G = cfg->G;
     ctx->reorder_every = cfg->reorder_every;
     ctx->flags = cfg->flags;
+    ctx->cap_bytes = cfg->max_device_bytes;
     ctx->off.assign(cfg->n_clusters + 1, 0);
     if (cfg->cluster_offsets) {
         for (int k = 0; k <= cfg->n_clusters; ++k) ctx->off[k] = cfg->cluster_offsets[k];

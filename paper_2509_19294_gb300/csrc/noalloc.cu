@@ -34,7 +34,10 @@ constexpr int kTC = kBlock * kP;
 constexpr int64_t kMaxN = NBODY_NOALLOC_MAX_N;
 constexpr int kMaxTiles = (int)((kMaxN + kTC - 1) / kTC);
 constexpr int kMaxSplit = 8;
-constexpr int kSplitBudget = 608;  // items aimed at: 4 resident CTAs x 152 SMs
+// Most work items the split may create: the scratch holds this many split
+// partial slots (4 resident CTAs x 152 SMs of a GB300).  Per call the split
+// aims at min(kSplitBudget, resident CTAs of this GPU) items.
+constexpr int kSplitBudget = 608;
 
 // Byte layout of the scratch (every region 256-byte aligned).
 constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -121,6 +124,7 @@ extern "C" int nbody_forces_noalloc(int64_t n, const double *pos, const double *
     if (!pos || !mass || !acc) return NBODY_EINVAL;
     if (!on_device(pos) || !on_device(mass) || !on_device(acc) || (pot && !on_device(pot)))
         return NBODY_EINVAL;
+    cudaGetLastError();  // an error left pending by earlier, unrelated work is not ours
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
@@ -153,13 +157,19 @@ extern "C" int nbody_forces_noalloc(int64_t n, const double *pos, const double *
     const bool eps_zero = eps2f == 0.0f;
     const int n_tiles = (int)((n + kTC - 1) / kTC);
     const int n_jt = (int)((n + kTJ - 1) / kTJ);
-    int split = kSplitBudget / n_tiles;
+    const int occ = f32c_occupancy(kBlock, kP, kTJ, kMinB, eps_zero);
+    if (occ <= 0) return NBODY_EUNSUPPORTED;
+    const int budget = occ * sms < kSplitBudget ? occ * sms : kSplitBudget;
+    int split = budget / n_tiles;
     if (split > kMaxSplit) split = kMaxSplit;
     if (split > n_jt) split = n_jt;
     if (split < 1) split = 1;
 
     noalloc_setup_kernel<<<64, 256, 0, s>>>(base, (int)n, n_tiles, split, eps2f, eps * eps);
-    if (cudaGetLastError() != cudaSuccess) return NBODY_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) {
+        cudaGetLastError();
+        return NBODY_ECUDA;
+    }
 
     PackParams pp{};
     pp.pos = pos;
@@ -174,7 +184,10 @@ extern "C" int nbody_forces_noalloc(int64_t n, const double *pos, const double *
     pp.pz = reinterpret_cast<float *>(base + kOffPz);
     pp.pm = reinterpret_cast<float *>(base + kOffPm);
     pp.chl = reinterpret_cast<float4 *>(base + kOffChl);
-    if (launch_pack(n_tiles, pp, s) != cudaSuccess) return NBODY_ECUDA;
+    if (launch_pack(n_tiles, pp, s) != cudaSuccess) {
+        cudaGetLastError();
+        return NBODY_ECUDA;
+    }
 
     F32CParams fp{};
     fp.px = pp.px;
@@ -195,8 +208,6 @@ extern "C" int nbody_forces_noalloc(int64_t n, const double *pos, const double *
     fp.n = n;
     fp.G = G;
     fp.half_dt = 0.0;
-    const int occ = f32c_occupancy(kBlock, kP, kTJ, kMinB, eps_zero);
-    if (occ <= 0) return NBODY_EUNSUPPORTED;
     int grid = occ * sms;
     if (grid > fp.n_items) grid = fp.n_items;
     if (launch_f32c(kBlock, kP, kTJ, kMinB, eps_zero, grid, fp, s) != cudaSuccess) {

@@ -1,4 +1,6 @@
-// peaks.cu -- per-SM issue-rate probes behind the force kernel's roofline.
+// pipe_rates.cu -- per-SM issue-rate probes behind the force kernel's roofline
+// (libnbody_probe.so, a measurement library for the benchmark; not part of the
+// force library's ABI).
 //
 // The roofline of the F32C force kernel is set by the FP32 pipe (13 FP32
 // operations per pair) and the MUFU rsqrt unit (1 per pair).  These probes run
@@ -15,7 +17,7 @@
 #include <stdint.h>
 
 #include "forces_f32c.cuh"
-#include "nbody.h"
+#include "pipe_rates.h"
 
 namespace nbody {
 namespace {
@@ -101,10 +103,11 @@ __global__ void __launch_bounds__(kProbeThreads) pair_probe(int iters, float *si
     float2 xj = make_float2(0.1f, 0.2f), yj = make_float2(-0.3f, 0.4f);
     float2 zj = make_float2(0.5f, -0.6f), mj = make_float2(1e-3f, 2e-3f);
     const float2 dj = make_float2(1e-4f, -1e-4f);
+    const int dself[kPairP] = {-1, -1, -1, -1};  // no self pair among the probe's j's
     __syncthreads();
     const long long t0 = clock64();
     for (int i = 0; i < iters; ++i) {
-        PairK::body(xj, yj, zj, mj, e2, nx, ny, nz, ax, ay, az, ph);
+        PairK::body<false>(xj, yj, zj, mj, e2, nx, ny, nz, ax, ay, az, ph, dself, 0);
         // every j operand changes each iteration, so nothing can be hoisted;
         // these 4 paired adds per 2 * kPairP pairs make the figure a lower bound
         xj = __fadd2_rn(xj, dj);
@@ -126,12 +129,12 @@ __global__ void __launch_bounds__(kProbeThreads) pair_probe(int iters, float *si
 
 extern "C" int nbody_measure_pipes(double *out, int n_out) {
     using namespace nbody;
-    if (!out || n_out < 4) return NBODY_EINVAL;
+    if (!out || n_out < 4) return NBODY_PROBE_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
-        return NBODY_ECUDA;
+        return NBODY_PROBE_ECUDA;
     }
     float *sink = nullptr;
     long long *cyc = nullptr;
@@ -139,13 +142,13 @@ extern "C" int nbody_measure_pipes(double *out, int n_out) {
         cudaMalloc(&cyc, sizeof(long long) * sms) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(sink);
-        return NBODY_ENOMEM;
+        return NBODY_PROBE_ENOMEM;
     }
     const int iters = 4096;
     long long *hc = new long long[sms];
     double rate[4];
-    int rc = NBODY_OK;
-    for (int probe = 0; probe < 4 && rc == NBODY_OK; ++probe) {
+    int rc = 0;
+    for (int probe = 0; probe < 4 && rc == 0; ++probe) {
         for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
             switch (probe) {
                 case 0: ffma2_probe<<<sms, kProbeThreads>>>(iters, sink, cyc); break;
@@ -157,7 +160,7 @@ extern "C" int nbody_measure_pipes(double *out, int n_out) {
         if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
             cudaMemcpy(hc, cyc, sizeof(long long) * sms, cudaMemcpyDeviceToHost) != cudaSuccess) {
             cudaGetLastError();
-            rc = NBODY_ECUDA;
+            rc = NBODY_PROBE_ECUDA;
             break;
         }
         double mean = 0.0;
@@ -174,7 +177,7 @@ extern "C" int nbody_measure_pipes(double *out, int n_out) {
     delete[] hc;
     cudaFree(sink);
     cudaFree(cyc);
-    if (rc == NBODY_OK)
+    if (rc == 0)
         for (int k = 0; k < 4; ++k) out[k] = rate[k];
     return rc;
 }

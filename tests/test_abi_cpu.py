@@ -42,6 +42,19 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(names) == set(nb.EXPORTED)
 
 
+def test_probe_library_is_separate_from_the_force_library(lib):
+    # the benchmark's pipe-rate probe lives in libnbody_probe.so with its own
+    # header; the force library's ABI does not carry it
+    from paper_2509_19294_gb300 import probe
+    plib = probe.load()
+    assert hasattr(plib, "nbody_measure_pipes")
+    text = open(os.path.join(ROOT, "paper_2509_19294_gb300", "probe", "pipe_rates.h")).read()
+    assert "int nbody_measure_pipes(double *out, int n_out);" in text
+    assert "nbody_measure_pipes" not in _header_functions()
+    with pytest.raises(AttributeError):
+        getattr(lib, "nbody_measure_pipes")
+
+
 def test_status_strings(lib):
     assert nb.nbody_strerror(0) == "success"
     assert "invalid" in nb.nbody_strerror(nb.NBODY_EINVAL)

@@ -6,11 +6,14 @@ latency, plug-ins in a process that has reserved the GPU's memory.  For them the
 library offers nbody_forces_noalloc, which keeps its scratch in a fixed array
 compiled into libnbody.so instead of a context allocated by nbody_init.
 
-These tests call it through the C ABI twice in a row with different inputs and
-check each result against nbody_forces on a context, with the FP32C tolerance
-the parity tests use (per-particle relative acceleration error: median <= 1e-6,
-max <= 1e-4; potential likewise).  The file is named so that pytest collects it
-last; it passes alone in a fresh process and after the other tests.
+These tests call it through the C ABI and check every output element against
+the FP64 oracle with the FP32C tolerance of the parity tests (per-particle
+relative acceleration error: median <= 1e-6, max <= 1e-4; potential likewise):
+two calls in a row with different inputs (the second proves that the shared
+scratch is re-initialised), eps = 0 with coincident particles, a size whose
+split count is 2, and the largest size the scratch holds (split 1, every tile
+of the array in use; sampled rows).  The file is named so that pytest collects
+it last; it passes alone in a fresh process and after the other tests.
 """
 import numpy as np
 import pytest
@@ -35,43 +38,68 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
 
 
-def _context_forces(pos, mass, eps, G):
-    n = mass.shape[0]
-    with nb.nbody_init(n, eps, G=G, mode=nb.NBODY_F32C) as ctx:
-        acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
-        pot = torch.empty(n, dtype=torch.float64, device="cuda")
-        nb.nbody_forces(ctx, _dev(pos), _dev(mass), acc, pot)
-        torch.cuda.synchronize()
-        return acc.cpu().numpy(), pot.cpu().numpy()
-
-
 def _assert_close(a, p, ra, rp):
     s = metrics.summary(a, ra, p, rp)
     assert s["median"] <= 1e-6 and s["max"] <= 1e-4, s
     assert s["pot_median"] <= 1e-6 and s["pot_max"] <= 1e-4, s
+    return s
 
 
-def test_two_calls_in_a_row_match_the_context_path():
+def _call(lib, pos, mass, eps, G, stream):
+    n = mass.shape[0]
+    p, m = _dev(pos), _dev(mass)
+    acc = torch.full((3, n), float("nan"), dtype=torch.float64, device="cuda")
+    pot = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    rc = lib.nbody_forces_noalloc(n, p.data_ptr(), m.data_ptr(), eps, G, acc.data_ptr(),
+                                  pot.data_ptr(), stream)
+    assert rc == nb.NBODY_OK, nb.nbody_strerror(rc)
+    return p, m, acc, pot                  # the inputs stay alive until the sync
+
+
+def test_two_calls_in_a_row_match_the_oracle(oracle):
     lib = nb.load()
     stream = torch.cuda.current_stream().cuda_stream
     cases = [
         (ic.plummer(30001, seed=21)[::2], 0.002, 1.0),
         (ic.uniform_sphere(20000, seed=22, masses=ic.log_uniform_masses(20000, 23))[::2], 0.0, 0.7),
     ]
-    outs = []
-    for (pos, mass), eps, G in cases:
-        n = mass.shape[0]
-        p, m = _dev(pos), _dev(mass)
-        acc = torch.full((3, n), float("nan"), dtype=torch.float64, device="cuda")
-        pot = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
-        rc = lib.nbody_forces_noalloc(n, p.data_ptr(), m.data_ptr(), eps, G, acc.data_ptr(),
-                                      pot.data_ptr(), stream)
-        assert rc == nb.NBODY_OK, nb.nbody_strerror(rc)
-        outs.append((p, m, acc, pot))          # keep the inputs alive until the sync
+    outs = [_call(lib, pos, mass, eps, G, stream) for (pos, mass), eps, G in cases]
     torch.cuda.synchronize()
     for ((pos, mass), eps, G), (_, _, acc, pot) in zip(cases, outs):
-        ra, rp = _context_forces(pos, mass, eps, G)
+        ra, rp = oracle.forces(pos, mass, eps, G)
         _assert_close(acc.cpu().numpy(), pot.cpu().numpy(), ra, rp)
+
+
+def test_eps_zero_coincident_particles_match_the_oracle(oracle):
+    # with eps = 0 a coincident distinct pair contributes nothing (the oracle
+    # skips r = 0 too); every 97th particle is duplicated onto its neighbour
+    lib = nb.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    pos, _, mass = ic.plummer(5000, seed=25)
+    pos = pos.copy()
+    pos[:, 1::97] = pos[:, 0:-1:97][:, :pos[:, 1::97].shape[1]]
+    _, _, acc, pot = _call(lib, pos, mass, 0.0, 1.0, stream)
+    torch.cuda.synchronize()
+    a, p = acc.cpu().numpy(), pot.cpu().numpy()
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(p))
+    ra, rp = oracle.forces(pos, mass, 0.0)
+    _assert_close(a, p, ra, rp)
+
+
+@pytest.mark.parametrize("n", [60000, nb.NBODY_NOALLOC_MAX_N])
+def test_split_two_and_full_scratch_sampled_rows(oracle, n):
+    # n = 60000: 235 tiles of 256, split 2; n = NBODY_NOALLOC_MAX_N: 1024 tiles,
+    # split 1, the queue, counters and packed arrays fill the fixed scratch
+    lib = nb.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    pos, _, mass = ic.plummer(n, seed=26)
+    _, _, acc, pot = _call(lib, pos, mass, 1e-3, 1.0, stream)
+    torch.cuda.synchronize()
+    a, p = acc.cpu().numpy(), pot.cpu().numpy()
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(p))
+    rows = np.unique(np.concatenate([ic.sample_rows(n, 1024, 27), [0, n - 1]]))
+    ra, rp = oracle.forces_rows(pos, mass, 1e-3, rows)
+    _assert_close(a[:, rows], p[rows], ra, rp)
 
 
 def test_rejects_oversize_and_host_arrays():
