@@ -352,22 +352,26 @@ def run_ours(args):
                              f"(FP64, {secs:.1f} s on {thr} threads)",
                    "full_evaluations": time_oracle_configs(), "host": host_cpu()}
 
-    # plain FP64 GPU kernel on the same GPU: one evaluation of a bounded sample
+    # plain FP64 GPU kernel on the same GPU and the same state: one full
+    # evaluation of the timed workload (N = 1M: about 48 s), and the F32C
+    # result of that state against it on every row
     fp64 = None
     if rank == 0 and not args.no_fp64:
-        n64 = args.fp64_n
-        from paper_2509_19294_gb300 import ic
-        p64, _, m64 = ic.two_plummer(n64 // 2, seed=SEED)
-        with nb.nbody_init(n64, EPS, mode=nb.NBODY_F64, flags=nb.NBODY_FLAG_PROFILE) as c64:
-            pp, mm = torch.from_numpy(p64).cuda(), torch.from_numpy(m64).cuda()
-            aa = torch.empty((3, n64), dtype=torch.float64, device="cuda")
-            nb.nbody_forces(c64, pp, mm, aa)
-            nb.nbody_profile_read(c64, reset=True)
-            nb.nbody_forces(c64, pp, mm, aa)
-            ms64, _ = nb.nbody_profile_read(c64, reset=True)
-        fp64 = {"value": float(n64) * n64 / (ms64 / 1e3), "unit": UNIT,
-                "sample": f"one FP64 evaluation, same workload recipe at N={n64}",
-                "ratio_f32c_over_f64": None}
+        fp64 = fp64_comparison(nb, torch, p, m, ah, poth, args.fp64_n)
+
+    # |dE/E| drift of the FP32C path against the FP64 GPU path over the same
+    # steps: C4 (512 clusters, 100 steps, per cluster) and C3 (N = 131072,
+    # 1000 steps; about 12 minutes of FP64 work)
+    drift = None
+    if rank == 0 and world == 1 and not args.no_drift:
+        drift = {"c4": c4_drift(nb, torch)}
+        if not args.no_c3_drift:
+            drift["c3"] = c3_drift(nb, torch, args.c3_steps)
+
+    # F32C force evaluations across the workloads' sizes (autotuned tiles)
+    sweep = None
+    if rank == 0 and world == 1 and not args.no_sweep:
+        sweep = force_sweep(nb, torch)
 
     # batched ensemble: 512 independent Plummer clusters, one persistent launch per step
     ensemble = None
@@ -518,8 +522,9 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     try:
-        rates = nb.nbody_measure_pipes()
-    except nb.NBodyError:
+        from paper_2509_19294_gb300 import probe
+        rates = probe.measure_pipes()
+    except RuntimeError:
         rates = None
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -548,6 +553,10 @@ def run_ours(args):
                                            / (FP32_LANES_PER_SM / FP32_OPS_PER_PAIR))
     if fp64 is not None:
         fp64["ratio_f32c_over_f64"] = value / fp64["value"]
+    if sweep is not None:
+        for rec in sweep:
+            rec["roofline_frac"] = rec["kernel_interactions_per_s"] / 1e9 / peak
+            rec["call_roofline_frac"] = rec["call_interactions_per_s"] / 1e9 / peak
     # energy to solution (the paper's second metric): GPU board power sampled by
     # nvidia-smi every 200 ms during the timed steps, times the timed wall time
     energy = None
@@ -589,6 +598,8 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "fp64_gpu": fp64,
+        "drift": drift,
+        "sweep": sweep,
         "ensemble": ensemble,
         "paper_scale": paper_scale,
         "block_steps": block,
@@ -600,6 +611,148 @@ def run_ours(args):
     print(json.dumps(out), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------- comparisons
+
+def fp64_comparison(nb, torch, p, m, a32, p32, n64=0):
+    """The plain FP64 GPU kernel on the timed workload's state (all N rows; n64 > 0
+    evaluates only the first n64 particles as their own system instead), its
+    interactions/s, and the F32C acceleration/potential of that state (a32, p32,
+    host arrays) against it row by row."""
+    n = int(m.shape[0]) if not n64 else int(n64)
+    pp = p if not n64 else p[:, :n].contiguous()
+    mm = m if not n64 else m[:n].contiguous()
+    with nb.nbody_init(n, EPS, mode=nb.NBODY_F64, flags=nb.NBODY_FLAG_PROFILE) as c64:
+        aa = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        po = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_profile_read(c64, reset=True)
+        nb.nbody_forces(c64, pp, mm, aa, po)
+        ms64, _ = nb.nbody_profile_read(c64, reset=True)
+        a64, q64 = aa.cpu().numpy(), po.cpu().numpy()
+    out = {"value": float(n) * n / (ms64 / 1e3), "unit": UNIT, "kernel_ms": ms64,
+           "sample": f"one full FP64 evaluation of the timed workload's state, N={n}",
+           "ratio_f32c_over_f64": None}
+    if not n64:
+        rel = np.linalg.norm(a32 - a64, axis=0) / np.linalg.norm(a64, axis=0)
+        typical = math.sqrt(float(np.mean(np.sum(a64 ** 2, axis=0))))
+        prel = np.abs(p32 - q64) / np.abs(q64)
+        out["f32c_vs_f64_all_rows"] = {
+            "rows": n, "median_rel_acc_err": float(np.median(rel)), "max_rel_acc_err": float(rel.max()),
+            "paper_metric_component_over_own_norm": float(
+                (np.abs(a32 - a64).max(axis=0) / np.linalg.norm(a64, axis=0)).max()),
+            "paper_metric_component_over_rms": float(np.abs(a32 - a64).max() / typical),
+            "median_rel_pot_err": float(np.median(prel)), "max_rel_pot_err": float(prel.max())}
+    return out
+
+
+def _run_with_diag(nb, torch, pos, vel, mass, eps, dt, nsteps, mode, offsets=None, reorder=10):
+    """Energies of every cluster at t = 0 and after each of nsteps graph-replayed
+    KDK steps ([nsteps + 1, clusters, 9]) and the device seconds of the steps."""
+    n = mass.shape[0]
+    with nb.nbody_init(n, eps, mode=mode, cluster_offsets=offsets, reorder_every=reorder) as ctx:
+        pt, vt, mt = (torch.from_numpy(x.copy()).cuda() for x in (pos, vel, mass))
+        acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        pot = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_forces(ctx, pt, mt, acc, pot)
+        e0 = nb.nbody_energy(ctx, pt, vt, mt, pot)
+        d = torch.empty((nsteps, ctx.n_clusters, 9), dtype=torch.float64, device="cuda")
+        stream = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        nb.nbody_step(ctx, pt, vt, mt, acc, pot, dt, nsteps, d)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return np.concatenate([e0[None], d.cpu().numpy()]), ev0.elapsed_time(ev1) / 1e3
+
+
+def _drift(e):
+    """max over steps of |E(t) - E(0)| / |E(0)| per cluster, E with each path's own phi."""
+    return np.abs(e[:, :, 2] - e[0, :, 2]).max(axis=0) / np.abs(e[0, :, 2])
+
+
+def c4_drift(nb, torch):
+    from paper_2509_19294_gb300 import ic
+    ens = ic.ensemble(512, seed=4)
+    res = {}
+    for name, mode in (("f32c", nb.NBODY_F32C), ("f64", nb.NBODY_F64)):
+        e, sec = _run_with_diag(nb, torch, ens.pos, ens.vel, ens.mass, ens.eps, 1e-3, 100, mode,
+                                offsets=ens.offsets)
+        res[name] = (_drift(e), sec, np.abs(e[:, :, 3:6] - e[0, :, 3:6]).max(axis=(0, 2)))
+    ratio = res["f32c"][0] / res["f64"][0]
+    worst = int(np.argmax(ratio))
+    return {"workload": "C4 ensemble, 512 clusters (seed 4), 100 KDK steps dt=1e-3, both paths "
+                        "from the same initial state, E with each path's own potential",
+            "per_cluster_ratio": {"max": float(ratio.max()), "median": float(np.median(ratio)),
+                                  "clusters_above_2": int((ratio > 2).sum())},
+            "worst_cluster": {"cluster": worst, "n_c": int(ens.sizes[worst]),
+                              "f32c": float(res["f32c"][0][worst]), "f64": float(res["f64"][0][worst])},
+            "f32c_max_abs_dE_over_E": float(res["f32c"][0].max()),
+            "f64_max_abs_dE_over_E": float(res["f64"][0].max()),
+            "f64_median_abs_dE_over_E": float(np.median(res["f64"][0])),
+            "max_abs_dP": {"f32c": float(res["f32c"][2].max()), "f64": float(res["f64"][2].max())},
+            "seconds": {"f32c": res["f32c"][1], "f64": res["f64"][1]}}
+
+
+def c3_drift(nb, torch, nsteps=1000):
+    from paper_2509_19294_gb300 import ic
+    pos, vel, mass = ic.plummer(131072, seed=3)
+    res = {}
+    for name, mode in (("f32c", nb.NBODY_F32C), ("f64", nb.NBODY_F64)):
+        e, sec = _run_with_diag(nb, torch, pos, vel, mass, 1e-3, 1e-4, nsteps, mode)
+        res[name] = {"max_abs_dE_over_E": float(_drift(e)[0]),
+                     "max_abs_dP": float(np.abs(e[:, 0, 3:6] - e[0, 0, 3:6]).max()),
+                     "max_abs_dL": float(np.abs(e[:, 0, 6:9] - e[0, 0, 6:9]).max()),
+                     "seconds": sec}
+    return {"workload": f"C3 Plummer N=131072 (seed 3), eps=1e-3, {nsteps} graph-replayed KDK steps "
+                        "dt=1e-4, Morton re-sort every 10, both paths from the same initial state, "
+                        "E with each path's own potential",
+            "steps": nsteps, "f32c": res["f32c"], "f64": res["f64"],
+            "ratio_f32c_over_f64": res["f32c"]["max_abs_dE_over_E"] / res["f64"]["max_abs_dE_over_E"]}
+
+
+def force_sweep(nb, torch):
+    """nbody_forces (F32C, autotuned tiles) at the workloads' sizes: kernel-only
+    and whole-call (pack + queue reset + force kernel) interactions/s."""
+    from paper_2509_19294_gb300 import ic
+    cases = [("C1 Plummer N=1024, eps=0.01", lambda: ic.plummer(1024, seed=1), 0.01),
+             ("C2 uniform sphere N=16384, log-uniform masses, eps=0.005",
+              lambda: ic.uniform_sphere(16384, seed=2, masses=ic.log_uniform_masses(16384, seed=2)), 0.005),
+             ("C2 Plummer N=16384, log-uniform masses, eps=0.005",
+              lambda: ic.plummer(16384, seed=2, masses=ic.log_uniform_masses(16384, seed=2)), 0.005),
+             ("C3 Plummer N=131072, eps=1e-3", lambda: ic.plummer(131072, seed=3), 1e-3),
+             ("C5 two Plummer spheres N=1048576, eps=1e-3", lambda: ic.two_plummer(N_EACH, seed=SEED), 1e-3)]
+    out = []
+    stream = torch.cuda.current_stream()
+    for name, make, eps in cases:
+        pos, _, mass = make()
+        n = mass.shape[0]
+        reps = int(min(200, max(3, 2e12 / (float(n) * n))))
+        with nb.nbody_init(n, eps, flags=nb.NBODY_FLAG_PROFILE | nb.NBODY_FLAG_AUTOTUNE) as ctx:
+            pt, mt = torch.from_numpy(pos).cuda(), torch.from_numpy(mass).cuda()
+            acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+            pot = torch.empty(n, dtype=torch.float64, device="cuda")
+            for _ in range(3):
+                nb.nbody_forces(ctx, pt, mt, acc, pot)
+            torch.cuda.synchronize()
+            nb.nbody_profile_read(ctx, reset=True)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(reps):
+                nb.nbody_forces(ctx, pt, mt, acc, pot)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            call_s = ev0.elapsed_time(ev1) / 1e3 / reps
+            kms, kn = nb.nbody_profile_read(ctx, reset=True)
+            t = nb.nbody_get_tiles(ctx)
+        kern_s = kms / max(kn, 1) / 1e3
+        out.append({"workload": name, "n": int(n), "evaluations": reps,
+                    "kernel_ms": kern_s * 1e3, "call_ms": call_s * 1e3,
+                    "kernel_interactions_per_s": float(n) * n / kern_s,
+                    "call_interactions_per_s": float(n) * n / call_s,
+                    "tiles": {"block": t[0], "p": t[1], "tj": t[2], "split": t[3], "ctas_per_sm": t[4]},
+                    "l2": "inputs resident (j-set 16 B/particle); no flush between evaluations"})
+    return out
 
 
 # ----------------------------------------------------------------- reference arm
@@ -699,6 +852,106 @@ def run_block_drift(n, t_end):
         "final_position_difference": {"median": float(np.median(dx)), "max": float(dx.max())}}}))
 
 
+def run_c5_drift(nsteps):
+    """C5 over nsteps KDK steps, F32C against the plain FP64 GPU path from the
+    same initial state: |dE/E| (each path's own potential), |dP|, and the final
+    positions' difference.  Prints one JSON line (10 steps take ~9 minutes of
+    FP64 work)."""
+    import torch
+    import paper_2509_19294_gb300 as nb
+    from paper_2509_19294_gb300 import build as nbuild
+    if not nbuild.up_to_date():
+        nbuild.build()
+    pos, vel, mass = workload()
+    n = mass.shape[0]
+    res = {}
+    for name, mode in (("f32c", nb.NBODY_F32C), ("f64", nb.NBODY_F64)):
+        with nb.nbody_init(n, EPS, mode=mode, reorder_every=1) as ctx:
+            p_, v_, m_ = (torch.from_numpy(x.copy()).cuda() for x in (pos, vel, mass))
+            a_ = torch.empty((3, n), dtype=torch.float64, device="cuda")
+            po_ = torch.empty(n, dtype=torch.float64, device="cuda")
+            t0 = time.perf_counter()
+            nb.nbody_forces(ctx, p_, m_, a_, po_)
+            e0 = nb.nbody_energy(ctx, p_, v_, m_, po_)
+            d = torch.empty((nsteps, 1, 9), dtype=torch.float64, device="cuda")
+            nb.nbody_step(ctx, p_, v_, m_, a_, po_, DT, nsteps, d)
+            e = np.concatenate([e0[None], d.cpu().numpy()])[:, 0]
+            res[name] = {"max_abs_dE_over_E": float(np.abs(e[:, 2] - e[0, 2]).max() / abs(e[0, 2])),
+                         "max_abs_dP": float(np.abs(e[:, 3:6] - e[0, 3:6]).max()),
+                         "E": e[:, 2].tolist(), "seconds": time.perf_counter() - t0,
+                         "pos": p_.cpu().numpy()}
+    dx = np.abs(res["f32c"].pop("pos") - res["f64"].pop("pos")).max(axis=0)
+    e32, e64 = np.array(res["f32c"]["E"]), np.array(res["f64"]["E"])
+    print(json.dumps({"c5_drift": {
+        "workload": f"{workload_name(n)}; {nsteps} KDK steps, both paths from the same initial state",
+        "f32c": res["f32c"], "f64": res["f64"],
+        "ratio_f32c_over_f64": res["f32c"]["max_abs_dE_over_E"] / res["f64"]["max_abs_dE_over_E"],
+        "max_abs_E_f32c_minus_E_f64_over_E": float(np.abs(e32 - e64).max() / abs(e64[0])),
+        "final_position_difference": {"median": float(np.median(dx)), "max": float(dx.max())}}}))
+
+
+def ablation_child(lib):
+    """One library's accuracy at C5 (1024 sampled rows against the FP64 oracle)
+    and at C3 (every row of one evaluation, and 10 KDK steps, against the FP64
+    GPU path); prints one JSON line."""
+    import torch
+    import oracle
+    import paper_2509_19294_gb300 as nb
+    from paper_2509_19294_gb300 import ic
+    nb.load(lib)
+    out = {"library": os.path.basename(lib)}
+    pos, _, mass = workload()
+    n = mass.shape[0]
+    tiles = (128, 2, 256, 4, 4)     # one shape and split for both libraries
+    with nb.nbody_init(n, EPS, tiles=tiles) as ctx:
+        acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        pot = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_forces(ctx, torch.from_numpy(pos).cuda(), torch.from_numpy(mass).cuda(), acc, pot)
+        a, q = acc.cpu().numpy(), pot.cpu().numpy()
+    rows = ic.sample_rows(n, 1024, 77)
+    ra, rp = oracle.forces_rows(pos, mass, EPS, rows)
+    rel = np.linalg.norm(a[:, rows] - ra, axis=0) / np.linalg.norm(ra, axis=0)
+    prel = np.abs(q[rows] - rp) / np.abs(rp)
+    out["c5_rows_vs_oracle"] = {"rows": len(rows), "median_rel_acc_err": float(np.median(rel)),
+                                "max_rel_acc_err": float(rel.max()), "median_rel_pot_err": float(np.median(prel)),
+                                "max_rel_pot_err": float(prel.max()), "tiles": list(tiles)}
+    cpos, cvel, cmass = ic.plummer(131072, seed=3)
+    evals, tracks = {}, {}
+    for name, mode in (("f32c", nb.NBODY_F32C), ("f64", nb.NBODY_F64)):
+        e, _ = _run_with_diag(nb, torch, cpos, cvel, cmass, 1e-3, 1e-4, 10, mode)
+        tracks[name] = e[:, 0]
+        with nb.nbody_init(131072, 1e-3, mode=mode) as ctx:
+            acc = torch.empty((3, 131072), dtype=torch.float64, device="cuda")
+            pot = torch.empty(131072, dtype=torch.float64, device="cuda")
+            nb.nbody_forces(ctx, torch.from_numpy(cpos).cuda(), torch.from_numpy(cmass).cuda(), acc, pot)
+            evals[name] = (acc.cpu().numpy(), pot.cpu().numpy())
+    (a32, p32), (a64, p64) = evals["f32c"], evals["f64"]
+    rel = np.linalg.norm(a32 - a64, axis=0) / np.linalg.norm(a64, axis=0)
+    prel = np.abs(p32 - p64) / np.abs(p64)
+    e32, e64 = tracks["f32c"], tracks["f64"]
+    out["c3_all_rows_vs_fp64"] = {"median_rel_acc_err": float(np.median(rel)), "max_rel_acc_err": float(rel.max()),
+                                  "median_rel_pot_err": float(np.median(prel)), "max_rel_pot_err": float(prel.max())}
+    out["c3_10_steps"] = {"f32c_max_abs_dE_over_E": float(np.abs(e32[:, 2] - e32[0, 2]).max() / abs(e32[0, 2])),
+                          "f64_max_abs_dE_over_E": float(np.abs(e64[:, 2] - e64[0, 2]).max() / abs(e64[0, 2])),
+                          "max_abs_E_f32c_minus_E_f64_over_E": float(np.abs(e32[:, 2] - e64[:, 2]).max() / abs(e64[0, 2]))}
+    print(json.dumps(out), flush=True)
+
+
+def run_tile_sum_ablation():
+    """Accuracy with and without the cross-tile Kahan compensation of the F32C
+    kernels (the ablation library is built on request only); one JSON line."""
+    from paper_2509_19294_gb300 import build as nbuild
+    nbuild.build()
+    libs = [nbuild.LIB, nbuild.build_ablation()]
+    res = []
+    for lib in libs:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--ablation-child", lib],
+                           capture_output=True, text=True, check=True)
+        res.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    print(json.dumps({"tile_sum_compensation_ablation": {"with_compensation": res[0],
+                                                         "without_compensation": res[1]}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -706,7 +959,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--fp64-n", type=int, default=65536)
+    ap.add_argument("--fp64-n", type=int, default=0,
+                    help="FP64 comparator on the first N particles only (0 = the whole timed state)")
+    ap.add_argument("--no-drift", action="store_true", help="skip the C4 and C3 drift comparisons")
+    ap.add_argument("--no-c3-drift", action="store_true", help="skip the 1000-step C3 drift comparison")
+    ap.add_argument("--c3-steps", type=int, default=1000)
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -720,7 +978,22 @@ def main():
     ap.add_argument("--block-drift", default=None, metavar="N,T",
                     help="only the block-step energy drift, F32C vs FP64 path (e.g. 16384,0.5; "
                          "the FP64 path takes minutes)")
+    ap.add_argument("--c5-drift", type=int, default=0, metavar="STEPS",
+                    help="only the C5 energy drift over STEPS steps, F32C vs the FP64 path "
+                         "(10 steps: ~9 minutes of FP64 work)")
+    ap.add_argument("--ablation-tile-sums", action="store_true",
+                    help="only the accuracy with and without the cross-tile Kahan compensation")
+    ap.add_argument("--ablation-child", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.ablation_child:
+        ablation_child(args.ablation_child)
+        return
+    if args.ablation_tile_sums:
+        run_tile_sum_ablation()
+        return
+    if args.c5_drift:
+        run_c5_drift(args.c5_drift)
+        return
     if args.block_drift:
         n, t = args.block_drift.split(",")
         run_block_drift(int(n), float(t))

@@ -100,21 +100,24 @@ def test_host_buffers_through_step(oracle):
 
 
 def test_conservation_f32c_within_twice_f64():
-    # Plummer, eps = 1e-3, equal masses: |dE/E|, |dP| and |dL| of the FP32C run
-    # stay within 2x of the FP64 GPU run over the same steps (plus a floor at the
-    # FP64 level, where both are pure roundoff)
+    # Plummer, eps = 1e-3, equal masses, 200 steps in four chunks: the FP32C
+    # run's |dE/E| drift stays within 2x of the FP64 GPU run's over the same
+    # steps, with no floor (the FP64 drift, ~6e-8, is far above the FP32C
+    # energy jitter).  Momentum: FP32 pair terms break Newton's third law only
+    # at the rounding level, so |dP| <= steps * dt * 1e-6 * sum m|a| (the
+    # median relative force error target as the per-pair asymmetry bound);
+    # the FP64 path's |dP| is pure roundoff and is no scale for it
     pos, vel, mass = ic.plummer(8192, seed=3)
     res = {}
     for mode in (nb.NBODY_F32C, nb.NBODY_F64):
-        *_, d = run_steps(pos, vel, mass, 1e-3, 1e-4, 200, mode, chunks=4, reorder_every=10)
-        res[mode] = d[:, 0, :]
-    e32, e64 = res[nb.NBODY_F32C], res[nb.NBODY_F64]
+        *_, acc, _, d = run_steps(pos, vel, mass, 1e-3, 1e-4, 200, mode, chunks=4, reorder_every=10)
+        res[mode] = (d[:, 0, :], acc)
+    (e32, a32), (e64, _) = res[nb.NBODY_F32C], res[nb.NBODY_F64]
     drift32 = np.abs(e32[:, 2] - e32[0, 2]).max() / abs(e32[0, 2])
     drift64 = np.abs(e64[:, 2] - e64[0, 2]).max() / abs(e64[0, 2])
-    assert drift32 <= 2 * drift64 + 1e-9, (drift32, drift64)
+    assert drift32 <= 2 * drift64, (drift32, drift64)
     dP32 = np.abs(e32[:, 3:6] - e32[0, 3:6]).max()
-    dP64 = np.abs(e64[:, 3:6] - e64[0, 3:6]).max()
-    assert dP32 <= 2 * dP64 + 1e-10, (dP32, dP64)
+    assert dP32 <= 200 * 1e-4 * 1e-6 * (mass * np.linalg.norm(a32, axis=0)).sum(), dP32
 
 
 def test_ensemble_steps_match_oracle(oracle):
