@@ -28,7 +28,8 @@
 //     absolute position, the rounding of the shift is per particle (not one
 //     coherent displacement of a whole tile pair), and the tile loop runs no
 //     FP64 instruction.  Each thread sums a tile's terms in
-//     FP32, then folds the tile sum into a Kahan-compensated FP32 accumulator;
+//     FP32 (the potential terms of each eight j's as a tree first), then
+//     folds the tile sum into a Kahan-compensated FP32 accumulator;
 //     sum - compensation is converted to FP64 at the end.
 //   * Split j-ranges (small N or load balance): each split writes its FP64
 //     partials; the CTA that finishes last (atomic ticket, no waiting) adds
@@ -86,8 +87,12 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 #endif
 }
 
-template <int BLOCK, int P, int TJ, bool EPS_ZERO>
+// TREE: potential terms added as a tree before they join the running sum, 4
+// (eight j's) or 2 (four j's) at a time; 4 needs 8 more registers per
+// i-particle held at once.
+template <int BLOCK, int P, int TJ, bool EPS_ZERO, int TREE = 4>
 struct F32CKernel {
+    static_assert(TREE == 2 || TREE == 4, "tree of two or four potential terms");
     static constexpr int TC = BLOCK * P;
     static constexpr int NV = TJ;  // float4 vectors per j-tile (4 arrays x TJ/4)
     static constexpr int NLD = (NV + BLOCK - 1) / BLOCK;
@@ -132,15 +137,16 @@ struct F32CKernel {
     }
 
     // One pair of j's (the halves of each float2, tile positions j0 and j0 + 1)
-    // against the thread's P i-particles.  MASK: d[k] is the tile position of
-    // i-particle k's own slot (or outside the tile), whose potential term is
-    // dropped.
+    // against the thread's P i-particles: accumulates the acceleration terms
+    // and returns the potential terms m_j s in mo (summed by the caller).
+    // MASK: d[k] is the tile position of i-particle k's own slot (or outside
+    // the tile), whose potential term is dropped.
     template <bool MASK>
     __device__ static __forceinline__ void body(float2 xj, float2 yj, float2 zj, float2 mj,
                                                 const float2 e2, const float2 (&nx)[P],
                                                 const float2 (&ny)[P], const float2 (&nz)[P],
                                                 float2 (&ax)[P], float2 (&ay)[P], float2 (&az)[P],
-                                                float2 (&ph)[P], const int (&d)[P], int j0) {
+                                                float2 (&mo)[P], const int (&d)[P], int j0) {
 #pragma unroll
         for (int k = 0; k < P; ++k) {
             const float2 dx = __fadd2_rn(xj, nx[k]);
@@ -165,7 +171,7 @@ struct F32CKernel {
                 mp.x = d[k] == j0 ? 0.0f : ms.x;
                 mp.y = d[k] == j0 + 1 ? 0.0f : ms.y;
             }
-            ph[k] = __fadd2_rn(ph[k], mp);
+            mo[k] = mp;
             ax[k] = __ffma2_rn(w3, dx, ax[k]);
             ay[k] = __ffma2_rn(w3, dy, ay[k]);
             az[k] = __ffma2_rn(w3, dz, az[k]);
@@ -173,24 +179,55 @@ struct F32CKernel {
     }
 
     // All pairs of one shared-memory j-tile (buffer b) against the thread's P
-    // i-particles, summed in FP32.
+    // i-particles, summed in FP32.  2 * TREE j's per iteration; their TREE
+    // potential terms per lane are added as a tree before they join the
+    // running sum (the same number of adds: a shorter loop-carried chain and
+    // smaller rounding errors).
     template <bool MASK>
     __device__ static __forceinline__ void tile_pass(const Smem &sm, int b, const float2 e2,
                                                      const float2 (&nx)[P], const float2 (&ny)[P],
                                                      const float2 (&nz)[P], float2 (&ax)[P],
                                                      float2 (&ay)[P], float2 (&az)[P],
                                                      float2 (&ph)[P], const int (&d)[P]) {
+        static_assert((TJ / 4) % 2 == 0, "two float4 columns per iteration");
         const float4 *jx = sm.j[b][0];
         const float4 *jy = sm.j[b][1];
         const float4 *jz = sm.j[b][2];
         const float4 *jm = sm.j[b][3];
+        if (TREE == 2) {
 #pragma unroll 2
-        for (int v = 0; v < TJ / 4; ++v) {
-            const float4 X = jx[v], Y = jy[v], Z = jz[v], M = jm[v];
-            body<MASK>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
-                       make_float2(M.x, M.y), e2, nx, ny, nz, ax, ay, az, ph, d, 4 * v);
-            body<MASK>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
-                       make_float2(M.z, M.w), e2, nx, ny, nz, ax, ay, az, ph, d, 4 * v + 2);
+            for (int v = 0; v < TJ / 4; ++v) {
+                float2 m0[P], m1[P];
+                const float4 X = jx[v], Y = jy[v], Z = jz[v], M = jm[v];
+                body<MASK>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+                           make_float2(M.x, M.y), e2, nx, ny, nz, ax, ay, az, m0, d, 4 * v);
+                body<MASK>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+                           make_float2(M.z, M.w), e2, nx, ny, nz, ax, ay, az, m1, d, 4 * v + 2);
+#pragma unroll
+                for (int k = 0; k < P; ++k) ph[k] = __fadd2_rn(ph[k], __fadd2_rn(m0[k], m1[k]));
+            }
+            return;
+        }
+#pragma unroll 1
+        for (int v = 0; v < TJ / 4; v += 2) {
+            float2 m0[P], m1[P], m2[P], m3[P];
+            {
+                const float4 X = jx[v], Y = jy[v], Z = jz[v], M = jm[v];
+                body<MASK>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+                           make_float2(M.x, M.y), e2, nx, ny, nz, ax, ay, az, m0, d, 4 * v);
+                body<MASK>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+                           make_float2(M.z, M.w), e2, nx, ny, nz, ax, ay, az, m1, d, 4 * v + 2);
+            }
+            {
+                const float4 X = jx[v + 1], Y = jy[v + 1], Z = jz[v + 1], M = jm[v + 1];
+                body<MASK>(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+                           make_float2(M.x, M.y), e2, nx, ny, nz, ax, ay, az, m2, d, 4 * v + 4);
+                body<MASK>(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+                           make_float2(M.z, M.w), e2, nx, ny, nz, ax, ay, az, m3, d, 4 * v + 6);
+            }
+#pragma unroll
+            for (int k = 0; k < P; ++k)
+                ph[k] = __fadd2_rn(ph[k], __fadd2_rn(__fadd2_rn(m0[k], m1[k]), __fadd2_rn(m2[k], m3[k])));
         }
     }
 
@@ -356,9 +393,11 @@ struct F32CKernel {
     }
 };
 
+// The tree of four where the register budget allows it: one CTA per SM (255
+// registers) or two i-particles per thread; two otherwise.
 template <int BLOCK, int P, int TJ, int MINB, bool EPS_ZERO>
 __global__ void __launch_bounds__(BLOCK, MINB) forces_f32c_kernel(const F32CParams p) {
-    F32CKernel<BLOCK, P, TJ, EPS_ZERO>::run(p);
+    F32CKernel<BLOCK, P, TJ, EPS_ZERO, (P <= 2 || MINB <= 2) ? 4 : 2>::run(p);
 }
 
 }  // namespace nbody

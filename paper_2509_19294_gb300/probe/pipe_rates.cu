@@ -107,7 +107,10 @@ __global__ void __launch_bounds__(kProbeThreads) pair_probe(int iters, float *si
     __syncthreads();
     const long long t0 = clock64();
     for (int i = 0; i < iters; ++i) {
-        PairK::body<false>(xj, yj, zj, mj, e2, nx, ny, nz, ax, ay, az, ph, dself, 0);
+        float2 mo[kPairP];
+        PairK::body<false>(xj, yj, zj, mj, e2, nx, ny, nz, ax, ay, az, mo, dself, 0);
+#pragma unroll
+        for (int k = 0; k < kPairP; ++k) ph[k] = __fadd2_rn(ph[k], mo[k]);  // the potential's add
         // every j operand changes each iteration, so nothing can be hoisted;
         // these 4 paired adds per 2 * kPairP pairs make the figure a lower bound
         xj = __fadd2_rn(xj, dj);
