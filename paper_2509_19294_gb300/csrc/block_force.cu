@@ -718,24 +718,6 @@ cudaError_t launch_subset_f32c(int block, int p, int tj, int groups, int minb, b
     return cudaLaunchKernel(sh->kernel, dim3(grid), dim3(block * groups), args, 0, st);
 }
 
-cudaError_t add_subset_f32c_node(cudaGraph_t body, int block, int p, int tj, int groups, int minb,
-                                 bool eps_zero, int grid, const F32CSubsetParams &prm) {
-    const SubsetShape *sh = find_subset(block, p, tj, groups, minb, eps_zero);
-    if (!sh) return cudaErrorNotSupported;
-    cudaGraphNode_t node;
-    if (grid <= 0) return cudaGraphAddEmptyNode(&node, body, nullptr, 0);
-    F32CSubsetParams arg = prm;
-    void *args[] = {(void *)&arg};
-    cudaKernelNodeParams kp{};
-    kp.func = const_cast<void *>(sh->kernel);
-    kp.gridDim = dim3(grid);
-    kp.blockDim = dim3(block * groups);
-    kp.sharedMemBytes = 0;
-    kp.kernelParams = args;
-    kp.extra = nullptr;
-    return cudaGraphAddKernelNode(&node, body, nullptr, 0, &kp);
-}
-
 cudaError_t launch_subset_f64(int max_items, const double *xp, const double *vp, const double *mass,
                               const ClusterDev *cl, const SubItem *items, const int *n_items,
                               const int32_t *act, int64_t n, double G, double *acc, double *jerk,

@@ -326,8 +326,6 @@ struct BlockPackParams {
     long long partial_cap;  // doubles in the split-partial buffer
     double dt_max, dt_min;
     float dt_min_f;  // dt_min as a float (exact: a power of two >= 2^-126)
-    cudaGraphConditionalHandle cond;  // force-pass switch (use_cond: the step is graph-captured)
-    bool use_cond;
 };
 
 // The step's time in units of dt_min (block_next_time_q with the level scan
@@ -371,11 +369,6 @@ __device__ __forceinline__ void pack_tail(const BlockPackParams &q, long long tn
                   q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max, q.cs_large,
                   q.workers_large, q.large_min, q.partial_cap);
         q.sc->ticket_pack = 0;
-        // in a graph: run only the subset kernel the plan chose
-        if (q.use_cond)
-            cudaGraphSetConditional(q.cond, q.sc->few || q.sc->n_items == 0 ? kSubsetNone
-                                            : q.sc->n_items_large > 0        ? kSubsetLarge
-                                                                             : kSubsetSmall);
     }
 }
 
@@ -783,8 +776,6 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         q.dt_max = b.dt_max;
         q.dt_min = b.dt_min;
         q.dt_min_f = (float)b.dt_min;
-        q.cond = b.cond;
-        q.use_cond = b.use_cond;
         // tc = NT * PER, NT = 256 where tc allows it (checked above: PER <= 4)
 #define NB_PACK(NT_, PER_)                                                                  \
     if (b.tc == (NT_) * (PER_)) {                                                           \

@@ -999,18 +999,6 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, bool fresh
     BlockLaunch b = block_launch(ctx, a);
     b.fresh = fresh || reorder;
     int rc;
-    // captured F32C steps: the force pass runs through a switch node that the
-    // plan (last CTA of the pack kernel) sets, so the subset kernel that the
-    // plan did not choose is not launched at all
-    b.use_cond = capturing && ctx->mode == NBODY_F32C;
-    b.cond = 0;
-    cudaGraph_t cap_graph = nullptr;
-    if (b.use_cond) {
-        cudaStreamCaptureStatus st;
-        NB_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &cap_graph, nullptr, nullptr, nullptr));
-        if (st != cudaStreamCaptureStatusActive) return fail(ctx, NBODY_ECUDA, "block step: capture not active");
-        NB_CUDA(cudaGraphConditionalHandleCreate(&b.cond, cap_graph, kSubsetNone, cudaGraphCondAssignDefault));
-    }
     if (ctx->mode == NBODY_F32C && reorder)
         NB_CUDA(launch_reorder(a.pos, ctx->n, ctx->chunks, ctx->n_chunks, ctx->chunk_first, ctx->ncl, j.dcl,
                                ctx->bpart, ctx->bbox, ctx->keys, ctx->vals, ctx->sort_n, ctx->max_cluster,
@@ -1048,43 +1036,17 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, bool fresh
         q.pyl = bs.pyl;
         q.pzl = bs.pzl;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;
-        F32CSubsetParams ql = q;
         q.n_items = &bs.sc->n_items_small;
-        ql.n_items = &bs.sc->n_items_large;
-        ql.base.counters = j.counters + 1;  // its own queue head
-        if (b.use_cond) {
-            cudaStreamCaptureStatus st;
-            const cudaGraphNode_t *deps = nullptr;
-            const cudaGraphEdgeData *edges = nullptr;
-            size_t nd = 0;
-            NB_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &cap_graph, &deps, &edges, &nd));
-            cudaGraphNodeParams np{};
-            np.type = cudaGraphNodeTypeConditional;
-            np.conditional.handle = b.cond;
-            np.conditional.type = cudaGraphCondTypeSwitch;
-            np.conditional.size = 2;  // kSubsetSmall, kSubsetLarge; kSubsetNone runs neither
-            cudaGraphNode_t node;
-            NB_CUDA(cudaGraphAddNode(&node, cap_graph, deps, edges, nd, &np));
-            NB_CUDA(add_subset_f32c_node(np.conditional.phGraph_out[kSubsetSmall], bs.sub.block, bs.sub.p,
-                                         bs.sub.tj, bs.sub.split, bs.sub.ctas_per_sm, ctx->eps_zero,
-                                         bs.workers, q));
-            NB_CUDA(add_subset_f32c_node(np.conditional.phGraph_out[kSubsetLarge], bs.sub_large.block,
-                                         bs.sub_large.p, bs.sub_large.tj, bs.sub_large.split,
-                                         bs.sub_large.ctas_per_sm, ctx->eps_zero, bs.workers_large, ql));
-            NB_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-            *kernels += 1;  // at most one of the two runs
-        } else {
-            NB_CUDA(launch_subset_f32c(bs.sub.block, bs.sub.p, bs.sub.tj, bs.sub.split,
-                                       bs.sub.ctas_per_sm, ctx->eps_zero, bs.workers, q, s));
-            NB_CUDA(launch_subset_f32c(bs.sub_large.block, bs.sub_large.p, bs.sub_large.tj,
-                                       bs.sub_large.split, bs.sub_large.ctas_per_sm, ctx->eps_zero,
-                                       bs.workers_large, ql, s));
-            *kernels += 2;
-        }
+        NB_CUDA(launch_subset_f32c(bs.sub.block, bs.sub.p, bs.sub.tj, bs.sub.split,
+                                   bs.sub.ctas_per_sm, ctx->eps_zero, bs.workers, q, s));
+        q.n_items = &bs.sc->n_items_large;
+        q.base.counters = j.counters + 1;  // its own queue head
+        NB_CUDA(launch_subset_f32c(bs.sub_large.block, bs.sub_large.p, bs.sub_large.tj, bs.sub_large.split,
+                                   bs.sub_large.ctas_per_sm, ctx->eps_zero, bs.workers_large, q, s));
         // few-particle pass or split-partial sum, whichever the plan chose
         NB_CUDA(launch_subset_tail(bs.max_chunks, std::max(bs.cs, bs.cs_large), 4 * ctx->sms, q, bs.act, bs.sc,
                                    bs.few_part, bs.info, s));
-        *kernels += 1;
+        *kernels += 3;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
     } else {
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][0], s, capturing))) return rc;

@@ -152,8 +152,7 @@ struct BlockScalars {
     int few, few_ncl;
     int few_cl[kFewMax], few_abeg[kFewMax], few_jbase[kFewMax + 1];
     // i-chunk size of this step and the queue size seen by each subset kernel
-    // (graph-replayed steps launch only the chosen one; eager steps launch
-    // both, and the one not chosen reads 0 and returns at once)
+    // (the one not chosen reads 0 and returns at once)
     int cs, n_items_small, n_items_large;
     // F32C: time of the tile frames' origins (units of dt_min), set by the
     // fresh pack
@@ -264,15 +263,7 @@ struct BlockLaunch {
     // second subset kernel for large active sets (cs_large == 0: none)
     int cs_large, workers_large, large_min;
     long long partial_cap;  // doubles in the subset kernels' split-partial buffer
-    // F32C steps captured in a graph: the plan sets this switch to the force
-    // pass it chose (kSubsetSmall, kSubsetLarge, or kSubsetNone for the
-    // few-particle pass and empty steps), so only that subset kernel runs
-    cudaGraphConditionalHandle cond;
-    bool use_cond;
 };
-
-// Values of the force-pass switch (BlockLaunch::cond).
-constexpr unsigned kSubsetSmall = 0, kSubsetLarge = 1, kSubsetNone = 2;
 
 cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, double dt_max,
                               double dt_min, double eta_s, double *t, double *dt, long long *tq,
@@ -301,10 +292,6 @@ cudaError_t launch_block_levels(int64_t n, const double *dt, double dt_max, doub
 // block * groups threads per CTA (see SubsetKernel in block_force.cu).
 cudaError_t launch_subset_f32c(int block, int p, int tj, int groups, int minb, bool eps_zero,
                                int grid, const F32CSubsetParams &prm, cudaStream_t s);
-// The same launch as a kernel node of `body` (a conditional node's body graph;
-// an empty node when grid <= 0).
-cudaError_t add_subset_f32c_node(cudaGraph_t body, int block, int p, int tj, int groups, int minb,
-                                 bool eps_zero, int grid, const F32CSubsetParams &prm);
 cudaError_t launch_subset_f64(int max_items, const double *xp, const double *vp, const double *mass,
                               const ClusterDev *cl, const SubItem *items, const int *n_items,
                               const int32_t *act, int64_t n, double G, double *acc, double *jerk,
