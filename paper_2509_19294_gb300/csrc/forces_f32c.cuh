@@ -208,7 +208,10 @@ struct F32CKernel {
             }
             return;
         }
-#pragma unroll 1
+        // two iterations in flight on the 1024-wide tiles (measured 0.8 % faster
+        // there, not on narrower ones)
+        constexpr int kUnroll = TJ >= 1024 ? 2 : 1;
+#pragma unroll kUnroll
         for (int v = 0; v < TJ / 4; v += 2) {
             float2 m0[P], m1[P], m2[P], m3[P];
             {
