@@ -8,10 +8,12 @@
 // is per SM per clock and independent of the clock frequency:
 //   * FP32: independent chains of paired FMA (__ffma2_rn), lane-operations.
 //   * MUFU: independent chains of rsqrt.approx.ftz.f32.
-//   * pair: the force kernel's own per-pair arithmetic (F32CKernel::body) on
-//           register-resident data whose j operands change every iteration
+//   * pair: the force kernel's own per-pair arithmetic (F32CKernel::body, its
+//           potential terms added as a tree of four as in the tile loop) on
+//           register-resident data whose j operands change every call
 //           (4 extra paired ops per 8 pairs), i.e. a lower bound on its
-//           ceiling without shared loads.
+//           ceiling without shared loads; one CTA of 256 threads per SM, as
+//           the kernel's C5 shapes run.
 //   * FP64: independent chains of fma(double).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -88,8 +90,11 @@ __global__ void __launch_bounds__(kProbeThreads) dfma_probe(int iters, float *si
 constexpr int kPairP = 4;
 using PairK = F32CKernel<256, kPairP, 512, false>;
 
-__global__ void __launch_bounds__(kProbeThreads) pair_probe(int iters, float *sink,
-                                                            long long *cycles) {
+// One CTA of 256 threads per SM with up to 255 registers, as the kernel's C5
+// shape (256, 4, 512 or 1024) runs.
+constexpr int kPairThreads = 256;
+__global__ void __launch_bounds__(kPairThreads, 1) pair_probe(int iters, float *sink,
+                                                              long long *cycles) {
     float2 nx[kPairP], ny[kPairP], nz[kPairP], ax[kPairP], ay[kPairP], az[kPairP], ph[kPairP];
 #pragma unroll
     for (int k = 0; k < kPairP; ++k) {
@@ -107,16 +112,22 @@ __global__ void __launch_bounds__(kProbeThreads) pair_probe(int iters, float *si
     __syncthreads();
     const long long t0 = clock64();
     for (int i = 0; i < iters; ++i) {
-        float2 mo[kPairP];
-        PairK::body<false>(xj, yj, zj, mj, e2, nx, ny, nz, ax, ay, az, mo, dself, 0);
+        // four j-pairs per iteration, their potential terms added as a tree,
+        // as the kernel's tile loop does
+        float2 m[4][kPairP];
 #pragma unroll
-        for (int k = 0; k < kPairP; ++k) ph[k] = __fadd2_rn(ph[k], mo[k]);  // the potential's add
-        // every j operand changes each iteration, so nothing can be hoisted;
-        // these 4 paired adds per 2 * kPairP pairs make the figure a lower bound
-        xj = __fadd2_rn(xj, dj);
-        yj = __fadd2_rn(yj, dj);
-        zj = __fadd2_rn(zj, dj);
-        mj = __fmul2_rn(mj, make_float2(1.0001f, 0.9999f));
+        for (int q = 0; q < 4; ++q) {
+            PairK::body<false>(xj, yj, zj, mj, e2, nx, ny, nz, ax, ay, az, m[q], dself, 0);
+            // every j operand changes each call, so nothing can be hoisted;
+            // these 4 paired ops per 2 * kPairP pairs make the figure a lower bound
+            xj = __fadd2_rn(xj, dj);
+            yj = __fadd2_rn(yj, dj);
+            zj = __fadd2_rn(zj, dj);
+            mj = __fmul2_rn(mj, make_float2(1.0001f, 0.9999f));
+        }
+#pragma unroll
+        for (int k = 0; k < kPairP; ++k)
+            ph[k] = __fadd2_rn(ph[k], __fadd2_rn(__fadd2_rn(m[0][k], m[1][k]), __fadd2_rn(m[2][k], m[3][k])));
     }
     __syncthreads();
     const long long t1 = clock64();
@@ -156,7 +167,7 @@ extern "C" int nbody_measure_pipes(double *out, int n_out) {
             switch (probe) {
                 case 0: ffma2_probe<<<sms, kProbeThreads>>>(iters, sink, cyc); break;
                 case 1: rsqrt_probe<<<sms, kProbeThreads>>>(iters, sink, cyc); break;
-                case 2: pair_probe<<<sms, kProbeThreads>>>(iters / 4, sink, cyc); break;
+                case 2: pair_probe<<<sms, kPairThreads>>>(iters / 4, sink, cyc); break;
                 default: dfma_probe<<<sms, kProbeThreads>>>(iters / 16, sink, cyc); break;
             }
         }
@@ -173,7 +184,7 @@ extern "C" int nbody_measure_pipes(double *out, int n_out) {
         switch (probe) {
             case 0: rate[0] = threads * iters * kChains * 2.0 / mean; break;
             case 1: rate[1] = threads * iters * kChains / mean; break;
-            case 2: rate[2] = threads * (iters / 4) * (2.0 * kPairP) / mean; break;
+            case 2: rate[2] = kPairThreads * (double)(iters / 4) * (4 * 2.0 * kPairP) / mean; break;
             default: rate[3] = threads * (iters / 16) * kChains / mean; break;
         }
     }

@@ -15,13 +15,15 @@ extern "C" {
 #define NBODY_PROBE_ECUDA (-3)  /* a CUDA runtime call or a probe launch failed */
 
 /*
- * Per-SM issue rates of the current GPU, measured with one CTA of 1024 threads
- * per SM and clock64() cycles (so they do not depend on the clock frequency).
+ * Per-SM issue rates of the current GPU, measured with one CTA per SM (1024
+ * threads; 256 for the pair arithmetic, as the force kernel's C5 shapes run)
+ * and clock64() cycles (so they do not depend on the clock frequency).
  * out (host, n_out >= 4):
  *   out[0] FP32 lane-operations per clock per SM with paired (f32x2) FMA
  *   out[1] MUFU rsqrt results per clock per SM
  *   out[2] pairwise interactions per clock per SM of the F32C kernel's per-pair
- *          arithmetic alone (register-resident operands, no shared-memory loads)
+ *          arithmetic alone, potential terms summed as in its tile loop
+ *          (register-resident operands, no shared-memory loads)
  *   out[3] FP64 FMA per clock per SM
  * Allocates and frees a small device buffer and synchronises the device.
  * Returns 0 or a negative NBODY_PROBE_E* code.
