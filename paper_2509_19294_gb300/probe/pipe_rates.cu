@@ -105,29 +105,39 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_probe(int iters, float *
         ax[k] = ay[k] = az[k] = ph[k] = make_float2(0.0f, 0.0f);
     }
     const float2 e2 = make_float2(1e-6f, 1e-6f);
-    float2 xj = make_float2(0.1f, 0.2f), yj = make_float2(-0.3f, 0.4f);
-    float2 zj = make_float2(0.5f, -0.6f), mj = make_float2(1e-3f, 2e-3f);
+    // four independent j-pairs per iteration (the kernel loads them from
+    // shared memory, so they do not depend on each other)
+    float2 xj[4], yj[4], zj[4], mj[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        xj[q] = make_float2(0.1f + 0.01f * q, 0.2f);
+        yj[q] = make_float2(-0.3f, 0.4f + 0.01f * q);
+        zj[q] = make_float2(0.5f, -0.6f - 0.01f * q);
+        mj[q] = make_float2(1e-3f, 2e-3f);
+    }
     const float2 dj = make_float2(1e-4f, -1e-4f);
     const int dself[kPairP] = {-1, -1, -1, -1};  // no self pair among the probe's j's
     __syncthreads();
     const long long t0 = clock64();
     for (int i = 0; i < iters; ++i) {
-        // four j-pairs per iteration, their potential terms added as a tree,
-        // as the kernel's tile loop does
+        // the potential terms of the four j-pairs added as a tree, as the
+        // kernel's tile loop does
         float2 m[4][kPairP];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            PairK::body<false>(xj, yj, zj, mj, e2, nx, ny, nz, ax, ay, az, m[q], dself, 0);
-            // every j operand changes each call, so nothing can be hoisted;
-            // these 4 paired ops per 2 * kPairP pairs make the figure a lower bound
-            xj = __fadd2_rn(xj, dj);
-            yj = __fadd2_rn(yj, dj);
-            zj = __fadd2_rn(zj, dj);
-            mj = __fmul2_rn(mj, make_float2(1.0001f, 0.9999f));
-        }
+        for (int q = 0; q < 4; ++q)
+            PairK::body<false>(xj[q], yj[q], zj[q], mj[q], e2, nx, ny, nz, ax, ay, az, m[q], dself, 0);
 #pragma unroll
         for (int k = 0; k < kPairP; ++k)
             ph[k] = __fadd2_rn(ph[k], __fadd2_rn(__fadd2_rn(m[0][k], m[1][k]), __fadd2_rn(m[2][k], m[3][k])));
+        // every j operand changes each iteration, so nothing can be hoisted;
+        // these 4 paired ops per 2 * kPairP pairs make the figure a lower bound
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            xj[q] = __fadd2_rn(xj[q], dj);
+            yj[q] = __fadd2_rn(yj[q], dj);
+            zj[q] = __fadd2_rn(zj[q], dj);
+            mj[q] = __fmul2_rn(mj[q], make_float2(1.0001f, 0.9999f));
+        }
     }
     __syncthreads();
     const long long t1 = clock64();
