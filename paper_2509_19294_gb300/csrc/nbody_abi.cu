@@ -1164,11 +1164,18 @@ int run_tuner(nbody_ctx *ctx, cudaStream_t s) {
     double total_pairs = 0.0;
     for (int k = 0; k < ctx->ncl; ++k) total_pairs += (double)cluster_n(ctx, k) * cluster_n(ctx, k);
     const double jfrac = std::min(1.0, 1.0e11 / std::max(total_pairs, 1.0));
-    double *acc = nullptr;
-    if (int rc0 = dev_alloc(ctx, &acc, (size_t)ctx->n * 4)) return rc0;
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     NB_CUDA(cudaEventCreate(&e0));
-    NB_CUDA(cudaEventCreate(&e1));
+    if (cudaError_t e = cudaEventCreate(&e1)) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ctx, e, "cudaEventCreate");
+    }
+    double *acc = nullptr;
+    if (int rc0 = dev_alloc(ctx, &acc, (size_t)ctx->n * 4)) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc0;
+    }
     std::vector<std::pair<double, nbody_tiles>> timed;
     int rc = NBODY_OK;
     for (int c = 0; c < ns && rc == NBODY_OK; ++c) {
