@@ -254,7 +254,7 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
     __shared__ float wsum[kFewThreads / 32][kFewBatch][7];
     __shared__ double csum[kFewMax][7];
     __shared__ double fsum[kFewThreads];  // [group][output], ngrp * n_out <= kFewThreads
-    __shared__ int fjb[kFewMax + 1], fcl[kFewMax], fab[kFewMax], fsb[kFewMax];
+    __shared__ int fjb[kFewMax + 1], fab[kFewMax], fsb[kFewMax];
     __shared__ float fe2[kFewMax];
     // the corrector's inputs, fetched by cp.async while the j-loop runs: per
     // particle h, then a0, j0, v0, x0 of each component; with a mirror, its
@@ -272,7 +272,6 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
         fjb[e] = sc->few_jbase[e];
         if (e < nf) {
             const int c = sc->few_cl[e];
-            fcl[e] = c;
             fab[e] = sc->few_abeg[e];
             fsb[e] = p.cl[c].slot_begin;
             fe2[e] = p.cl[c].eps2f;
@@ -495,7 +494,7 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
                 fv = (double)reinterpret_cast<const float *>(&pre_cv[aa])[cp];
                 fc = fma(fv, (double)(tnq - pre_t0q) * q.corr.dt_min, pre_c0[aa][cp]);
             }
-            correct_particle_x4_pre(q.corr, pre_u[aa], act[aa], valid, sub, pre[aa][0], pre[aa][1 + 4 * cp],
+            correct_particle_x4_pre<true>(q.corr, pre_u[aa], act[aa], valid, sub, pre[aa][0], pre[aa][1 + 4 * cp],
                                     pre[aa][2 + 4 * cp], pre[aa][3 + 4 * cp], pre[aa][4 + 4 * cp], fc, fv,
                                     p.G * csum[aa][cp], p.G * csum[aa][3 + cp], -p.G * ph, sc->t_next, tnq);
         }
@@ -559,7 +558,7 @@ __device__ void reduce_pass(const F32CSubsetParams &q, const SubItem *__restrict
                 }
                 const int slot = q.act_slot[it.a0 + (valid ? la : (u % subs) * 32)];
                 const double G = q.base.G;
-                correct_particle_x4(q.corr, q.base.perm[slot], slot, valid, sub, G * ra, G * rj, -G * rp,
+                correct_particle_x4<true>(q.corr, q.base.perm[slot], slot, valid, sub, G * ra, G * rj, -G * rp,
                                     sc->t_next, sc->t_next_q);
             }
         } else if (g == 0 && l < it.na) {

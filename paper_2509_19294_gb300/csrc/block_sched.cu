@@ -719,7 +719,7 @@ __global__ void block_correct_kernel(const BlockCorrect c, const int32_t *__rest
             A1[d] = a1[d * c.n + i];
             J1[d] = j1[d * c.n + i];
         }
-        correct_particle(c, i, -1, A1, J1, p1[i], tn, tnq);  // no mirror on this path
+        correct_particle<false>(c, i, -1, A1, J1, p1[i], tn, tnq);  // no mirror on this path
     }
 }
 
