@@ -21,7 +21,6 @@ struct JerkShape {
 
 const JerkShape kJerkShapes[] = {SHAPE(128, 2, 256, 2), SHAPE(256, 2, 256, 1), SHAPE(256, 2, 512, 1),
                                  SHAPE(128, 1, 128, 4), SHAPE(64, 2, 128, 4), SHAPE(128, 2, 128, 3)};
-constexpr int kNumJerkShapes = sizeof(kJerkShapes) / sizeof(kJerkShapes[0]);
 
 const JerkShape *find(int block, int p, int tj, int minb, bool eps_zero) {
     for (const JerkShape &s : kJerkShapes)
