@@ -216,8 +216,12 @@ int nbody_step_hermite(nbody_ctx *ctx, double *pos, double *vel, const double *m
  * particles difference close pairs exactly (position offsets as float pairs):
  * FP32-rounded offsets would make a close pair's forces noisy enough for the
  * criterion (its third-derivative term scales as 1/h^3) to shrink its step
- * towards dt_min.  With NBODY_F64 every pair is FP64 and the step decisions
- * equal the FP64 oracle's.
+ * towards dt_min.  The F32C corrector keeps x, v and the derivative
+ * estimates in FP64 and evaluates the criterion in FP32 (it only selects a
+ * power of two, from inputs that carry the FP32 pair sums' error), so a
+ * decision can differ from the FP64 one where the criterion lies within that
+ * error of a power-of-two boundary.  With NBODY_F64 every pair is FP64 and the
+ * step decisions equal the FP64 oracle's.
  *
  * nbody_block_start: computes a, jerk, pot at the current state (t = 0) and the
  *   initial steps, the largest power of two <= min(dt_max, eta_s |a|/|a'|),
