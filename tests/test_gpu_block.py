@@ -32,7 +32,7 @@ def _built():
 
 
 def block_run(pos, vel, mass, eps, mode, eta=0.02, eta_s=0.01, t_end=T_END, offsets=None, flags=0,
-              jerk_tiles=None, **kw):
+              jerk_tiles=None, dt_max=DT_MAX, dt_min=DT_MIN, **kw):
     n = mass.shape[0]
     with nb.nbody_init(n, eps, mode=mode, cluster_offsets=offsets, flags=flags, **kw) as ctx:
         if jerk_tiles is not None:
@@ -41,7 +41,7 @@ def block_run(pos, vel, mass, eps, mode, eta=0.02, eta_s=0.01, t_end=T_END, offs
         a = torch.empty((3, n), dtype=torch.float64, device="cuda")
         j = torch.empty((3, n), dtype=torch.float64, device="cuda")
         ph = torch.empty(n, dtype=torch.float64, device="cuda")
-        nb.nbody_block_start(ctx, p, v, m, a, j, ph, DT_MAX, DT_MIN, eta, eta_s)
+        nb.nbody_block_start(ctx, p, v, m, a, j, ph, dt_max, dt_min, eta, eta_s)
         blocks, evals = nb.nbody_block_advance(ctx, p, v, m, a, j, ph, t_end)
         t, dt = nb.nbody_block_state(ctx)
         return host(p), host(v), host(a), host(j), dt, t, blocks, evals
@@ -109,6 +109,31 @@ def test_f32c_block_steps_track_oracle(oracle, jerk_tiles):
     assert np.median(dx) <= 1e-10 and dx.max() <= 1e-7, (np.median(dx), dx.max())
     s = metrics.summary(ga, ra)
     assert s["median"] <= 1e-6, s
+
+
+def test_f32c_step_criterion_outside_the_float_range_takes_the_fp64_decision():
+    # G x 2^40 with every time x 2^-20 (velocities x 2^20) is the same motion:
+    # the acceleration and its first three derivatives scale by 2^40, 2^60,
+    # 2^80 and 2^100, and every FP32 and FP64 operation before the step
+    # criterion scales exactly by a power of two.  The squared norms then
+    # leave the range (2^-120 .. 2^120) in which the F32C corrector takes the
+    # criterion in FP32, so the scaled run takes the FP64 decisions: the
+    # unscaled run's steps except where FP32 and FP64 rounding of the
+    # criterion fall on either side of a power of two, the same evaluations
+    # and, away from such flips, the same trajectories
+    pos, vel, mass = cluster_system(2000, 53)
+    s = 2.0 ** 20
+    bp, bv, _, _, bdt, bt, bb, be = block_run(pos, vel, mass, 0.005, nb.NBODY_F32C)
+    sp, sv, _, _, sdt, st, sb, se = block_run(pos, vel * s, mass, 0.005, nb.NBODY_F32C, G=s * s,
+                                              t_end=T_END / s, dt_max=DT_MAX / s, dt_min=DT_MIN / s)
+    assert np.all(st * s == T_END) and np.all(bt == T_END)
+    same = sdt * s == bdt
+    assert np.mean(same) >= 0.99, np.mean(same)
+    assert abs(sb - bb) <= 0.01 * bb and abs(se - be) <= 0.01 * be, (sb, bb, se, be)
+    dx = np.abs(sp - bp).max(axis=0)
+    assert np.median(dx) <= 1e-10 and dx.max() <= 1e-7, (np.median(dx), dx.max())
+    dv = np.abs(sv / s - bv).max(axis=0)
+    assert np.median(dv) <= 1e-10 and dv.max() <= 1e-5, (np.median(dv), dv.max())
 
 
 @pytest.mark.parametrize("mode", [nb.NBODY_F64, nb.NBODY_F32C])
