@@ -1,8 +1,9 @@
 // block_force.cu -- individual (block) time steps: the force pass on the
 // active subset (see block_sched.cu for the step's pipeline).  The subset
 // kernels evaluate i-chunks of the active list against all j of their
-// cluster; the tail kernel runs either the few-particle pass or the ordered sum
-// of the subset kernels' split partials.  An active particle is evaluated with
+// cluster, each CTA an even range of (i-chunk, j-tile) units; the tail kernel
+// runs either the few-particle pass or the ordered sum of the partials of the
+// i-chunks that several CTAs' ranges share.  An active particle is evaluated with
 // its own j-set offset and its own tile centre: per j-tile each thread forms
 // the exact centre difference for each of its particles, so the self pair's
 // separation is exactly zero, as in the full kernels, and its potential term is
@@ -34,13 +35,16 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 namespace {
 
-// Subset kernel: persistent CTAs over the device-built queue of (i-chunk of the
-// active list, j-range) items.  A CTA holds BLOCK * P active particles (P per
-// thread) in G thread groups of BLOCK; all groups hold the same particles and
-// each takes one G-th of every shared-memory j-tile, so a small active set
-// still keeps G times more warps busy.  The groups' Kahan sums are added in
-// group order (FP64, shared memory); a j-range split is written as an FP64
-// partial that subset_tail_kernel sums in split order.
+// Subset kernel: CTA w takes the w-th of the plan's even ranges of (i-chunk of
+// the active list, j-tile) units, in unit order: the tail of one i-chunk's
+// j-tiles, whole i-chunks, the head of another.  A CTA holds BLOCK * P active
+// particles (P per thread) in G thread groups of BLOCK; all groups hold the
+// same particles and each takes one G-th of every shared-memory j-tile, so a
+// small active set still keeps G times more warps busy.  The groups' Kahan
+// sums are added in group order (FP64, shared memory); an i-chunk covered
+// whole is finalised at once, a part of one is written as an FP64 partial
+// (slot 2w for the range's first i-chunk, 2w + 1 for its last) that
+// subset_tail_kernel adds in CTA order.
 template <int BLOCK, int P, int TJ, int G, bool EPS_ZERO>
 struct SubsetKernel {
     using JK = F32CJerkKernel<BLOCK, P, TJ, EPS_ZERO>;
@@ -83,17 +87,37 @@ struct SubsetKernel {
     __device__ static void run(const F32CSubsetParams q) {
         __shared__ Smem sm;
         const F32CJerkParams &p = q.base;
-        const int n_items = *q.n_items;
-        // CTAs beyond the item count would find the queue empty: they leave
-        // without touching its head (the others still drain it)
-        if ((int)blockIdx.x >= n_items) return;
+        // CTA w takes units [w W / nw, (w + 1) W / nw)
+        const int nw = *q.n_items;
+        if ((int)blockIdx.x >= nw) return;
+        const long long W = q.sc->n_units;
+        const int w = blockIdx.x;
+        const long long u0 = (long long)w * W / nw, u1 = (long long)(w + 1) * W / nw;
         const int li = threadIdx.x % BLOCK, g = threadIdx.x / BLOCK;
-        for (;;) {
-            if (threadIdx.x == 0) sm.item = atomicAdd(p.counters, 1);
-            __syncthreads();
-            const int item_idx = sm.item;
-            if (item_idx >= n_items) break;
-            const SubItem it = q.items[item_idx];
+        for (long long u = u0, unext = u0; u < u1; u = unext) {
+            SubItem it;
+            {
+                int lo = 0, hi = q.ncl;  // cluster: the last c with unit_off[c] <= u
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) / 2;
+                    if (q.unit_off[mid] <= u) lo = mid;
+                    else hi = mid;
+                }
+                const int n_jt = p.cl[lo].n_jt;
+                const long long local = u - q.unit_off[lo];
+                const int ci = (int)(local / n_jt), t = (int)(local % n_jt);
+                const int t1 = (int)min((long long)n_jt, t + (u1 - u));
+                it.cluster = lo;
+                it.a0 = q.act_begin[lo] + ci * CS;
+                it.na = min(CS, q.act_n[lo] - ci * CS);
+                it.chunk = q.ich_off[lo] + ci;
+                it.jt0 = t;
+                it.jt1 = t1;
+                it.nsplit = (t == 0 && t1 == n_jt) ? 1 : 2;  // 1: the whole j range
+                it.pbase = 2 * w;
+                it.split = u == u0 ? 0 : 1;  // partial slot 2w (first range) or 2w + 1 (last)
+                unext = u + (t1 - t);
+            }
             const ClusterDev cl = p.cl[it.cluster];
             const float2 e2 = make_float2(cl.eps2f, cl.eps2f);
             int slot[P];
@@ -509,31 +533,51 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
     if (threadIdx.x == 0) sc->ticket_few = 0;
 }
 
-// Sum the split partials of every chunk and finalise.  Work unit = 32
-// particles of one chunk; its 8 warps each sum one contiguous eighth of the
-// splits (loads unrolled, so their latencies overlap), then warp 0 adds the
-// eight group sums in group order.  The order of every addition is fixed by
-// (nsplit, particle), so the result does not depend on scheduling.
+// Sum the partials of every i-chunk that several CTAs' ranges share, and
+// finalise.  The CTAs wa..wb whose ranges cover the chunk's j-tiles follow
+// from its first unit: wa wrote it to slot 2 wa if its range starts at the
+// chunk, else to 2 wa + 1 (its range's last i-chunk), every later one to its
+// first slot 2w.  Work unit = 32 particles of one chunk; its 8 warps each sum
+// one contiguous eighth of the parts (loads unrolled, so their latencies
+// overlap), then warp 0 adds the eight group sums in group order.  The order
+// of every addition is fixed by the plan, so the result does not depend on
+// scheduling.
 constexpr int kReduceWarps = 8;
 
-__device__ void reduce_pass(const F32CSubsetParams &q, const SubItem *__restrict__ info,
-                            const BlockScalars *__restrict__ sc) {
+__device__ void reduce_pass(const F32CSubsetParams &q, const BlockScalars *__restrict__ sc) {
     const int cs = sc->cs;
     __shared__ double part[kReduceWarps][7][32];
     const int subs = (cs + 31) / 32;
     const int units = sc->n_chunks * subs;
     const int lane = threadIdx.x % 32, g = threadIdx.x / 32;
+    const long long W = sc->n_units;
+    const int nw = sc->n_workers;
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
-        const SubItem it = info[u / subs];
+        // the unit's i-chunk, its range and CTAs (every thread, the same few loads)
+        const int ch = u / subs;
+        int lo = 0, hi = q.ncl;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) / 2;
+            if (q.ich_off[mid] <= ch) lo = mid;
+            else hi = mid;
+        }
+        const int n_jt = q.base.cl[lo].n_jt, ci = ch - q.ich_off[lo];
+        const long long uc = q.unit_off[lo] + (long long)ci * n_jt;
+        const int wa = (int)(((uc + 1) * nw - 1) / W), wb = (int)(((uc + n_jt) * nw - 1) / W);
+        SubItem it;
+        it.a0 = q.act_begin[lo] + ci * cs;
+        it.na = min(cs, q.act_n[lo] - ci * cs);
+        const int nparts = wb - wa + 1;
         const int l = (u % subs) * 32 + lane;
-        if (it.nsplit <= 1 || (u % subs) * 32 >= it.na) continue;  // uniform over the CTA
-        const int s0 = (int)((int64_t)g * it.nsplit / kReduceWarps);
-        const int s1 = (int)((int64_t)(g + 1) * it.nsplit / kReduceWarps);
+        if (nparts <= 1 || (u % subs) * 32 >= it.na) continue;  // uniform over the CTA
+        const int slot_a = (long long)wa * W / nw == uc ? 2 * wa : 2 * wa + 1;
+        const int s0 = (int)((int64_t)g * nparts / kReduceWarps);
+        const int s1 = (int)((int64_t)(g + 1) * nparts / kReduceWarps);
         double tot[7] = {0, 0, 0, 0, 0, 0, 0};
         if (l < it.na) {
 #pragma unroll 4
             for (int s = s0; s < s1; ++s) {
-                const double *ps = q.partial + (size_t)(it.pbase + s) * 7 * cs + l;
+                const double *ps = q.partial + (size_t)(s == 0 ? slot_a : 2 * (wa + s)) * 7 * cs + l;
 #pragma unroll
                 for (int c = 0; c < 7; ++c) tot[c] += ps[c * cs];
             }
@@ -583,12 +627,12 @@ static_assert(kFewThreads == 32 * kReduceWarps, "one block size for both passes"
 
 __global__ void __launch_bounds__(kFewThreads, 2)
     subset_tail_kernel(const F32CSubsetParams q, const int32_t *__restrict__ act, BlockScalars *sc,
-                       double *__restrict__ few_part, const SubItem *__restrict__ info) {
+                       double *__restrict__ few_part) {
     if (sc->few) {  // uniform
         if ((int)blockIdx.x < kFewCtas) few_pass(q, act, sc, few_part);
         return;
     }
-    reduce_pass(q, info, sc);
+    reduce_pass(q, sc);
 }
 
 struct SubsetShape {
@@ -691,11 +735,10 @@ int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap) 
 }
 
 cudaError_t launch_subset_tail(int max_chunks, int max_cs, int max_ctas, const F32CSubsetParams &prm,
-                               const int32_t *act, BlockScalars *sc, double *few_part, const SubItem *info,
-                               cudaStream_t s) {
+                               const int32_t *act, BlockScalars *sc, double *few_part, cudaStream_t s) {
     const int64_t units = (int64_t)max_chunks * ((max_cs + 31) / 32);
     const int grid = (int)std::max<int64_t>(kFewCtas, std::min<int64_t>(units, max_ctas));
-    subset_tail_kernel<<<grid, kFewThreads, 0, s>>>(prm, act, sc, few_part, info);
+    subset_tail_kernel<<<grid, kFewThreads, 0, s>>>(prm, act, sc, few_part);
     return cudaGetLastError();
 }
 

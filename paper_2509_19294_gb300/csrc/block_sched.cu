@@ -15,15 +15,16 @@
 //      slot-ordered mirror (offsets from per-tile frames moving at constant
 //      velocity), pack it as the j-set (the jerk path's geometry) with the
 //      low parts of the position offsets, flag and count the active slots per
-//      tile; the last CTA plans the step (offsets, regime, split, queue
-//      size).  block_fresh_kernel replaces it after a re-sort and at the start
+//      tile; the last CTA plans the step (offsets, regime, and the force
+//      pass's work: the (i-chunk, j-tile) units cut into one even range per
+//      CTA).  block_fresh_kernel replaces it after a re-sort and at the start
 //      of an advance: it predicts from the FP64 rows, sets the frames and
 //      writes the mirror.
-//   3. block_queue_kernel: ordered compaction of the active slots, work items
+//   3. block_compact_kernel: ordered compaction of the active slots
 //   4. the force pass (block_force.cu): the small-set and the large-set subset
 //      kernels, then subset_tail_kernel, which either runs the few-particle
-//      pass (<= kFewMax active; the subset kernels then find an empty queue)
-//      or sums the subset kernels' split partials in order
+//      pass (<= kFewMax active; the subset kernels then have no work) or sums
+//      the partials of the i-chunks that several CTAs' ranges share, in order
 //   5. the Hermite corrector and next-step choice, in the epilogue of 4
 #include <algorithm>
 #include <cuda_runtime.h>
@@ -201,15 +202,21 @@ __device__ void block_exclusive_scan(const int *in, int *out, int n, int *total)
 
 // The step's plan (one thread, after the scan of the per-unit active counts;
 // cluster c owns units [unit_first[c], unit_first[c + 1])): per-cluster active
-// ranges and i-chunk counts, the split count, the work-queue size, and the
-// queue head reset for the subset kernel.
+// ranges and i-chunk counts, the regime, and the force pass's work.  F32C
+// (even_units): the (i-chunk, j-tile) units in unit order -- clusters, their
+// i-chunks, the j-tiles -- cut into one contiguous range for each of up to
+// `workers` CTAs (at least kMinUnits units a range; item_off[c] = cluster c's
+// first unit).  A static even split: the subset kernels' work per CTA is equal
+// to a unit, where a queue of (i-chunk, j-range) items handed out two rounds
+// of 5-6 j-tiles and left SMs idle for the last ones.  FP64 path: queue items
+// (i-chunk, j-range split), split chosen so the last round is fullest.
 __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_units,
                           const int32_t *__restrict__ unit_first, int ncl,
                           const ClusterDev *__restrict__ cl, int cs_small, int workers_small,
                           int max_split, int *__restrict__ act_begin, int *__restrict__ act_n,
                           int *__restrict__ ich_off, int *__restrict__ item_off, BlockScalars *sc,
                           int *queue_head, int few_max, int cs_large, int workers_large, int large_min,
-                          long long partial_cap) {
+                          long long partial_cap, bool even_units = false) {
     const bool few = total > 0 && total <= few_max;
     const bool large = !few && cs_large > 0 && total >= large_min;
     const int cs = large ? cs_large : cs_small;
@@ -237,11 +244,11 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
     sc->few_jbase[nf] = jb;
     int split = chunks > 0 ? (2 * workers) / chunks : 1;
     if (split > max_split) split = max_split;
-    if (split < 1) split = 1;
+    if (split < 1 || even_units) split = 1;
     // equal-cost items drain in ceil(items / workers) rounds: among the next few
     // split counts that fit the partial buffer, take the one whose last round
     // is fullest (the smaller on ties)
-    if (chunks > 0) {
+    if (chunks > 0 && !even_units) {
         // fullness of the last round, items / (workers * rounds), compared
         // exactly as fractions in integers (no FP64 division on this thread,
         // which every step waits for)
@@ -261,19 +268,35 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
         split = pick;
     }
     int items = 0;
-    for (int c = 0; c < ncl; ++c) {
-        item_off[c] = items;
-        const int sc_c = split < cl[c].n_jt ? split : (cl[c].n_jt > 0 ? cl[c].n_jt : 1);
-        items += (ich_off[c + 1] - ich_off[c]) * sc_c;
+    if (even_units) {
+        constexpr long long kMinUnits = 4;  // bounds the partials summed per chunk
+        long long w = 0;
+        for (int c = 0; c < ncl; ++c) {
+            item_off[c] = (int)w;
+            w += (long long)(ich_off[c + 1] - ich_off[c]) * cl[c].n_jt;
+        }
+        item_off[ncl] = (int)w;
+        long long nw = w / kMinUnits;
+        if (nw > workers) nw = workers;
+        if (nw < 1) nw = 1;
+        sc->n_units = w;
+        sc->n_workers = chunks > 0 ? (int)nw : 0;
+    } else {
+        for (int c = 0; c < ncl; ++c) {
+            item_off[c] = items;
+            const int sc_c = split < cl[c].n_jt ? split : (cl[c].n_jt > 0 ? cl[c].n_jt : 1);
+            items += (ich_off[c + 1] - ich_off[c]) * sc_c;
+        }
+        item_off[ncl] = items;
     }
-    item_off[ncl] = items;
     sc->n_active = total;
     sc->n_chunks = chunks;
     sc->split = split;
     sc->n_items = items;
     sc->cs = cs;
-    sc->n_items_small = large ? 0 : items;
-    sc->n_items_large = large ? items : 0;
+    const int work = even_units ? sc->n_workers : items;  // what the chosen subset kernel sees
+    sc->n_items_small = large ? 0 : work;
+    sc->n_items_large = large ? work : 0;
     if (total > 0) {
         sc->blocks += 1;
         sc->evals += total;
@@ -367,7 +390,7 @@ __device__ __forceinline__ void pack_tail(const BlockPackParams &q, long long tn
         if (fresh) q.sc->frame_t0q = tnq;
         plan_step(q.tile_off, total, q.n_tiles, q.tile_first, q.ncl, q.cl, q.cs, q.workers, q.max_split,
                   q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max, q.cs_large,
-                  q.workers_large, q.large_min, q.partial_cap);
+                  q.workers_large, q.large_min, q.partial_cap, true);
         q.sc->ticket_pack = 0;
     }
 }
@@ -681,27 +704,16 @@ __global__ void block_items_kernel(int ncl, const ClusterDev *__restrict__ cl,
     }
 }
 
-// F32C queue: one CTA per centre tile compacts the tile's active slots to
-// act[] (slot order within each cluster), and all threads build the items.
+// F32C compaction: one CTA per centre tile writes the tile's active slots to
+// act[] (slot order within each cluster); the force pass's work comes from
+// the plan (no items).
 template <int NT>
 __global__ void __launch_bounds__(NT)
-    block_queue_kernel(const uint8_t *__restrict__ flag, int tc, const int *__restrict__ tile_cnt,
-                       const int *__restrict__ tile_off, int32_t *__restrict__ act, int ncl,
-                       const ClusterDev *__restrict__ cl, const int *__restrict__ act_begin,
-                       const int *__restrict__ act_n, const int *__restrict__ ich_off,
-                       const int *__restrict__ item_off, const BlockScalars *__restrict__ sc,
-                       int max_items, SubItem *__restrict__ items, SubItem *__restrict__ info) {
+    block_compact_kernel(const uint8_t *__restrict__ flag, int tc, const int *__restrict__ tile_cnt,
+                       const int *__restrict__ tile_off, int32_t *__restrict__ act) {
     const int tile = blockIdx.x;
     if (tile_cnt[tile] > 0)  // uniform over the CTA
         compact_run<NT>(flag, (int64_t)tile * tc, (int64_t)(tile + 1) * tc, __ldcg(tile_off + tile), act);
-    const int n_items = sc->n_items;
-    const int split = sc->split;
-    const int cs = sc->cs;
-    for (int k = blockIdx.x * NT + threadIdx.x; k < n_items && k < max_items; k += gridDim.x * NT) {
-        const SubItem it = make_item(k, ncl, cl, cs, split, act_begin, act_n, ich_off, item_off);
-        items[k] = it;
-        if (it.split == 0) info[it.chunk] = it;
-    }
 }
 
 // The corrector as a pass over the active list: row = act[k] (FP64 path).
@@ -802,13 +814,11 @@ cudaError_t launch_block_queue(const BlockLaunch &b, cudaStream_t s, int *kernel
     cudaError_t e;
     if (b.px) {
         if (b.tc % 256 == 0)
-            NB_BL((block_queue_kernel<256><<<b.n_tiles, 256, 0, s>>>(
-                b.flag, b.tc, b.cnt, b.chunk_off, b.act, b.ncl, b.cl, b.act_begin, b.act_n, b.ich_off,
-                b.item_off, b.sc, b.max_items, b.items, b.info)));
+            NB_BL((block_compact_kernel<256><<<b.n_tiles, 256, 0, s>>>(b.flag, b.tc, b.cnt, b.chunk_off,
+                                                                     b.act)));
         else
-            NB_BL((block_queue_kernel<128><<<b.n_tiles, 128, 0, s>>>(
-                b.flag, b.tc, b.cnt, b.chunk_off, b.act, b.ncl, b.cl, b.act_begin, b.act_n, b.ich_off,
-                b.item_off, b.sc, b.max_items, b.items, b.info)));
+            NB_BL((block_compact_kernel<128><<<b.n_tiles, 128, 0, s>>>(b.flag, b.tc, b.cnt, b.chunk_off,
+                                                                     b.act)));
     } else {
         NB_BL((block_scatter_kernel<<<b.n_chunks, 256, 0, s>>>(b.flag, b.chunks, b.chunk_off, b.act)));
         NB_BL((block_items_kernel<<<grid_of(b.max_items, 256), 256, 0, s>>>(

@@ -923,8 +923,10 @@ int alloc_block(nbody_ctx *ctx) {
     for (int **q : {&b.act_begin, &b.act_n, &b.ich_off, &b.item_off})
         if ((rc = dev_alloc(ctx, q, ncl + 1))) return rc;
     if ((rc = dev_alloc(ctx, &b.act, n))) return rc;
-    if ((rc = dev_alloc(ctx, &b.items, (size_t)b.max_items))) return rc;
-    if ((rc = dev_alloc(ctx, &b.info, (size_t)b.max_chunks))) return rc;
+    if (!f32c) {  // the FP64 path's work queue (the F32C plan cuts even ranges of units)
+        if ((rc = dev_alloc(ctx, &b.items, (size_t)b.max_items))) return rc;
+        if ((rc = dev_alloc(ctx, &b.info, (size_t)b.max_chunks))) return rc;
+    }
     if ((rc = dev_alloc(ctx, &b.sc, 1))) return rc;
     NB_CUDA(cudaMemset(b.sc, 0, sizeof(BlockScalars)));
     return NBODY_OK;
@@ -1028,8 +1030,13 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, bool fresh
         q.base = jerk_params(ctx, j.a1, j.j1, bs.p1);
         q.corr = corr;
         q.act_slot = bs.act;
-        q.items = bs.items;
         q.n_items = &bs.sc->n_items;
+        q.act_begin = bs.act_begin;
+        q.act_n = bs.act_n;
+        q.ich_off = bs.ich_off;
+        q.unit_off = bs.item_off;
+        q.ncl = ctx->ncl;
+        q.sc = bs.sc;
         q.partial = bs.partial;
         q.tcj = j.tc;
         q.pxl = bs.pxl;
@@ -1045,7 +1052,7 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, bool fresh
                                    bs.sub_large.ctas_per_sm, ctx->eps_zero, bs.workers_large, q, s));
         // few-particle pass or split-partial sum, whichever the plan chose
         NB_CUDA(launch_subset_tail(bs.max_chunks, std::max(bs.cs, bs.cs_large), 4 * ctx->sms, q, bs.act, bs.sc,
-                                   bs.few_part, bs.info, s));
+                                   bs.few_part, s));
         *kernels += 3;
         if (slot >= 0 && (rc = record(ctx, ctx->ev[slot][1], s, capturing))) return rc;
     } else {

@@ -151,12 +151,18 @@ struct BlockScalars {
     // particles, their first active index and the prefix of their sizes
     int few, few_ncl;
     int few_cl[kFewMax], few_abeg[kFewMax], few_jbase[kFewMax + 1];
-    // i-chunk size of this step and the queue size seen by each subset kernel
-    // (the one not chosen reads 0 and returns at once)
+    // i-chunk size of this step and the work each subset kernel sees (F32C:
+    // the CTAs with a range of units; the kernel not chosen reads 0 and
+    // returns at once)
     int cs, n_items_small, n_items_large;
     // F32C: time of the tile frames' origins (units of dt_min), set by the
     // fresh pack
     long long frame_t0q;
+    // F32C subset kernels: the step's work, n_units (i-chunk, j-tile) units in
+    // unit order (clusters, their i-chunks, the j-tiles), split evenly over
+    // n_workers CTAs; item_off holds each cluster's first unit
+    long long n_units;
+    int n_workers;
 };
 
 // Subset acceleration + jerk kernel: base carries the j-set (the jerk path's
@@ -223,8 +229,12 @@ struct F32CSubsetParams {
     F32CJerkParams base;
     BlockCorrect corr;        // corr.sc == nullptr: store a1, j1, p1 instead
     const int32_t *act_slot;  // active list: j-set slot of each active particle
-    const SubItem *items;
-    const int *n_items;       // device count
+    const int *n_items;       // device count: the CTAs with a range of units
+    // the plan, per cluster: first active index, active count, first i-chunk,
+    // first (i-chunk, j-tile) unit; and the step's scalars (n_units, n_workers)
+    const int *act_begin, *act_n, *ich_off, *unit_off;
+    int ncl;
+    const BlockScalars *sc;
     double *partial;          // [slots][7][block * p]
     int tcj;                  // j-set centre-tile size
     // low parts of the packed position offsets (px + pxl, ...), or null: the
@@ -249,8 +259,8 @@ struct BlockLaunch {
     // per row chunk (FP64) or per centre tile (F32C): active counts, offsets
     int *cnt, *chunk_off, *act_begin, *act_n, *ich_off, *item_off;
     int32_t *act;
-    SubItem *items;
-    SubItem *info;  // per i-chunk: range, cluster, split count, partial base
+    SubItem *items;  // FP64 path: the work queue
+    SubItem *info;   // FP64 path: per i-chunk: range, cluster, split count, partial base
     BlockScalars *sc;
     // F32C j-set geometry (px == nullptr on the FP64 path)
     const int32_t *perm, *tile_cluster, *tile_first;
@@ -273,7 +283,7 @@ cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, 
 // queue size, queue head reset).
 cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kernels);
 // Ordered compaction of the active particles (rows, or j-set slots for F32C)
-// and the work queue.
+// and, on the FP64 path, the work queue.
 cudaError_t launch_block_queue(const BlockLaunch &b, cudaStream_t s, int *kernels);
 int subset_occupancy(int block, int p, int tj, int groups, int minb, bool eps_zero);
 int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap);
@@ -283,8 +293,7 @@ int subset_shapes(int *block, int *p, int *tj, int *groups, int *minb, int cap);
 // the deterministic parallel sum of the subset kernels' split partials; both
 // apply the epilogue and the corrector.
 cudaError_t launch_subset_tail(int max_chunks, int max_cs, int max_ctas, const F32CSubsetParams &prm,
-                               const int32_t *act, BlockScalars *sc, double *few_part, const SubItem *info,
-                               cudaStream_t s);
+                               const int32_t *act, BlockScalars *sc, double *few_part, cudaStream_t s);
 // Level counts of all particles and the first t_next (start of block stepping).
 cudaError_t launch_block_levels(int64_t n, const double *dt, double dt_max, double dt_min,
                                 const Chunk *chunks, int n_chunks, const long long *tq, double *part,
