@@ -97,14 +97,14 @@ struct SubsetKernel {
         for (long long u = u0, unext = u0; u < u1; u = unext) {
             SubItem it;
             {
-                int lo = 0, hi = q.ncl;  // cluster: the last c with unit_off[c] <= u
+                int lo = 0, hi = q.ncl;  // cluster: the last c with work_off[c] <= u
                 while (hi - lo > 1) {
                     const int mid = (lo + hi) / 2;
-                    if (q.unit_off[mid] <= u) lo = mid;
+                    if (q.work_off[mid] <= u) lo = mid;
                     else hi = mid;
                 }
                 const int n_jt = p.cl[lo].n_jt;
-                const long long local = u - q.unit_off[lo];
+                const long long local = u - q.work_off[lo];
                 const int ci = (int)(local / n_jt), t = (int)(local % n_jt);
                 const int t1 = (int)min((long long)n_jt, t + (u1 - u));
                 it.cluster = lo;
@@ -562,7 +562,7 @@ __device__ void reduce_pass(const F32CSubsetParams &q, const BlockScalars *__res
             else hi = mid;
         }
         const int n_jt = q.base.cl[lo].n_jt, ci = ch - q.ich_off[lo];
-        const long long uc = q.unit_off[lo] + (long long)ci * n_jt;
+        const long long uc = q.work_off[lo] + (long long)ci * n_jt;
         const int wa = (int)(((uc + 1) * nw - 1) / W), wb = (int)(((uc + n_jt) * nw - 1) / W);
         SubItem it;
         it.a0 = q.act_begin[lo] + ci * cs;

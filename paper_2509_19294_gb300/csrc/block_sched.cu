@@ -203,10 +203,10 @@ __device__ void block_exclusive_scan(const int *in, int *out, int n, int *total)
 // The step's plan (one thread, after the scan of the per-unit active counts;
 // cluster c owns units [unit_first[c], unit_first[c + 1])): per-cluster active
 // ranges and i-chunk counts, the regime, and the force pass's work.  F32C
-// (even_units): the (i-chunk, j-tile) units in unit order -- clusters, their
-// i-chunks, the j-tiles -- cut into one contiguous range for each of up to
-// `workers` CTAs (at least kMinUnits units a range; item_off[c] = cluster c's
-// first unit).  A static even split: the subset kernels' work per CTA is equal
+// (work_off given): the (i-chunk, j-tile) units in unit order -- clusters,
+// their i-chunks, the j-tiles -- cut into one contiguous range for each of up
+// to `workers` CTAs (at least kMinUnits units a range; work_off[c] = cluster
+// c's first unit).  A static even split: the subset kernels' work per CTA is equal
 // to a unit, where a queue of (i-chunk, j-range) items handed out two rounds
 // of 5-6 j-tiles and left SMs idle for the last ones.  FP64 path: queue items
 // (i-chunk, j-range split), split chosen so the last round is fullest.
@@ -216,7 +216,8 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
                           int max_split, int *__restrict__ act_begin, int *__restrict__ act_n,
                           int *__restrict__ ich_off, int *__restrict__ item_off, BlockScalars *sc,
                           int *queue_head, int few_max, int cs_large, int workers_large, int large_min,
-                          long long partial_cap, bool even_units = false) {
+                          long long partial_cap, long long *__restrict__ work_off = nullptr) {
+    const bool even_units = work_off != nullptr;  // F32C: even ranges of units
     const bool few = total > 0 && total <= few_max;
     const bool large = !few && cs_large > 0 && total >= large_min;
     const int cs = large ? cs_large : cs_small;
@@ -272,10 +273,10 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
         constexpr long long kMinUnits = 4;  // bounds the partials summed per chunk
         long long w = 0;
         for (int c = 0; c < ncl; ++c) {
-            item_off[c] = (int)w;
+            work_off[c] = w;
             w += (long long)(ich_off[c + 1] - ich_off[c]) * cl[c].n_jt;
         }
-        item_off[ncl] = (int)w;
+        work_off[ncl] = w;
         long long nw = w / kMinUnits;
         if (nw > workers) nw = workers;
         if (nw < 1) nw = 1;
@@ -342,6 +343,7 @@ struct BlockPackParams {
     const int32_t *tile_first;
     int ncl, cs, workers, max_split;
     int *act_begin, *act_n, *ich_off, *item_off;
+    long long *work_off;  // per cluster: first (i-chunk, j-tile) unit of the step's work
     BlockScalars *sc;
     int *queue_head;
     int few_max;
@@ -390,7 +392,7 @@ __device__ __forceinline__ void pack_tail(const BlockPackParams &q, long long tn
         if (fresh) q.sc->frame_t0q = tnq;
         plan_step(q.tile_off, total, q.n_tiles, q.tile_first, q.ncl, q.cl, q.cs, q.workers, q.max_split,
                   q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max, q.cs_large,
-                  q.workers_large, q.large_min, q.partial_cap, true);
+                  q.workers_large, q.large_min, q.partial_cap, q.work_off);
         q.sc->ticket_pack = 0;
     }
 }
@@ -782,6 +784,7 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         q.flag = b.flag; q.tile_cnt = b.cnt; q.tile_off = b.chunk_off; q.tile_first = b.tile_first;
         q.ncl = b.ncl; q.cs = b.cs; q.workers = b.workers; q.max_split = b.max_split;
         q.act_begin = b.act_begin; q.act_n = b.act_n; q.ich_off = b.ich_off; q.item_off = b.item_off;
+        q.work_off = b.work_off;
         q.sc = b.sc; q.queue_head = b.queue_head; q.few_max = b.few_max;
         q.cs_large = b.cs_large; q.workers_large = b.workers_large; q.large_min = b.large_min;
         q.partial_cap = b.partial_cap;

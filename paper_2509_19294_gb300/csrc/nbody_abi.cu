@@ -92,6 +92,7 @@ struct BlockState {
     uint8_t *flag = nullptr;
     int *cnt = nullptr, *chunk_off = nullptr, *act_begin = nullptr, *act_n = nullptr;
     int *ich_off = nullptr, *item_off = nullptr;
+    long long *work_off = nullptr;
     int32_t *act = nullptr;
     SubItem *items = nullptr, *info = nullptr;
     BlockScalars *sc = nullptr;
@@ -839,6 +840,7 @@ void free_block(nbody_ctx *ctx) {
     b.m = SlotMirror{};
     dev_free(&b.flag);
     for (int **q : {&b.cnt, &b.chunk_off, &b.act_begin, &b.act_n, &b.ich_off, &b.item_off}) dev_free(q);
+    dev_free(&b.work_off);
     dev_free(&b.act);
     dev_free(&b.items);
     dev_free(&b.info);
@@ -922,6 +924,7 @@ int alloc_block(nbody_ctx *ctx) {
         if ((rc = dev_alloc(ctx, q, nunit))) return rc;
     for (int **q : {&b.act_begin, &b.act_n, &b.ich_off, &b.item_off})
         if ((rc = dev_alloc(ctx, q, ncl + 1))) return rc;
+    if (f32c && (rc = dev_alloc(ctx, &b.work_off, ncl + 1))) return rc;
     if ((rc = dev_alloc(ctx, &b.act, n))) return rc;
     if (!f32c) {  // the FP64 path's work queue (the F32C plan cuts even ranges of units)
         if ((rc = dev_alloc(ctx, &b.items, (size_t)b.max_items))) return rc;
@@ -966,6 +969,7 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
     b.act_n = bs.act_n;
     b.ich_off = bs.ich_off;
     b.item_off = bs.item_off;
+    b.work_off = bs.work_off;
     b.act = bs.act;
     b.items = bs.items;
     b.info = bs.info;
@@ -1034,7 +1038,7 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, bool fresh
         q.act_begin = bs.act_begin;
         q.act_n = bs.act_n;
         q.ich_off = bs.ich_off;
-        q.unit_off = bs.item_off;
+        q.work_off = bs.work_off;
         q.ncl = ctx->ncl;
         q.sc = bs.sc;
         q.partial = bs.partial;

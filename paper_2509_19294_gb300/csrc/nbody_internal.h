@@ -160,7 +160,7 @@ struct BlockScalars {
     long long frame_t0q;
     // F32C subset kernels: the step's work, n_units (i-chunk, j-tile) units in
     // unit order (clusters, their i-chunks, the j-tiles), split evenly over
-    // n_workers CTAs; item_off holds each cluster's first unit
+    // n_workers CTAs (the plan's work_off holds each cluster's first unit)
     long long n_units;
     int n_workers;
 };
@@ -232,7 +232,8 @@ struct F32CSubsetParams {
     const int *n_items;       // device count: the CTAs with a range of units
     // the plan, per cluster: first active index, active count, first i-chunk,
     // first (i-chunk, j-tile) unit; and the step's scalars (n_units, n_workers)
-    const int *act_begin, *act_n, *ich_off, *unit_off;
+    const int *act_begin, *act_n, *ich_off;
+    const long long *work_off;
     int ncl;
     const BlockScalars *sc;
     double *partial;          // [slots][7][block * p]
@@ -258,6 +259,7 @@ struct BlockLaunch {
     uint8_t *flag;  // per row (FP64) or per j-set slot (F32C)
     // per row chunk (FP64) or per centre tile (F32C): active counts, offsets
     int *cnt, *chunk_off, *act_begin, *act_n, *ich_off, *item_off;
+    long long *work_off;  // F32C: per cluster, first (i-chunk, j-tile) unit of the step's work
     int32_t *act;
     SubItem *items;  // FP64 path: the work queue
     SubItem *info;   // FP64 path: per i-chunk: range, cluster, split count, partial base
