@@ -205,8 +205,9 @@ __device__ void block_exclusive_scan(const int *in, int *out, int n, int *total)
 // ranges and i-chunk counts, the regime, and the force pass's work.  F32C
 // (work_off given): the (i-chunk, j-tile) units in unit order -- clusters,
 // their i-chunks, the j-tiles -- cut into one contiguous range for each of up
-// to `workers` CTAs (at least kMinUnits units a range; work_off[c] = cluster
-// c's first unit).  A static even split: the subset kernels' work per CTA is equal
+// to `workers` CTAs (at least kMinUnits units a range, and a multiple of the
+// SM count once there are that many, so that every SM holds as many ranges;
+// work_off[c] = cluster c's first unit).  A static even split: the subset kernels' work per CTA is equal
 // to a unit, where a queue of (i-chunk, j-range) items handed out two rounds
 // of 5-6 j-tiles and left SMs idle for the last ones.  FP64 path: queue items
 // (i-chunk, j-range split), split chosen so the last round is fullest.
@@ -216,7 +217,7 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
                           int max_split, int *__restrict__ act_begin, int *__restrict__ act_n,
                           int *__restrict__ ich_off, int *__restrict__ item_off, BlockScalars *sc,
                           int *queue_head, int few_max, int cs_large, int workers_large, int large_min,
-                          long long partial_cap, long long *__restrict__ work_off = nullptr) {
+                          long long partial_cap, long long *__restrict__ work_off = nullptr, int sms = 1) {
     const bool even_units = work_off != nullptr;  // F32C: even ranges of units
     const bool few = total > 0 && total <= few_max;
     const bool large = !few && cs_large > 0 && total >= large_min;
@@ -270,7 +271,7 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
     }
     int items = 0;
     if (even_units) {
-        constexpr long long kMinUnits = 4;  // bounds the partials summed per chunk
+        constexpr long long kMinUnits = 2;  // bounds the partials summed per chunk
         long long w = 0;
         for (int c = 0; c < ncl; ++c) {
             work_off[c] = w;
@@ -279,6 +280,7 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
         work_off[ncl] = w;
         long long nw = w / kMinUnits;
         if (nw > workers) nw = workers;
+        if (nw > sms) nw -= nw % sms;  // every SM the same number of ranges
         if (nw < 1) nw = 1;
         sc->n_units = w;
         sc->n_workers = chunks > 0 ? (int)nw : 0;
@@ -349,6 +351,7 @@ struct BlockPackParams {
     int few_max;
     int cs_large, workers_large, large_min;
     long long partial_cap;  // doubles in the split-partial buffer
+    int sms;
     double dt_max, dt_min;
     float dt_min_f;  // dt_min as a float (exact: a power of two >= 2^-126)
 };
@@ -392,7 +395,7 @@ __device__ __forceinline__ void pack_tail(const BlockPackParams &q, long long tn
         if (fresh) q.sc->frame_t0q = tnq;
         plan_step(q.tile_off, total, q.n_tiles, q.tile_first, q.ncl, q.cl, q.cs, q.workers, q.max_split,
                   q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max, q.cs_large,
-                  q.workers_large, q.large_min, q.partial_cap, q.work_off);
+                  q.workers_large, q.large_min, q.partial_cap, q.work_off, q.sms);
         q.sc->ticket_pack = 0;
     }
 }
@@ -788,6 +791,7 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         q.sc = b.sc; q.queue_head = b.queue_head; q.few_max = b.few_max;
         q.cs_large = b.cs_large; q.workers_large = b.workers_large; q.large_min = b.large_min;
         q.partial_cap = b.partial_cap;
+        q.sms = b.sms;
         q.dt_max = b.dt_max;
         q.dt_min = b.dt_min;
         q.dt_min_f = (float)b.dt_min;

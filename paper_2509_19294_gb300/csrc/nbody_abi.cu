@@ -991,6 +991,7 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
         b.workers_large = bs.workers_large;
         b.large_min = bs.large_min;
         b.partial_cap = bs.partial_cap;
+        b.sms = ctx->sms;
     }
     return b;
 }

@@ -275,6 +275,7 @@ struct BlockLaunch {
     // second subset kernel for large active sets (cs_large == 0: none)
     int cs_large, workers_large, large_min;
     long long partial_cap;  // doubles in the subset kernels' split-partial buffer
+    int sms;  // multiprocessors (the even split's range count is a multiple)
 };
 
 cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, double dt_max,
