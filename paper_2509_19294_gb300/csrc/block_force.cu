@@ -518,9 +518,10 @@ __device__ void few_pass(const F32CSubsetParams &q, const int32_t *__restrict__ 
                 fv = (double)reinterpret_cast<const float *>(&pre_cv[aa])[cp];
                 fc = fma(fv, (double)(tnq - pre_t0q) * q.corr.dt_min, pre_c0[aa][cp]);
             }
-            correct_particle_x4_pre<true>(q.corr, pre_u[aa], act[aa], valid, sub, pre[aa][0], pre[aa][1 + 4 * cp],
-                                    pre[aa][2 + 4 * cp], pre[aa][3 + 4 * cp], pre[aa][4 + 4 * cp], fc, fv,
-                                    p.G * csum[aa][cp], p.G * csum[aa][3 + cp], -p.G * ph, sc->t_next, tnq);
+            correct_particle_x4_pre<true>(q.corr, pre_u[aa], act[aa], valid, sub, pre[aa][0],
+                                          pre[aa][1 + 4 * cp], pre[aa][2 + 4 * cp], pre[aa][3 + 4 * cp],
+                                          pre[aa][4 + 4 * cp], fc, fv, p.G * csum[aa][cp],
+                                          p.G * csum[aa][3 + cp], -p.G * ph, sc->t_next, tnq);
         }
     } else {
         for (int a = threadIdx.x; a < na; a += blockDim.x) {
@@ -603,7 +604,7 @@ __device__ void reduce_pass(const F32CSubsetParams &q, const BlockScalars *__res
                 const int slot = q.act_slot[it.a0 + (valid ? la : (u % subs) * 32)];
                 const double G = q.base.G;
                 correct_particle_x4<true>(q.corr, q.base.perm[slot], slot, valid, sub, G * ra, G * rj, -G * rp,
-                                    sc->t_next, sc->t_next_q);
+                                          sc->t_next, sc->t_next_q);
             }
         } else if (g == 0 && l < it.na) {
             double r[7];

@@ -216,7 +216,7 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
                           const ClusterDev *__restrict__ cl, int cs_small, int workers_small,
                           int max_split, int *__restrict__ act_begin, int *__restrict__ act_n,
                           int *__restrict__ ich_off, int *__restrict__ item_off, BlockScalars *sc,
-                          int *queue_head, int few_max, int cs_large, int workers_large, int large_min,
+                          int few_max, int cs_large, int workers_large, int large_min,
                           long long partial_cap, long long *__restrict__ work_off = nullptr, int sms = 1) {
     const bool even_units = work_off != nullptr;  // F32C: even ranges of units
     const bool few = total > 0 && total <= few_max;
@@ -304,7 +304,6 @@ __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_uni
         sc->blocks += 1;
         sc->evals += total;
     }
-    if (queue_head) queue_head[0] = queue_head[1] = 0;  // small and large subset kernels
 }
 
 // Compaction stage 2 (FP64 path, one CTA): chunk offsets and the plan.
@@ -318,7 +317,7 @@ __global__ void __launch_bounds__(kScan)
     __syncthreads();
     if (threadIdx.x == 0)
         plan_step(chunk_off, total, n_chunks, chunk_first, ncl, cl, cs, workers, max_split, act_begin,
-                  act_n, ich_off, item_off, sc, nullptr, 0, 0, 0, 0, 0);
+                  act_n, ich_off, item_off, sc, 0, 0, 0, 0, 0);
 }
 
 // F32C: one CTA per centre tile of the j-set.  Predicts the tile's particles to
@@ -347,7 +346,6 @@ struct BlockPackParams {
     int *act_begin, *act_n, *ich_off, *item_off;
     long long *work_off;  // per cluster: first (i-chunk, j-tile) unit of the step's work
     BlockScalars *sc;
-    int *queue_head;
     int few_max;
     int cs_large, workers_large, large_min;
     long long partial_cap;  // doubles in the split-partial buffer
@@ -394,7 +392,7 @@ __device__ __forceinline__ void pack_tail(const BlockPackParams &q, long long tn
         q.sc->t_next = (double)tnq * q.dt_min;
         if (fresh) q.sc->frame_t0q = tnq;
         plan_step(q.tile_off, total, q.n_tiles, q.tile_first, q.ncl, q.cl, q.cs, q.workers, q.max_split,
-                  q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.queue_head, q.few_max, q.cs_large,
+                  q.act_begin, q.act_n, q.ich_off, q.item_off, q.sc, q.few_max, q.cs_large,
                   q.workers_large, q.large_min, q.partial_cap, q.work_off, q.sms);
         q.sc->ticket_pack = 0;
     }
@@ -788,7 +786,7 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         q.ncl = b.ncl; q.cs = b.cs; q.workers = b.workers; q.max_split = b.max_split;
         q.act_begin = b.act_begin; q.act_n = b.act_n; q.ich_off = b.ich_off; q.item_off = b.item_off;
         q.work_off = b.work_off;
-        q.sc = b.sc; q.queue_head = b.queue_head; q.few_max = b.few_max;
+        q.sc = b.sc; q.few_max = b.few_max;
         q.cs_large = b.cs_large; q.workers_large = b.workers_large; q.large_min = b.large_min;
         q.partial_cap = b.partial_cap;
         q.sms = b.sms;

@@ -985,7 +985,6 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
         b.pxl = bs.pxl; b.pyl = bs.pyl; b.pzl = bs.pzl;
         b.pvx = j.pvx; b.pvy = j.pvy; b.pvz = j.pvz;
         b.chl = j.chl; b.vchl = j.vchl;
-        b.queue_head = j.counters;
         b.few_max = kFewMax;
         b.cs_large = bs.cs_large;
         b.workers_large = bs.workers_large;
@@ -1029,8 +1028,7 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, bool fresh
     corr.dt_min = bs.dt_min;
     corr.eta = bs.eta;
     if (ctx->mode == NBODY_F32C) {
-        // the force kernels' epilogues apply the corrector (no separate pass);
-        // the large-set kernel gets its own queue head
+        // the force kernels' epilogues apply the corrector (no separate pass)
         F32CSubsetParams q{};
         q.base = jerk_params(ctx, j.a1, j.j1, bs.p1);
         q.corr = corr;
@@ -1052,7 +1050,6 @@ int enqueue_block_step(nbody_ctx *ctx, const Arrays &a, bool reorder, bool fresh
         NB_CUDA(launch_subset_f32c(bs.sub.block, bs.sub.p, bs.sub.tj, bs.sub.split,
                                    bs.sub.ctas_per_sm, ctx->eps_zero, bs.workers, q, s));
         q.n_items = &bs.sc->n_items_large;
-        q.base.counters = j.counters + 1;  // its own queue head
         NB_CUDA(launch_subset_f32c(bs.sub_large.block, bs.sub_large.p, bs.sub_large.tj, bs.sub_large.split,
                                    bs.sub_large.ctas_per_sm, ctx->eps_zero, bs.workers_large, q, s));
         // few-particle pass or split-partial sum, whichever the plan chose

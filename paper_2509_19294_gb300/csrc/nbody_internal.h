@@ -270,7 +270,6 @@ struct BlockLaunch {
     float *px, *py, *pz, *pm, *pvx, *pvy, *pvz;
     float *pxl, *pyl, *pzl;  // low parts of the position offsets (block steps)
     float4 *chl, *vchl;
-    int *queue_head;  // [2]: the small- and large-set subset kernels' queue heads
     int few_max;  // 0 disables the few-particle path
     // second subset kernel for large active sets (cs_large == 0: none)
     int cs_large, workers_large, large_min;
