@@ -87,12 +87,12 @@ struct SubsetKernel {
     __device__ static void run(const F32CSubsetParams q) {
         __shared__ Smem sm;
         const F32CJerkParams &p = q.base;
-        // CTA w takes units [w W / nw, (w + 1) W / nw)
+        // CTA w takes the w-th of nw even ranges of the W units
         const int nw = *q.n_items;
         if ((int)blockIdx.x >= nw) return;
         const long long W = q.sc->n_units;
         const int w = blockIdx.x;
-        const long long u0 = (long long)w * W / nw, u1 = (long long)(w + 1) * W / nw;
+        const long long u0 = even_range_begin(w, W, nw), u1 = even_range_begin(w + 1, W, nw);
         const int li = threadIdx.x % BLOCK, g = threadIdx.x / BLOCK;
         for (long long u = u0, unext = u0; u < u1; u = unext) {
             SubItem it;
@@ -114,8 +114,8 @@ struct SubsetKernel {
                 it.jt0 = t;
                 it.jt1 = t1;
                 it.nsplit = (t == 0 && t1 == n_jt) ? 1 : 2;  // 1: the whole j range
-                it.pbase = 2 * w;
-                it.split = u == u0 ? 0 : 1;  // partial slot 2w (first range) or 2w + 1 (last)
+                it.pbase = (int)even_range_slot(w, u - t, W, nw);  // the partial's slot
+                it.split = 0;
                 unext = u + (t1 - t);
             }
             const ClusterDev cl = p.cl[it.cluster];
@@ -564,14 +564,15 @@ __device__ void reduce_pass(const F32CSubsetParams &q, const BlockScalars *__res
         }
         const int n_jt = q.base.cl[lo].n_jt, ci = ch - q.ich_off[lo];
         const long long uc = q.work_off[lo] + (long long)ci * n_jt;
-        const int wa = (int)(((uc + 1) * nw - 1) / W), wb = (int)(((uc + n_jt) * nw - 1) / W);
+        const int wa = (int)even_range_of(uc, W, nw), wb = (int)even_range_of(uc + n_jt - 1, W, nw);
         SubItem it;
         it.a0 = q.act_begin[lo] + ci * cs;
         it.na = min(cs, q.act_n[lo] - ci * cs);
         const int nparts = wb - wa + 1;
         const int l = (u % subs) * 32 + lane;
         if (nparts <= 1 || (u % subs) * 32 >= it.na) continue;  // uniform over the CTA
-        const int slot_a = (long long)wa * W / nw == uc ? 2 * wa : 2 * wa + 1;
+        // range wa's slot; every later range starts inside the chunk: slot 2r
+        const int slot_a = (int)even_range_slot(wa, uc, W, nw);
         const int s0 = (int)((int64_t)g * nparts / kReduceWarps);
         const int s1 = (int)((int64_t)(g + 1) * nparts / kReduceWarps);
         double tot[7] = {0, 0, 0, 0, 0, 0, 0};

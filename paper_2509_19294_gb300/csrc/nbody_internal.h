@@ -209,6 +209,28 @@ __host__ __device__ __forceinline__ int block_level(double h, double dt_max) {
     return (int)((bm >> 52) & 0x7FF) - (int)((bh >> 52) & 0x7FF);
 }
 
+// Even split of the block-step subset kernels' work (F32C): n_units
+// (i-chunk, j-tile) units in order, cut into n_ranges contiguous ranges, one
+// per CTA; range r is [even_range_begin(r), even_range_begin(r + 1)).
+__host__ __device__ __forceinline__ long long even_range_begin(long long r, long long n_units,
+                                                              long long n_ranges) {
+    return r * n_units / n_ranges;
+}
+
+// The range holding unit u (the last r with even_range_begin(r) <= u).
+__host__ __device__ __forceinline__ long long even_range_of(long long u, long long n_units,
+                                                           long long n_ranges) {
+    return ((u + 1) * n_ranges - 1) / n_units;
+}
+
+// Partial slot of range r's part of an i-chunk whose first unit is uc and that
+// other ranges share: 2r when the range starts in the chunk (its first
+// i-chunk), 2r + 1 when it started before (the chunk is its last).
+__host__ __device__ __forceinline__ long long even_range_slot(long long r, long long uc, long long n_units,
+                                                             long long n_ranges) {
+    return even_range_begin(r, n_units, n_ranges) >= uc ? 2 * r : 2 * r + 1;
+}
+
 // The next block time (in units of dt_min) after a step at time tq_now that
 // moved n_moved particles.  Every t_i is a multiple of its step dt_i with
 // t_i <= t_now < t_i + dt_i, so min (t_i + dt_i) is the next multiple of the
