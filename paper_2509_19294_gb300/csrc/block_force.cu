@@ -622,9 +622,9 @@ __device__ void reduce_pass(const F32CSubsetParams &q, const BlockScalars *__res
 }
 
 // The force pass's last kernel: the few-particle pass when the plan chose it
-// (on kFewCtas CTAs), else the ordered sum of the subset kernels' split
-// partials.  One launch for either, after the subset kernels (which find an
-// empty queue in the few-particle case).
+// (on kFewCtas CTAs), else the ordered sum of the shared i-chunks' partials.
+// One launch for either, after the subset kernels (which have no work in the
+// few-particle case).
 static_assert(kFewThreads == 32 * kReduceWarps, "one block size for both passes");
 
 __global__ void __launch_bounds__(kFewThreads, 2)

@@ -207,10 +207,11 @@ __device__ void block_exclusive_scan(const int *in, int *out, int n, int *total)
 // their i-chunks, the j-tiles -- cut into one contiguous range for each of up
 // to `workers` CTAs (at least kMinUnits units a range, and a multiple of the
 // SM count once there are that many, so that every SM holds as many ranges;
-// work_off[c] = cluster c's first unit).  A static even split: the subset kernels' work per CTA is equal
-// to a unit, where a queue of (i-chunk, j-range) items handed out two rounds
-// of 5-6 j-tiles and left SMs idle for the last ones.  FP64 path: queue items
-// (i-chunk, j-range split), split chosen so the last round is fullest.
+// work_off[c] = cluster c's first unit).  A static even split: every CTA
+// gets the same work to within a unit, where a queue of (i-chunk, j-range)
+// items handed out two rounds of 5-6 j-tiles and left SMs idle for the last
+// ones.  FP64 path: queue items (i-chunk, j-range split), the split chosen so
+// that the last round is fullest.
 __device__ void plan_step(const int *__restrict__ unit_off, int total, int n_units,
                           const int32_t *__restrict__ unit_first, int ncl,
                           const ClusterDev *__restrict__ cl, int cs_small, int workers_small,

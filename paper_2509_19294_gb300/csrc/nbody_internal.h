@@ -303,8 +303,8 @@ cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, 
                               double dt_min, double eta_s, double *t, double *dt, long long *tq,
                               cudaStream_t s);
 // t_next (FP64 path: integer min; F32C: from the level counts), prediction
-// (+ the packed j-set for F32C), flags, counts and the plan (offsets, split,
-// queue size, queue head reset).
+// (+ the packed j-set for F32C), flags, counts and the plan (offsets, regime,
+// and the force pass's work: F32C even ranges of units, FP64 queue items).
 cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kernels);
 // Ordered compaction of the active particles (rows, or j-set slots for F32C)
 // and, on the FP64 path, the work queue.
