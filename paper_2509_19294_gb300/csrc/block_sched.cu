@@ -200,112 +200,6 @@ __device__ void block_exclusive_scan(const int *in, int *out, int n, int *total)
     if (threadIdx.x == 0) *total = carry;
 }
 
-// The step's plan (one thread, after the scan of the per-unit active counts;
-// cluster c owns units [unit_first[c], unit_first[c + 1])): per-cluster active
-// ranges and i-chunk counts, the regime, and the force pass's work.  F32C
-// (work_off given): the (i-chunk, j-tile) units in unit order -- clusters,
-// their i-chunks, the j-tiles -- cut into one contiguous range for each of up
-// to `workers` CTAs (at least kMinUnits units a range, and a multiple of the
-// SM count once there are that many, so that every SM holds as many ranges;
-// work_off[c] = cluster c's first unit).  A static even split: every CTA
-// gets the same work to within a unit, where a queue of (i-chunk, j-range)
-// items handed out two rounds of 5-6 j-tiles and left SMs idle for the last
-// ones.  FP64 path: queue items (i-chunk, j-range split), the split chosen so
-// that the last round is fullest.
-__device__ void plan_step(const int *__restrict__ unit_off, int total, int n_units,
-                          const int32_t *__restrict__ unit_first, int ncl,
-                          const ClusterDev *__restrict__ cl, int cs_small, int workers_small,
-                          int max_split, int *__restrict__ act_begin, int *__restrict__ act_n,
-                          int *__restrict__ ich_off, int *__restrict__ item_off, BlockScalars *sc,
-                          int few_max, int cs_large, int workers_large, int large_min,
-                          long long partial_cap, long long *__restrict__ work_off = nullptr, int sms = 1) {
-    const bool even_units = work_off != nullptr;  // F32C: even ranges of units
-    const bool few = total > 0 && total <= few_max;
-    const bool large = !few && cs_large > 0 && total >= large_min;
-    const int cs = large ? cs_large : cs_small;
-    const int workers = large ? workers_large : workers_small;
-    int chunks = 0, nf = 0, jb = 0;
-    for (int c = 0; c < ncl; ++c) {
-        const int b = unit_first[c], e = unit_first[c + 1];
-        const int a0 = b < n_units ? unit_off[b] : total;
-        const int a1 = e < n_units ? unit_off[e] : total;
-        act_begin[c] = a0;
-        act_n[c] = a1 - a0;
-        ich_off[c] = chunks;
-        if (!few) chunks += (a1 - a0 + cs - 1) / cs;
-        if (few && a1 > a0) {  // at most total (<= kFewMax) clusters
-            sc->few_cl[nf] = c;
-            sc->few_abeg[nf] = a0;
-            sc->few_jbase[nf] = jb;
-            jb += cl[c].n;
-            ++nf;
-        }
-    }
-    ich_off[ncl] = chunks;
-    sc->few = few;
-    sc->few_ncl = nf;
-    sc->few_jbase[nf] = jb;
-    int split = chunks > 0 ? (2 * workers) / chunks : 1;
-    if (split > max_split) split = max_split;
-    if (split < 1 || even_units) split = 1;
-    // equal-cost items drain in ceil(items / workers) rounds: among the next few
-    // split counts that fit the partial buffer, take the one whose last round
-    // is fullest (the smaller on ties)
-    if (chunks > 0 && !even_units) {
-        // fullness of the last round, items / (workers * rounds), compared
-        // exactly as fractions in integers (no FP64 division on this thread,
-        // which every step waits for)
-        const long long max_slots = partial_cap / (7LL * cs);
-        long long best_items = 0, best_rounds = 1;
-        int pick = split;
-        for (int sp = split; sp <= split + 3 && sp <= max_split; ++sp) {
-            const long long items = (long long)chunks * sp;
-            if (sp > 1 && items > max_slots) break;
-            const long long rounds = (items + workers - 1) / workers;
-            if (items * best_rounds > best_items * rounds) {
-                best_items = items;
-                best_rounds = rounds;
-                pick = sp;
-            }
-        }
-        split = pick;
-    }
-    int items = 0;
-    if (even_units) {
-        constexpr long long kMinUnits = 2;  // bounds the partials summed per chunk
-        long long w = 0;
-        for (int c = 0; c < ncl; ++c) {
-            work_off[c] = w;
-            w += (long long)(ich_off[c + 1] - ich_off[c]) * cl[c].n_jt;
-        }
-        work_off[ncl] = w;
-        long long nw = w / kMinUnits;
-        if (nw > workers) nw = workers;
-        if (nw > sms) nw -= nw % sms;  // every SM the same number of ranges
-        if (nw < 1) nw = 1;
-        sc->n_units = w;
-        sc->n_workers = chunks > 0 ? (int)nw : 0;
-    } else {
-        for (int c = 0; c < ncl; ++c) {
-            item_off[c] = items;
-            const int sc_c = split < cl[c].n_jt ? split : (cl[c].n_jt > 0 ? cl[c].n_jt : 1);
-            items += (ich_off[c + 1] - ich_off[c]) * sc_c;
-        }
-        item_off[ncl] = items;
-    }
-    sc->n_active = total;
-    sc->n_chunks = chunks;
-    sc->split = split;
-    sc->n_items = items;
-    sc->cs = cs;
-    const int work = even_units ? sc->n_workers : items;  // what the chosen subset kernel sees
-    sc->n_items_small = large ? 0 : work;
-    sc->n_items_large = large ? work : 0;
-    if (total > 0) {
-        sc->blocks += 1;
-        sc->evals += total;
-    }
-}
 
 // Compaction stage 2 (FP64 path, one CTA): chunk offsets and the plan.
 __global__ void __launch_bounds__(kScan)
