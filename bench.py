@@ -465,18 +465,35 @@ def run_ours(args):
                 b1, e1_ = nb.nbody_block_advance(cb, p_, v_, m_, a_, j_, po_, 2.0 ** -4)
                 torch.cuda.synchronize()
                 sec = time.perf_counter() - t0
-                kms = nb.nbody_profile_read(cb, reset=True)[0] if flags else None
+                kms = nb.nbody_profile_read(cb, reset=True)[0] if flags & nb.NBODY_FLAG_PROFILE else None
+                trace = nb.nbody_block_trace(cb, b0 + 1, b1) if flags & nb.NBODY_FLAG_TRACE else None
                 _, dts = nb.nbody_block_state(cb)
-            return b1 - b0, e1_ - e0_, sec, kms, dts
+            return b1 - b0, e1_ - e0_, sec, kms, dts, trace
 
-        blocks, evals, sec, _, dts = block_run(0)
-        blocks_p, evals_p, sec_p, kms, _ = block_run(nb.NBODY_FLAG_PROFILE)
+        # the timed run records each step's start and size on the device (one
+        # thread's timer read and two stores a step)
+        blocks, evals, sec, _, dts, trace = block_run(nb.NBODY_FLAG_TRACE)
+        blocks_p, evals_p, sec_p, kms, _, _ = block_run(nb.NBODY_FLAG_PROFILE)
+        step_s, step_n = trace
+        regimes = {}
+        for name, lo, hi in (("few_particle_le_32", 1, 32), ("small_set_33_511", 33, 511),
+                             ("large_set_ge_512", 512, 1 << 62), ("one_active", 1, 1)):
+            sel = (step_n >= lo) & (step_n <= hi)
+            if sel.any():
+                regimes[name] = {"steps": int(sel.sum()), "seconds": float(step_s[sel].sum()),
+                                 "median_step_us": float(np.median(step_s[sel]) * 1e6),
+                                 "interactions_per_s": float(step_n[sel].sum() * float(PAPER_N)
+                                                             / step_s[sel].sum())}
         block = {"workload": "Plummer sphere N=102400 (seed 7), eps=1e-3, Hermite with individual "
                              "power-of-two steps (dt_max 2^-7, Aarseth eta 0.02) from t=2^-7 to 2^-4",
                  "block_steps": int(blocks), "particle_evaluations": int(evals),
                  "mean_active": evals / max(blocks, 1), "seconds": sec,
                  "interactions_per_s": evals * float(PAPER_N) / sec,
                  "subset_kernel_ms_total": kms,
+                 "per_regime": regimes,
+                 "per_regime_scope": "device trace (NBODY_FLAG_TRACE) of the timed run: a step runs "
+                                     "from its pack's start to the next one's; by active particles "
+                                     "(few-particle pass <= 32, small-set kernel < 512, large-set)",
                  "profiled_run": {"seconds": sec_p, "same_schedule": bool(blocks_p == blocks and
                                                                           evals_p == evals)},
                  "steps_histogram": {f"2^{int(round(np.log2(v)))}": int(c)

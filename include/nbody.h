@@ -84,6 +84,7 @@ extern "C" {
 #define NBODY_FLAG_PROFILE 2      /* time every force-kernel launch with CUDA events */
 #define NBODY_FLAG_CHECK_FINITE 4 /* verify outputs are finite after each call (syncs) */
 #define NBODY_FLAG_NO_GRAPH 8     /* nbody_step launches eagerly instead of graph replay */
+#define NBODY_FLAG_TRACE 16       /* F32C block steps: record each step's start and size (nbody_block_trace) */
 
 /*
  * Tile shape of the F32C force kernel.  block = threads per CTA, p = i-particles
@@ -248,6 +249,24 @@ int nbody_block_advance(nbody_ctx *ctx, double *pos, double *vel, const double *
                         double *jerk, double *pot, double t_end, int64_t *blocks, int64_t *evals,
                         void *stream);
 int nbody_block_state(nbody_ctx *ctx, double *t_host, double *dt_host, void *stream);
+
+/*
+ * With NBODY_FLAG_TRACE (NBODY_F32C block steps): the device records, as each
+ * block step's pack starts, the global timer (ns) and the number of particles
+ * the previous step moved, in a ring of NBODY_TRACE_CAP records indexed by the
+ * step count.  nbody_block_trace copies records first .. first + count - 1 to
+ * out (host, 2 * count values: time, count): record k holds the start of step
+ * k + 1 (steps counted from 1 as *blocks counts them) and the size of step k,
+ * so step k took record k's time minus record k - 1's.  The record after an
+ * advance call's last step is its end (the next pack's start, or the call's
+ * end); the next call's first step starts from its own record, which replaces
+ * it, so read a call's records before the next call.  Requires
+ * first + count <= blocks + 1 and count <= NBODY_TRACE_CAP, with the records
+ * not yet overwritten (blocks + 1 - first <= NBODY_TRACE_CAP); NBODY_EINVAL
+ * otherwise, NBODY_ESTATE without the flag.  Synchronises `stream`.
+ */
+#define NBODY_TRACE_CAP 65536
+int nbody_block_trace(nbody_ctx *ctx, uint64_t *out, int64_t first, int64_t count, void *stream);
 
 /* Tile shape of the acceleration + jerk kernel in use (zeros before its first use or in F64). */
 int nbody_get_jerk_tiles(const nbody_ctx *ctx, nbody_tiles *out);

@@ -41,13 +41,15 @@ NBODY_FLAG_AUTOTUNE = 1
 NBODY_FLAG_PROFILE = 2
 NBODY_FLAG_CHECK_FINITE = 4
 NBODY_FLAG_NO_GRAPH = 8
+NBODY_FLAG_TRACE = 16
+NBODY_TRACE_CAP = 65536
 
 EXPORTED = ("nbody_init", "nbody_destroy", "nbody_forces", "nbody_step", "nbody_energy",
             "nbody_tune", "nbody_get_tiles", "nbody_tiles_supported", "nbody_profile_read",
             "nbody_kernel_launches", "nbody_strerror", "nbody_last_error_message",
             "nbody_forces_noalloc", "nbody_forces_jerk",
             "nbody_step_hermite", "nbody_get_jerk_tiles", "nbody_set_jerk_tiles",
-            "nbody_block_start", "nbody_block_advance", "nbody_block_state")
+            "nbody_block_start", "nbody_block_advance", "nbody_block_state", "nbody_block_trace")
 
 
 class NBodyTiles(ctypes.Structure):
@@ -127,6 +129,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.nbody_block_advance.restype = ctypes.c_int
         lib.nbody_block_state.argtypes = [vp, vp, vp, vp]
         lib.nbody_block_state.restype = ctypes.c_int
+        lib.nbody_block_trace.argtypes = [vp, vp, i64, i64, vp]
+        lib.nbody_block_trace.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -324,6 +328,18 @@ def nbody_block_state(ctx: Context, stream=None):
                                   ctypes.c_void_p(dt.ctypes.data), _stream(stream))
     _check(ctx, rc, "nbody_block_state")
     return t, dt
+
+
+def nbody_block_trace(ctx: Context, first: int, last: int, stream=None):
+    """Steps first .. last (counted from 1, NBODY_FLAG_TRACE): (seconds, active
+    particles) of each, from trace records first - 1 .. last."""
+    count = last - first + 2
+    out = np.empty(2 * count, np.uint64)
+    rc = load().nbody_block_trace(ctx.handle, ctypes.c_void_p(out.ctypes.data), first - 1, count,
+                                  _stream(stream))
+    _check(ctx, rc, "nbody_block_trace")
+    rec = out.reshape(count, 2)
+    return np.diff(rec[:, 0].astype(np.int64)) * 1e-9, rec[1:, 1].astype(np.int64)
 
 
 def nbody_get_jerk_tiles(ctx: Context):

@@ -245,9 +245,40 @@ struct BlockPackParams {
     int cs_large, workers_large, large_min;
     long long partial_cap;  // doubles in the split-partial buffer
     int sms;
+    unsigned long long *trace;  // per-step trace ring (2 values a record) or null
+    int trace_cap;
     double dt_max, dt_min;
     float dt_min_f;  // dt_min as a float (exact: a power of two >= 2^-126)
 };
+
+// Per-step trace (NBODY_FLAG_TRACE): as the step starts, the global timer and
+// the previous step's active count at record `blocks` (the steps planned so
+// far).  A pack after a step that moved nobody (the batch's steps past t_end)
+// leaves the record alone, so that the last real step's end stays; a fresh
+// pack (the start of an advance call, a re-sort) always writes, so that a
+// call's first step starts at its own record.
+__device__ __forceinline__ void trace_step(const BlockPackParams &q, bool always) {
+    if (!q.trace || blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int moved = q.sc->n_active;
+    if (!always && moved == 0) return;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    unsigned long long *r = q.trace + 2 * (q.sc->blocks % q.trace_cap);
+    r[0] = t;
+    r[1] = (unsigned long long)moved;
+}
+
+// The end record of an advance call's last step when no pack followed it in
+// the call (the record that pack would have written).
+__global__ void block_trace_end_kernel(const BlockScalars *__restrict__ sc, unsigned long long *trace, int cap) {
+    const int moved = sc->n_active;
+    if (moved == 0) return;  // a pack after the last step wrote it
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    unsigned long long *r = trace + 2 * (sc->blocks % cap);
+    r[0] = t;
+    r[1] = (unsigned long long)moved;
+}
 
 // The step's time in units of dt_min (block_next_time_q with the level scan
 // done by one warp-wide ballot instead of a loop of dependent loads; every
@@ -320,6 +351,7 @@ __device__ __forceinline__ void predict_rows(const BlockPackParams &q, int64_t u
 // the mirror takes each particle's offsets from the frame at its own time.
 template <int NT, int PER>
 __global__ void __launch_bounds__(NT) block_fresh_kernel(const BlockPackParams q) {
+    trace_step(q, true);
     __shared__ float redf[NT / 32][8];
     __shared__ float cen[6];
     const int tile = blockIdx.x;
@@ -448,6 +480,7 @@ __global__ void __launch_bounds__(NT) block_fresh_kernel(const BlockPackParams q
 // pack wrote.
 template <int NT, int PER>
 __global__ void __launch_bounds__(NT) block_pack_kernel(const BlockPackParams q) {
+    trace_step(q, false);
     __shared__ int wcnt[NT / 32];
     const int tile = blockIdx.x;
     const long long tnq = next_time_q_warp(q.sc, q.dt_max, q.dt_min);
@@ -685,6 +718,8 @@ cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kern
         q.cs_large = b.cs_large; q.workers_large = b.workers_large; q.large_min = b.large_min;
         q.partial_cap = b.partial_cap;
         q.sms = b.sms;
+        q.trace = b.trace;
+        q.trace_cap = b.trace_cap;
         q.dt_max = b.dt_max;
         q.dt_min = b.dt_min;
         q.dt_min_f = (float)b.dt_min;
@@ -736,6 +771,11 @@ cudaError_t launch_block_correct(const BlockCorrect &c, const int32_t *act, cons
     // grid-stride over the active list: a few waves suffice for every particle
     const int grid = std::min(grid_of(c.n, 256), 2 * 152);
     block_correct_kernel<<<grid, 256, 0, s>>>(c, act, a1, j1, p1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_trace_end(const BlockScalars *sc, unsigned long long *trace, int cap, cudaStream_t s) {
+    block_trace_end_kernel<<<1, 1, 0, s>>>(sc, trace, cap);
     return cudaGetLastError();
 }
 

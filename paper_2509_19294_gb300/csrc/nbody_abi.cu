@@ -93,6 +93,7 @@ struct BlockState {
     int *cnt = nullptr, *chunk_off = nullptr, *act_begin = nullptr, *act_n = nullptr;
     int *ich_off = nullptr, *item_off = nullptr;
     long long *work_off = nullptr;
+    unsigned long long *trace = nullptr;  // NBODY_FLAG_TRACE: NBODY_TRACE_CAP records of (time, count)
     int32_t *act = nullptr;
     SubItem *items = nullptr, *info = nullptr;
     BlockScalars *sc = nullptr;
@@ -841,6 +842,7 @@ void free_block(nbody_ctx *ctx) {
     dev_free(&b.flag);
     for (int **q : {&b.cnt, &b.chunk_off, &b.act_begin, &b.act_n, &b.ich_off, &b.item_off}) dev_free(q);
     dev_free(&b.work_off);
+    dev_free(&b.trace);
     dev_free(&b.act);
     dev_free(&b.items);
     dev_free(&b.info);
@@ -925,6 +927,10 @@ int alloc_block(nbody_ctx *ctx) {
     for (int **q : {&b.act_begin, &b.act_n, &b.ich_off, &b.item_off})
         if ((rc = dev_alloc(ctx, q, ncl + 1))) return rc;
     if (f32c && (rc = dev_alloc(ctx, &b.work_off, ncl + 1))) return rc;
+    if (f32c && (ctx->flags & NBODY_FLAG_TRACE)) {
+        if ((rc = dev_alloc(ctx, &b.trace, 2 * (size_t)NBODY_TRACE_CAP))) return rc;
+        NB_CUDA(cudaMemset(b.trace, 0, 2 * (size_t)NBODY_TRACE_CAP * sizeof(unsigned long long)));
+    }
     if ((rc = dev_alloc(ctx, &b.act, n))) return rc;
     if (!f32c) {  // the FP64 path's work queue (the F32C plan cuts even ranges of units)
         if ((rc = dev_alloc(ctx, &b.items, (size_t)b.max_items))) return rc;
@@ -991,6 +997,8 @@ BlockLaunch block_launch(nbody_ctx *ctx, const Arrays &a) {
         b.large_min = bs.large_min;
         b.partial_cap = bs.partial_cap;
         b.sms = ctx->sms;
+        b.trace = bs.trace;
+        b.trace_cap = NBODY_TRACE_CAP;
     }
     return b;
 }
@@ -1392,6 +1400,28 @@ int nbody_get_tiles(const nbody_ctx *ctx, nbody_tiles *out) {
 
 int64_t nbody_kernel_launches(const nbody_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+int nbody_block_trace(nbody_ctx *ctx, uint64_t *out, int64_t first, int64_t count, void *stream) {
+    int rc = guard(ctx);
+    if (rc) return rc;
+    if (!(ctx->flags & NBODY_FLAG_TRACE) || !ctx->bs.trace)
+        return fail(ctx, NBODY_ESTATE, "no trace: NBODY_FLAG_TRACE with NBODY_F32C block steps");
+    cudaStream_t s = (cudaStream_t)stream;
+    NB_CUDA(cudaStreamSynchronize(s));
+    long long blocks = 0;
+    NB_CUDA(cudaMemcpy(&blocks, &ctx->bs.sc->blocks, sizeof blocks, cudaMemcpyDeviceToHost));
+    if (count < 0 || first < 0 || (count > 0 && !out) || first + count > blocks + 1 ||
+        count > NBODY_TRACE_CAP || blocks + 1 - first > NBODY_TRACE_CAP)
+        return fail(ctx, NBODY_EINVAL, "trace records out of range");
+    for (int64_t k = 0; k < count;) {  // the ring in at most two pieces
+        const int64_t at = (first + k) % NBODY_TRACE_CAP;
+        const int64_t piece = std::min<int64_t>(count - k, NBODY_TRACE_CAP - at);
+        NB_CUDA(cudaMemcpy(out + 2 * k, ctx->bs.trace + 2 * at, (size_t)piece * 2 * sizeof(uint64_t),
+                           cudaMemcpyDeviceToHost));
+        k += piece;
+    }
+    return NBODY_OK;
+}
+
 int nbody_profile_read(nbody_ctx *ctx, double *ms_total, int64_t *launches, int reset) {
     if (!ctx) return NBODY_EINVAL;
     for (int sl = 0; sl < kProfSlots; ++sl) {
@@ -1699,6 +1729,7 @@ int nbody_block_advance(nbody_ctx *ctx, double *pos, double *vel, const double *
             }
         }
     }
+    if (b.trace) NB_CUDA(launch_block_trace_end(b.sc, b.trace, NBODY_TRACE_CAP, s));
     if (blocks) *blocks = h.blocks;
     if (evals) *evals = h.evals;
     return NBODY_OK;

@@ -404,6 +404,8 @@ struct BlockLaunch {
     int cs_large, workers_large, large_min;
     long long partial_cap;  // doubles in the subset kernels' split-partial buffer
     int sms;  // multiprocessors (the even split's range count is a multiple)
+    unsigned long long *trace;  // F32C per-step trace (NBODY_FLAG_TRACE) or null
+    int trace_cap;
 };
 
 cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, double dt_max,
@@ -413,6 +415,9 @@ cudaError_t launch_block_init(int64_t n, const double *acc, const double *jerk, 
 // (+ the packed j-set for F32C), flags, counts and the plan (offsets, regime,
 // and the force pass's work: F32C even ranges of units, FP64 queue items).
 cudaError_t launch_block_prepare(const BlockLaunch &b, cudaStream_t s, int *kernels);
+// NBODY_FLAG_TRACE: the end record of an advance call's last step, if no pack
+// after it wrote one.
+cudaError_t launch_block_trace_end(const BlockScalars *sc, unsigned long long *trace, int cap, cudaStream_t s);
 // Ordered compaction of the active particles (rows, or j-set slots for F32C)
 // and, on the FP64 path, the work queue.
 cudaError_t launch_block_queue(const BlockLaunch &b, cudaStream_t s, int *kernels);

@@ -136,6 +136,34 @@ def test_f32c_step_criterion_outside_the_float_range_takes_the_fp64_decision():
     assert np.median(dv) <= 1e-10 and dv.max() <= 1e-5, (np.median(dv), dv.max())
 
 
+def test_f32c_block_trace_records_every_step():
+    # NBODY_FLAG_TRACE: one record per step, each step's size its active
+    # count; two advance calls, each read back after it
+    pos, vel, mass = cluster_system(2000, 53)
+    n = mass.shape[0]
+    with nb.nbody_init(n, 0.005, mode=nb.NBODY_F32C, flags=nb.NBODY_FLAG_TRACE) as ctx:
+        p, v, m = dev(pos), dev(vel), dev(mass)
+        a = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        j = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        ph = torch.empty(n, dtype=torch.float64, device="cuda")
+        nb.nbody_block_start(ctx, p, v, m, a, j, ph, DT_MAX, DT_MIN, 0.02, 0.01)
+        b1, e1 = nb.nbody_block_advance(ctx, p, v, m, a, j, ph, T_END / 2)
+        s1, n1 = nb.nbody_block_trace(ctx, 1, b1)
+        b2, e2 = nb.nbody_block_advance(ctx, p, v, m, a, j, ph, T_END)
+        s2, n2 = nb.nbody_block_trace(ctx, b1 + 1, b2)
+        for secs, act, blocks, evals in ((s1, n1, b1, e1), (s2, n2, b2 - b1, e2 - e1)):
+            assert len(secs) == blocks and len(act) == blocks
+            assert np.all(act >= 1) and act.sum() == evals
+            assert np.all(secs > 0) and secs.sum() < 10.0
+        with pytest.raises(nb.NBodyError) as e:
+            nb.nbody_block_trace(ctx, 1, b2 + 1)  # the record after the last one does not exist
+        assert e.value.code == nb.NBODY_EINVAL
+    with nb.nbody_init(n, 0.005, mode=nb.NBODY_F32C) as ctx:
+        with pytest.raises(nb.NBodyError) as e:
+            nb.nbody_block_trace(ctx, 1, 1)
+        assert e.value.code == nb.NBODY_ESTATE
+
+
 @pytest.mark.parametrize("mode", [nb.NBODY_F64, nb.NBODY_F32C])
 def test_ensemble_block_steps_equal_independent_clusters(oracle, mode):
     ens = ic.ensemble(5, seed=54, n_min=256, n_max=900)
